@@ -1,0 +1,108 @@
+"""Camera covariances by the paper's route (oracle), Sec. 3 and Sec. 4.2.
+
+The natural covariance is the top-left block of the inverse of the bordered
+matrix [M H; H^T 0] (Eq. inversion-of-extended-information-matrix).  Sec. 4.2
+conditions it with diagonal S = diag(S_a, S_b) (S Q^-1 S), permutes the point
+parameters first, Q_p = [A_p B_p; B_p^T D_p], and inverts Q_p by block matrix
+inversion (Eq. block-inversion-Qp): the camera part is the top-left block of
+Z_p^-1, Z_p = D_p - B_p^T A_p^-1 B_p (Eq. schur-complement-inversion), and
+Sigma_P = S_P Z_s S_P.
+
+Readings (the paper leaves S_a, S_b unspecified): S_a = diag(M)^-1/2 (Jacobi
+scaling of the columns of J) and S_b makes each column of S_a H unit-norm.
+The result does not depend on S.  Z_p is symmetric indefinite; it is
+inverted by LU with partial pivoting (LAPACK getrf/getrs via scipy).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from . import camera, information, nullspace
+
+
+def _scales(U, A, HP, HX, mode):
+    n, m = U.shape[0], A.shape[0]
+    if mode == "none":
+        sP, sX, sb = np.ones((n, 9)), np.ones((m, 3)), np.ones(7)
+    elif mode == "jacobi":
+        sP = 1.0 / np.sqrt(np.einsum("nii->ni", U))
+        sX = 1.0 / np.sqrt(np.einsum("mii->mi", A))
+        col = np.sqrt(((sP[:, :, None] * HP) ** 2).sum((0, 1))
+                      + ((sX[:, :, None] * HX) ** 2).sum((0, 1)))
+        sb = 1.0 / col
+    else:
+        raise ValueError(mode)
+    return sP, sX, sb
+
+
+def schur_system(scene, scaling="jacobi"):
+    """Z_p = D_p - B_p^T A_p^-1 B_p of the (conditioned) permuted bordered
+    matrix, dense (9n+7)^2, plus the scale vector of its rows/columns."""
+    U, A, W, Jc, Jp = information.blocks(scene)
+    HP = nullspace.camera_rows(scene, Jc, Jp)
+    HX = nullspace.point_rows(scene.pts)
+    return _schur_from_blocks(scene, U, A, W, HP, HX, scaling)
+
+
+def _schur_from_blocks(scene, U, A, W, HP, HX, scaling):
+    n, m, t = scene.n, scene.m, scene.t
+    N = 9 * n
+    sP, sX, sb = _scales(U, A, HP, HX, scaling)
+    # conditioned blocks: S_a M S_a and S_a H S_b
+    Us = sP[:, :, None] * U * sP[:, None, :]
+    As = sX[:, :, None] * A * sX[:, None, :]
+    Ws = sP[scene.obs_cam][:, :, None] * W * sX[scene.obs_pt][:, None, :]
+    HPs = sP[:, :, None] * HP * sb
+    HXs = sX[:, :, None] * HX * sb
+    # A_p^-1: block diagonal with the inverted 3x3 point blocks
+    Ainv = np.linalg.inv(As)
+    ii = (3 * np.arange(m)[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
+    jj = (3 * np.arange(m)[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
+    Ap_inv = sp.csr_matrix((Ainv.ravel(), (ii.ravel(), jj.ravel())), shape=(3 * m, 3 * m))
+    # B_p = [M_XP, H_X]: rows of points, columns of cameras then the 7 of H
+    r = (3 * scene.obs_pt[:, None, None] + np.arange(3)[None, :, None]).repeat(9, 2)
+    c = (9 * scene.obs_cam[:, None, None] + np.arange(9)[None, None, :]).repeat(3, 1)
+    rh = (np.arange(3 * m)[:, None]).repeat(7, 1)
+    ch = (N + np.arange(7)[None, :]).repeat(3 * m, 0)
+    Bp = sp.csr_matrix((np.concatenate([Ws.transpose(0, 2, 1).ravel(), HXs.reshape(-1, 7).ravel()]),
+                        (np.concatenate([r.ravel(), rh.ravel()]),
+                         np.concatenate([c.ravel(), ch.ravel()]))),
+                       shape=(3 * m, N + 7))
+    # D_p = [M_PP, H_P; H_P^T, 0]
+    Dp = np.zeros((N + 7, N + 7))
+    for i in range(n):
+        Dp[9 * i:9 * i + 9, 9 * i:9 * i + 9] = Us[i]
+    Dp[:N, N:] = HPs.reshape(N, 7)
+    Dp[N:, :N] = HPs.reshape(N, 7).T
+    Zp = Dp - (Bp.T @ (Ap_inv @ Bp)).toarray()
+    scale = np.concatenate([sP.ravel(), sb])
+    return Zp, scale
+
+
+def schur_blocks_unscaled(scene):
+    """Z (9n x 9n), G (9n x 7) and W7 (7 x 7) with Z_p = [Z, G; G^T, -W7]
+    for the unconditioned system: Z = M_PP - M_PX A^-1 M_XP,
+    G = H_P - M_PX A^-1 H_X, W7 = H_X^T A^-1 H_X."""
+    Zp, _ = schur_system(scene, scaling="none")
+    N = 9 * scene.n
+    return Zp[:N, :N], Zp[:N, N:], -Zp[N:, N:]
+
+
+def camera_covariance(scene, scaling="jacobi", full=False):
+    """Sigma_P = S_P Z_s S_P, Z_s the top-left 9n x 9n block of Z_p^-1.
+    Returns the diagonal 9x9 blocks (n, 9, 9), or the whole 9n x 9n matrix."""
+    Zp, scale = schur_system(scene, scaling)
+    N = 9 * scene.n
+    lu = sla.lu_factor(Zp, check_finite=True)
+    E = np.zeros((N + 7, N))
+    E[np.arange(N), np.arange(N)] = 1.0
+    Zinv_cols = sla.lu_solve(lu, E)
+    Zs = Zinv_cols[:N, :N]
+    sP = scale[:N]
+    Sigma = sP[:, None] * Zs * sP[None, :]
+    if full:
+        return Sigma
+    n = scene.n
+    return np.stack([Sigma[9 * i:9 * i + 9, 9 * i:9 * i + 9] for i in range(n)])

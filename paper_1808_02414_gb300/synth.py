@@ -1,0 +1,268 @@
+"""Seeded synthetic SfM scenes (inputs only).
+
+This module draws cameras, points, tracks and noisy image observations with
+the shapes of the paper's datasets (Table 1: mean track length N_u/N_X of
+about 3-8).  It is the one module that both the CUDA path and the CPU oracle
+are fed from; it holds none of the covariance method's arithmetic.  Camera
+rotations are built as look-at matrices and handed out as angle-axis vectors;
+the observed image points u are synthetic measurements (a look-at projection
+plus Gaussian noise) and never enter the covariance, which depends only on
+the parameters, the index set S and Sigma_u (Sec. 3, Eq. for M).
+
+Camera vector (9 values): r (angle-axis, 3), t (3), f, k1, k2, with the camera
+frame X_c = R(r) X + t, +z forward, and u = f (1 + k1 rho^2 + k2 rho^4) x for
+x = X_c[:2] / X_c[2].
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+__all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
+           "subscene", "WORKLOADS", "workload"]
+
+
+@dataclass
+class Scene:
+    cams: np.ndarray          # (n, 9) float64
+    pts: np.ndarray           # (m, 3) float64
+    obs_cam: np.ndarray       # (t,) int32, observations sorted by point
+    obs_pt: np.ndarray        # (t,) int32
+    obs_u: np.ndarray         # (t, 2) float64
+    sigma: float = 1.0
+    obs_cov: np.ndarray | None = None   # (t, 2, 2) float64 or None (sigma^2 I)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.cams.shape[0]
+
+    @property
+    def m(self) -> int:
+        return self.pts.shape[0]
+
+    @property
+    def t(self) -> int:
+        return self.obs_cam.shape[0]
+
+    def obs_records(self) -> np.ndarray:
+        """Observations as the packed 24-byte record array of the C ABI."""
+        rec = np.zeros(self.t, dtype=OBS_DTYPE)
+        rec["cam"] = self.obs_cam
+        rec["pt"] = self.obs_pt
+        rec["u"] = self.obs_u
+        return rec
+
+
+OBS_DTYPE = np.dtype([("cam", "<i4"), ("pt", "<i4"), ("u", "<f8", (2,))])
+
+
+def _look_at(center: np.ndarray, up: np.ndarray) -> np.ndarray:
+    """World-to-camera rotation whose third row points from center to origin."""
+    z = -center / np.linalg.norm(center)
+    if abs(float(z @ up)) > 0.95:
+        up = np.array([1.0, 0.0, 0.0])
+    x = np.cross(z, up)
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    return np.stack([x, y, z])
+
+
+def _roll(gamma: float) -> np.ndarray:
+    c, s = np.cos(gamma), np.sin(gamma)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def _angle_axis(R: np.ndarray) -> np.ndarray:
+    """Rotation vector of a proper rotation with angle below pi - 0.1."""
+    cos_t = np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)
+    theta = np.arccos(cos_t)
+    w = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]]) / 2.0
+    if theta < 1e-7:
+        return w
+    return w * (theta / np.sin(theta))
+
+
+def _make_cameras(rng, centers: np.ndarray, f_range=(950.0, 1050.0), k_std=1e-3):
+    """Look-at cameras with a random roll; the roll is redrawn until the
+    rotation angle lies in (0.05, pi - 0.1), where the angle-axis vector read
+    off the matrix is well defined and accurate."""
+    n = centers.shape[0]
+    cams = np.zeros((n, 9))
+    Rs = np.zeros((n, 3, 3))
+    up = np.array([0.0, 0.0, 1.0])
+    for i in range(n):
+        R = None
+        for _ in range(64):
+            base = _look_at(centers[i], up)
+            for _ in range(64):
+                cand = _roll(rng.uniform(0.0, 2.0 * np.pi)) @ base
+                theta = np.arccos(np.clip((np.trace(cand) - 1.0) / 2.0, -1.0, 1.0))
+                if 0.05 < theta < np.pi - 0.1:
+                    R = cand
+                    break
+            if R is not None:
+                break
+            # a camera looking almost straight down -z has a rotation angle
+            # near pi for every roll: redraw its direction on the same sphere
+            d = rng.normal(size=3)
+            centers[i] = np.linalg.norm(centers[i]) * d / np.linalg.norm(d)
+        if R is None:
+            raise RuntimeError("could not place a camera")
+        Rs[i] = R
+        cams[i, 0:3] = _angle_axis(R)
+        cams[i, 3:6] = -R @ centers[i]
+    cams[:, 6] = rng.uniform(f_range[0], f_range[1], n)
+    cams[:, 7] = rng.normal(0.0, k_std, n)
+    cams[:, 8] = rng.normal(0.0, k_std, n)
+    return cams, Rs
+
+
+def _distinct_tracks(rng, n: int, lengths: np.ndarray) -> list[np.ndarray]:
+    """For each point, `lengths[j]` distinct camera indices drawn uniformly."""
+    m = lengths.shape[0]
+    out: list[np.ndarray | None] = [None] * m
+    for L in np.unique(lengths):
+        idx = np.nonzero(lengths == L)[0]
+        if L * (L - 1) > n:
+            # rejection would rarely succeed: take the first L of a random
+            # permutation (argsort of uniform keys), a few rows at a time
+            for c0 in range(0, idx.size, 4096):
+                blk = idx[c0:c0 + 4096]
+                rows = np.argsort(rng.random((blk.size, n)), axis=1)[:, :L]
+                for k, j in enumerate(blk):
+                    out[j] = rows[k]
+            continue
+        rows = rng.integers(0, n, size=(idx.size, L))
+        while True:
+            srt = np.sort(rows, axis=1)
+            bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0] if L > 1 else np.array([], int)
+            if bad.size == 0:
+                break
+            rows[bad] = rng.integers(0, n, size=(bad.size, L))
+        for k, j in enumerate(idx):
+            out[j] = rows[k]
+    return out  # type: ignore[return-value]
+
+
+def _observe(rng, cams, Rs, pts, tracks, noise_px=1.0):
+    cam_idx = np.concatenate(tracks).astype(np.int32)
+    pt_idx = np.repeat(np.arange(len(tracks), dtype=np.int32),
+                       [len(tr) for tr in tracks])
+    # sort by (point, camera) for a deterministic layout
+    order = np.lexsort((cam_idx, pt_idx))
+    cam_idx, pt_idx = cam_idx[order], pt_idx[order]
+    Xc = np.einsum("tij,tj->ti", Rs[cam_idx], pts[pt_idx]) + cams[cam_idx, 3:6]
+    if np.any(Xc[:, 2] <= 0.0):
+        raise RuntimeError("synthetic point behind a camera")
+    x = Xc[:, :2] / Xc[:, 2:3]
+    rho2 = (x * x).sum(1)
+    g = 1.0 + cams[cam_idx, 7] * rho2 + cams[cam_idx, 8] * rho2 * rho2
+    u = cams[cam_idx, 6:7] * g[:, None] * x + rng.normal(0.0, noise_px, size=x.shape)
+    return cam_idx, pt_idx, u
+
+
+def _ensure_min_obs(rng, n, tracks, min_obs=5):
+    counts = np.bincount(np.concatenate(tracks), minlength=n)
+    for c in np.nonzero(counts < min_obs)[0]:
+        need = min_obs - counts[c]
+        cand = [j for j in rng.permutation(len(tracks)) if c not in tracks[j]]
+        for j in cand[:need]:
+            tracks[j] = np.append(tracks[j], c)
+    return tracks
+
+
+def ring_scene(n=20, m=500, track_len=5, radius=10.0, seed=0, noise_px=1.0,
+               sigma=1.0) -> Scene:
+    """n cameras on a ring of `radius` in the z=0 plane at angles 2*pi*i/n,
+    looking at the origin; m points uniform in [-1/2, 1/2]^3; every point seen
+    by exactly `track_len` distinct random cameras."""
+    rng = np.random.default_rng(seed)
+    ang = 2.0 * np.pi * np.arange(n) / n
+    centers = np.stack([radius * np.cos(ang), radius * np.sin(ang), np.zeros(n)], 1)
+    cams, Rs = _make_cameras(rng, centers)
+    pts = rng.uniform(-0.5, 0.5, size=(m, 3))
+    tracks = _distinct_tracks(rng, n, np.full(m, min(track_len, n)))
+    tracks = _ensure_min_obs(rng, n, tracks)
+    ci, pi, u = _observe(rng, cams, Rs, pts, tracks, noise_px)
+    return Scene(cams, pts, ci, pi, u, sigma, None,
+                 {"kind": "ring", "seed": seed, "n": n, "m": m})
+
+
+def shell_scene(n=1000, m=100_000, p_geom=1.0 / 7.0, radius=10.0, seed=1,
+                noise_px=1.0, sigma=1.0, min_obs=5) -> Scene:
+    """n cameras with directions uniform on the sphere at `radius`, looking at
+    the origin; m points uniform in the unit cube [-1/2, 1/2]^3; track length
+    L = 1 + Geometric(p) (min 2, mean 1/p + 1), capped at n, distinct cameras."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    centers = radius * d
+    cams, Rs = _make_cameras(rng, centers)
+    pts = rng.uniform(-0.5, 0.5, size=(m, 3))
+    lengths = np.minimum(1 + rng.geometric(p_geom, size=m), n)
+    tracks = _distinct_tracks(rng, n, lengths)
+    tracks = _ensure_min_obs(rng, n, tracks, min_obs)
+    ci, pi, u = _observe(rng, cams, Rs, pts, tracks, noise_px)
+    return Scene(cams, pts, ci, pi, u, sigma, None,
+                 {"kind": "shell", "seed": seed, "n": n, "m": m})
+
+
+def tiny_scene(n=4, m=14, track_len=3, seed=0, anisotropic=False) -> Scene:
+    """A very small ring scene for brute-force checks.  With `anisotropic`,
+    each observation gets its own random SPD 2x2 covariance."""
+    sc = ring_scene(n=n, m=m, track_len=track_len, seed=seed)
+    if anisotropic:
+        rng = np.random.default_rng(1000 + seed)
+        a = rng.uniform(0.5, 2.0, size=(sc.t, 2))
+        th = rng.uniform(0, np.pi, size=sc.t)
+        c, s = np.cos(th), np.sin(th)
+        Rr = np.stack([np.stack([c, -s], -1), np.stack([s, c], -1)], -2)
+        sc.obs_cov = np.einsum("tij,tj,tkj->tik", Rr, a, Rr)
+    return sc
+
+
+def subscene(sc: Scene, cam_ids: np.ndarray, min_track=2) -> Scene:
+    """The sub-reconstruction spanned by `cam_ids`: their observations of points
+    still seen by at least `min_track` of them (Sec. 5, sub-reconstructions)."""
+    cam_ids = np.asarray(cam_ids)
+    remap = -np.ones(sc.n, dtype=np.int64)
+    remap[cam_ids] = np.arange(cam_ids.size)
+    keep = remap[sc.obs_cam] >= 0
+    cnt = np.bincount(sc.obs_pt[keep], minlength=sc.m)
+    keep &= cnt[sc.obs_pt] >= min_track
+    pts_used = np.unique(sc.obs_pt[keep])
+    premap = -np.ones(sc.m, dtype=np.int64)
+    premap[pts_used] = np.arange(pts_used.size)
+    ci = remap[sc.obs_cam[keep]].astype(np.int32)
+    pi = premap[sc.obs_pt[keep]].astype(np.int32)
+    order = np.lexsort((ci, pi))
+    cov = None if sc.obs_cov is None else sc.obs_cov[keep][order]
+    return Scene(sc.cams[cam_ids].copy(), sc.pts[pts_used].copy(), ci[order], pi[order],
+                 sc.obs_u[keep][order], sc.sigma, cov,
+                 {"kind": "sub", "parent": sc.meta, "n": int(cam_ids.size)})
+
+
+def batch_scenes(k=256, n_lo=10, n_hi=300, pts_per_cam=100, p_geom=0.2, seed=4):
+    """k independent sub-reconstructions, n_b ~ U{n_lo..n_hi}, m_b = 100 n_b,
+    track length 1 + Geometric(p) (mean 6 for p = 0.2)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=k)
+    return [shell_scene(n=int(nb), m=int(pts_per_cam * nb), p_geom=p_geom,
+                        seed=int(seed * 100003 + b)) for b, nb in enumerate(ns)]
+
+
+# Named workloads: the camera counts, point counts and track statistics of the
+# small ring case, the 1000-camera and the 4000-camera shell scenes.
+WORKLOADS = {
+    "ring20": dict(fn="ring", n=20, m=500, track_len=5, seed=0),
+    "shell1k": dict(fn="shell", n=1000, m=100_000, p_geom=1.0 / 7.0, seed=1),
+    "shell4k": dict(fn="shell", n=4000, m=400_000, p_geom=1.0 / 7.0, seed=2),
+}
+
+
+def workload(name: str, **over) -> Scene:
+    spec = dict(WORKLOADS[name])
+    spec.update(over)
+    fn = spec.pop("fn")
+    return ring_scene(**spec) if fn == "ring" else shell_scene(**spec)
