@@ -1,0 +1,170 @@
+/*
+ * ccov: camera covariance propagation for bundle-adjusted reconstructions on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Polic, Foerstner, Pajdla, "Fast and Accurate Camera Covariance
+ * Computation for Large 3D Reconstruction".  Given the estimated cameras and
+ * points, the index set S of observations and the image-point covariance
+ * Sigma_u (Sec. 3), the library returns the 9x9 camera blocks of the natural
+ * covariance, i.e. the camera part of the inverse of the bordered information
+ * matrix [M H; H^T 0] (Sec. 3, Eq. inversion-of-extended-information-matrix),
+ * which equals the camera part of the Moore-Penrose inverse of M.
+ *
+ * Camera model (9 values per camera, row-major n x 9):
+ *   P_i = {r (angle-axis, 3), t (3), f, k1, k2},  X_c = R(r) X + t,
+ *   u_hat = f (1 + k1 rho^2 + k2 rho^4) (X_c[0], X_c[1]) / X_c[2],
+ *   rho^2 = (X_c[0]^2 + X_c[1]^2) / X_c[2]^2.
+ * This is the translation form of the projection of Sec. 4.1 with two radial
+ * distortion terms.  Output blocks use the same parameter order.
+ *
+ * Call order on one context: ccov_create -> ccov_information -> ccov_schur ->
+ * ccov_nullspace -> ccov_covariance.  ccov_nullspace may come anywhere before
+ * ccov_covariance.  A call made out of order returns CCOV_ERR_INVALID_ARG.
+ * Each call runs on the context's CUDA stream and returns after that stream
+ * has finished the call's work, so its status covers device-side checks.
+ *
+ * Ownership: the caller owns every buffer it passes; ccov_create copies the
+ * inputs; outputs are written into caller-allocated buffers.  The library
+ * allocates its own device workspace in ccov_create (with cudaMalloc) and
+ * frees it in ccov_destroy.  No global state: one context per thread.
+ * Errors: every entry point returns a ccov_status; after a failure the
+ * context stays valid for ccov_destroy and ccov_last_error.
+ */
+#ifndef CCOV_H
+#define CCOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CCOV_API __attribute__((visibility("default")))
+#else
+#define CCOV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccov_ctx ccov_ctx;
+
+/* One observation u_ij of point `pt` in camera `cam` (24 bytes, packed as
+ * int32, int32, float64[2]).  The observed u does not enter the covariance
+ * (M depends on theta, S and Sigma_u only, Sec. 3); it is validated as finite. */
+typedef struct {
+    int32_t cam;
+    int32_t pt;
+    double u[2];
+} ccov_obs;
+
+typedef enum {
+    CCOV_OK = 0,
+    CCOV_ERR_INVALID_ARG = 1,   /* bad size, index, pointer, order of calls */
+    CCOV_ERR_DEGENERATE = 2,    /* track < 2, camera < 2 obs, point behind a camera,
+                                   singular point block A_j or W7, matrix not SPD */
+    CCOV_ERR_NOT_CONVERGED = 3,
+    CCOV_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    CCOV_ERR_OOM = 5,           /* device allocation failed */
+    CCOV_ERR_CUDA = 6           /* any other CUDA runtime error */
+} ccov_status;
+
+enum { CCOV_PREC_FP64 = 0, CCOV_PREC_MIXED = 1 };
+enum { CCOV_MEM_HOST = 0, CCOV_MEM_DEVICE = 1 };
+enum { CCOV_NULL_PAPER = 0, CCOV_NULL_CLOSED = 1 };
+
+typedef struct {
+    int precision;        /* CCOV_PREC_FP64 (default) or CCOV_PREC_MIXED */
+    int mixed_slices;     /* MIXED only: 8-bit digit slices per operand, 4..7; 0 = 6 */
+    int nullspace_route;  /* CCOV_NULL_PAPER: rotation rows from J_r H_r = B (Sec. 4.1,
+                             Eq. rotation-nullspace-equation), default;
+                             CCOV_NULL_CLOSED: -J_r^-1(r) in closed form */
+    int input_memory;     /* where ccov_create's / ccov_load's arrays live:
+                             CCOV_MEM_HOST (default) or CCOV_MEM_DEVICE */
+    int reserved[8];      /* set to zero */
+} ccov_options;
+
+/* Per-context counters of the last calls (device times from CUDA events). */
+typedef struct {
+    int64_t n, m, t, N, N_pad;
+    double ms_information, ms_schur, ms_nullspace, ms_covariance;
+    double ms_factor, ms_inverse;       /* parts of ms_covariance */
+    int64_t bytes_device;               /* device workspace held by the context */
+    int64_t launches;                   /* kernels launched by the last four calls */
+} ccov_stats;
+
+/* Create a context for one scene and copy its inputs to the device.
+ *   cameras  n x 9 float64, row-major, parameter order (r, t, f, k1, k2)
+ *   points   m x 3 float64, row-major
+ *   obs      t records sorted by point index (non-decreasing `pt`); each
+ *            (cam, pt) pair at most once; every point needs >= 2 observations
+ *            and every camera >= 2
+ *   sigma    isotropic image-point standard deviation in pixels (> 0); used
+ *            when obs_cov is NULL, Sigma_u = sigma^2 I (Sec. 3)
+ *   obs_cov  NULL, or t x 4 float64: per-observation 2x2 SPD covariance
+ *            Sigma_u_ij, row-major (Sec. 3, block-diagonal Sigma_u)
+ *   opt      NULL for defaults
+ *   stream   a cudaStream_t, or NULL for a stream the context creates
+ * Errors: INVALID_ARG for sizes, indices, ordering or non-finite values;
+ * DEGENERATE for tracks or cameras with fewer than two observations;
+ * OOM when the device workspace (about 2 (9n)^2 x 8 bytes) does not fit. */
+CCOV_API ccov_status ccov_create(const double* cameras, int64_t n, const double* points, int64_t m,
+                        const ccov_obs* obs, int64_t t, double sigma, const double* obs_cov,
+                        const ccov_options* opt, void* stream, ccov_ctx** out);
+
+/* Replace the inputs of an existing context by a scene of the same n, m, t
+ * and the same index set S (same cam/pt columns of `obs`).  `memory` says
+ * where the arrays live (CCOV_MEM_HOST or CCOV_MEM_DEVICE).  Resets the call
+ * sequence to "created". */
+CCOV_API ccov_status ccov_load(ccov_ctx* ctx, const double* cameras, const double* points,
+                      const ccov_obs* obs, const double* obs_cov, int memory);
+
+/* Step (a), Sec. 3 Eq. normal-equation-system: analytic reprojection
+ * Jacobians of every observation, whitened by Sigma_u^-1/2, and the blocks of
+ * M = J^T Sigma_u^-1 J: U_i (camera), A_j^-1 (point, inverted) and W_ij.
+ * DEGENERATE if a point lies behind a camera or a point block is singular. */
+CCOV_API ccov_status ccov_information(ccov_ctx* ctx);
+
+/* Step (b), Sec. 4.2 Eq. schur-complement-inversion: eliminate the 3x3 point
+ * blocks.  Builds the dense reduced camera matrix Z = U - W A^-1 W^T
+ * (9n x 9n, FP64, lower triangle), the border part -W A^-1 H_X of G and
+ * W7 = H_X^T A^-1 H_X, i.e. Z_p = [Z, G; G^T, -W7] of Eq. block-inversion-Qp
+ * for the unconditioned system. */
+CCOV_API ccov_status ccov_schur(ccov_ctx* ctx);
+
+/* Step (c), Sec. 4.1: the camera rows H_P (n x 9 x 7, columns [T, omega, mu])
+ * of the similarity nullspace.  Translation and scale columns in closed form
+ * (Eq. transformation-conditions); rotation rows from J_r H_r = B per camera
+ * (Eq. rotation-nullspace-equation), least squares over the camera's rows.
+ * H_P_out: NULL, or a host buffer of n*63 float64 (row-major 9 x 7 blocks). */
+CCOV_API ccov_status ccov_nullspace(ccov_ctx* ctx, double* H_P_out);
+
+/* Step (d), Sec. 4.2: Sigma_P = top-left block of Z_p^-1 =
+ * (Z + G W7^-1 G^T)^-1 (block inversion of Z_p), computed as Jacobi scaling,
+ * Cholesky factorisation, triangular inverse and the 9x9 diagonal blocks of
+ * the inverse.  out: n*81 float64 (row-major 9 x 9 blocks) on the host
+ * (out_memory = CCOV_MEM_HOST) or the device (CCOV_MEM_DEVICE).
+ * est_rel_err: NULL, or n doubles receiving a per-block estimate of the
+ * relative error (0 for the FP64 path).  DEGENERATE if the scaled reduced
+ * matrix is not positive definite. */
+CCOV_API ccov_status ccov_covariance(ccov_ctx* ctx, double* out, int out_memory, double* est_rel_err);
+
+/* Copies of intermediate results for checking (host buffers, NULL to skip):
+ *   U     n x 81 camera blocks of M          A_inv  m x 9 inverted point blocks
+ *   W     t x 27 (9 x 3 per observation, in observation order)
+ *   Z     (9n) x (9n) after ccov_schur: lower triangle valid, upper undefined
+ *   G     (9n) x 7 after ccov_schur and ccov_nullspace (H_P - W A^-1 H_X)
+ *   W7    7 x 7 */
+CCOV_API ccov_status ccov_get_blocks(ccov_ctx* ctx, double* U, double* A_inv, double* W);
+CCOV_API ccov_status ccov_get_schur(ccov_ctx* ctx, double* Z, double* G, double* W7);
+
+CCOV_API ccov_status ccov_get_stats(const ccov_ctx* ctx, ccov_stats* out);
+CCOV_API void ccov_destroy(ccov_ctx* ctx);
+CCOV_API const char* ccov_status_string(ccov_status s);
+/* Message of the last failure on this context ("" if none). */
+CCOV_API const char* ccov_last_error(const ccov_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCOV_H */

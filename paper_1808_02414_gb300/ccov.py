@@ -1,0 +1,223 @@
+"""Thin ctypes binding of the ccov C ABI (include/ccov.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libccov.so.  Host arrays are numpy arrays; device arrays are CUDA
+torch tensors (their data pointers are passed with CCOV_MEM_DEVICE).  If the
+library has not been built, importing works but the first call raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .synth import OBS_DTYPE
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libccov.so")
+
+CCOV_OK, CCOV_ERR_INVALID_ARG, CCOV_ERR_DEGENERATE, CCOV_ERR_NOT_CONVERGED = 0, 1, 2, 3
+CCOV_ERR_TIMEOUT, CCOV_ERR_OOM, CCOV_ERR_CUDA = 4, 5, 6
+CCOV_PREC_FP64, CCOV_PREC_MIXED = 0, 1
+CCOV_MEM_HOST, CCOV_MEM_DEVICE = 0, 1
+CCOV_NULL_PAPER, CCOV_NULL_CLOSED = 0, 1
+
+EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_nullspace",
+            "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_stats",
+            "ccov_destroy", "ccov_status_string", "ccov_last_error"]
+
+
+class CcovError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ccov status {status}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("mixed_slices", C.c_int), ("nullspace_route", C.c_int),
+                ("input_memory", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("t", C.c_int64), ("N", C.c_int64),
+                ("N_pad", C.c_int64), ("ms_information", C.c_double), ("ms_schur", C.c_double),
+                ("ms_nullspace", C.c_double), ("ms_covariance", C.c_double),
+                ("ms_factor", C.c_double), ("ms_inverse", C.c_double),
+                ("bytes_device", C.c_int64), ("launches", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libccov.so (built in-tree by paper_1808_02414_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1808_02414_gb300.build` (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    P, I64, D, I = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    sig = {
+        "ccov_create": ([P, I64, P, I64, P, I64, D, P, P, P, C.POINTER(C.c_void_p)], I),
+        "ccov_load": ([P, P, P, P, P, I], I),
+        "ccov_information": ([P], I),
+        "ccov_schur": ([P], I),
+        "ccov_nullspace": ([P, P], I),
+        "ccov_covariance": ([P, P, I, P], I),
+        "ccov_get_blocks": ([P, P, P, P], I),
+        "ccov_get_schur": ([P, P, P, P], I),
+        "ccov_get_stats": ([P, C.POINTER(Stats)], I),
+        "ccov_destroy": ([P], None),
+        "ccov_status_string": ([I], C.c_char_p),
+        "ccov_last_error": ([P], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def obs_records(obs_cam, obs_pt, obs_u) -> np.ndarray:
+    rec = np.zeros(len(obs_cam), dtype=OBS_DTYPE)
+    rec["cam"] = obs_cam
+    rec["pt"] = obs_pt
+    rec["u"] = obs_u
+    return rec
+
+
+class Context:
+    """One scene on the device (ccov_ctx).  Method names follow the C ABI."""
+
+    def __init__(self, cameras, points, obs, sigma=1.0, obs_cov=None, precision=CCOV_PREC_FP64,
+                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None):
+        L = load()
+        dev = _is_device(cameras)
+        if not dev:
+            cameras = np.ascontiguousarray(cameras, dtype=np.float64)
+            points = np.ascontiguousarray(points, dtype=np.float64)
+            if obs_cov is not None:
+                obs_cov = np.ascontiguousarray(obs_cov, dtype=np.float64).reshape(-1, 4)
+        n, m = int(cameras.shape[0]), int(points.shape[0])
+        t = int(obs.shape[0]) if not dev else int(obs.numel() // 24)
+        opt = Options(precision, mixed_slices, nullspace_route,
+                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST)
+        h = C.c_void_p()
+        s = L.ccov_create(_ptr(cameras), n, _ptr(points), m, _ptr(obs), t, float(sigma),
+                          _ptr(obs_cov), C.byref(opt), stream, C.byref(h))
+        self._h = h
+        self.n, self.m, self.t = n, m, t
+        self._check(s)
+
+    def _check(self, s: int):
+        if s != CCOV_OK:
+            L = load()
+            msg = L.ccov_last_error(self._h).decode() if self._h else ""
+            raise CcovError(s, msg or L.ccov_status_string(s).decode())
+
+    def ccov_load(self, cameras, points, obs, obs_cov=None):
+        mem = CCOV_MEM_DEVICE if _is_device(cameras) else CCOV_MEM_HOST
+        self._check(load().ccov_load(self._h, _ptr(cameras), _ptr(points), _ptr(obs),
+                                     _ptr(obs_cov), mem))
+
+    def ccov_information(self):
+        self._check(load().ccov_information(self._h))
+
+    def ccov_schur(self):
+        self._check(load().ccov_schur(self._h))
+
+    def ccov_nullspace(self, want_hp=False):
+        hp = np.empty((self.n, 9, 7)) if want_hp else None
+        self._check(load().ccov_nullspace(self._h, _ptr(hp)))
+        return hp
+
+    def ccov_covariance(self, out=None, want_err=False):
+        """Returns (n, 9, 9) blocks on the host, or fills `out` (a CUDA tensor)."""
+        err = np.empty(self.n) if want_err else None
+        if out is None:
+            host = np.empty((self.n, 9, 9))
+            self._check(load().ccov_covariance(self._h, _ptr(host), CCOV_MEM_HOST, _ptr(err)))
+            return (host, err) if want_err else host
+        self._check(load().ccov_covariance(self._h, _ptr(out), CCOV_MEM_DEVICE, _ptr(err)))
+        return (out, err) if want_err else out
+
+    def ccov_get_blocks(self):
+        U = np.empty((self.n, 9, 9))
+        A = np.empty((self.m, 3, 3))
+        W = np.empty((self.t, 9, 3))
+        self._check(load().ccov_get_blocks(self._h, _ptr(U), _ptr(A), _ptr(W)))
+        return U, A, W
+
+    def ccov_get_schur(self, want_z=True):
+        N = 9 * self.n
+        Z = np.empty((N, N)) if want_z else None
+        G = np.empty((N, 7))
+        W7 = np.empty((7, 7))
+        self._check(load().ccov_get_schur(self._h, _ptr(Z), _ptr(G), _ptr(W7)))
+        return Z, G, W7
+
+    def ccov_get_stats(self) -> dict:
+        st = Stats()
+        self._check(load().ccov_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def run(self, out=None):
+        """Steps (a)-(d) in order."""
+        self.ccov_information()
+        self.ccov_schur()
+        self.ccov_nullspace()
+        return self.ccov_covariance(out)
+
+    def close(self):
+        if self._h:
+            load().ccov_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_scene(scene, **kw) -> Context:
+    return Context(scene.cams, scene.pts, scene.obs_records(), scene.sigma,
+                   None if scene.obs_cov is None else scene.obs_cov.reshape(-1, 4), **kw)
+
+
+def camera_covariances(scene, **kw) -> np.ndarray:
+    """Per-camera 9x9 covariance blocks of a scene through the C ABI."""
+    with from_scene(scene, **kw) as ctx:
+        return ctx.run()

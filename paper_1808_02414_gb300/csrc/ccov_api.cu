@@ -1,0 +1,497 @@
+// The C ABI of include/ccov.h: host-side validation, index construction,
+// device memory and the order of the kernel launches of steps (a)-(d).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ccov_internal.cuh"
+
+using ccov::Ctx;
+
+struct ccov_ctx {
+    Ctx c;
+};
+
+namespace {
+
+ccov_status fail(Ctx* c, ccov_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+ccov_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(c, CCOV_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(c, CCOV_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                   \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return cuda_fail(&c, _e, where); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(Ctx& c, T** p, size_t count) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e == cudaSuccess) c.bytes += (int64_t)(count * sizeof(T));
+    return e;
+}
+
+void free_all(Ctx& c) {
+    void* ptrs[] = {c.d_cams, c.d_pts, c.d_obs, c.d_obscov, c.d_pt_ptr, c.d_cam_ptr, c.d_cam_perm,
+                    c.d_camprep, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.d_Gp, c.d_W7, c.d_HP, c.d_R,
+                    c.d_P, c.d_Linv, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    ccov::mixed_free(c);
+    for (auto& e : c.ev)
+        if (e) cudaEventDestroy(e);
+    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+}
+
+bool finite_all(const double* p, int64_t k) {
+    for (int64_t i = 0; i < k; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Host validation of the scene and construction of the two indices:
+// pt_ptr (CSR by point over the point-sorted observations) and the camera
+// grouping cam_ptr / cam_perm (counting sort by camera).
+ccov_status build_index(Ctx& c, const double* cams, const double* pts, const ccov_obs* obs,
+                        const double* cov, std::vector<int>& pt_ptr, std::vector<int>& cam_ptr,
+                        std::vector<int>& cam_perm) {
+    const int64_t n = c.n, m = c.m, t = c.t;
+    if (!finite_all(cams, 9 * n)) return fail(&c, CCOV_ERR_INVALID_ARG, "non-finite camera parameter");
+    if (!finite_all(pts, 3 * m)) return fail(&c, CCOV_ERR_INVALID_ARG, "non-finite point");
+    pt_ptr.assign(m + 1, 0);
+    cam_ptr.assign(n + 1, 0);
+    std::vector<int64_t> stamp(n, -1);
+    int64_t prev = -1;
+    for (int64_t o = 0; o < t; ++o) {
+        const ccov_obs& r = obs[o];
+        if (r.cam < 0 || r.cam >= n || r.pt < 0 || r.pt >= m)
+            return fail(&c, CCOV_ERR_INVALID_ARG, "observation %lld: index out of range", (long long)o);
+        if (r.pt < prev)
+            return fail(&c, CCOV_ERR_INVALID_ARG, "observations must be sorted by point (at %lld)", (long long)o);
+        if (!std::isfinite(r.u[0]) || !std::isfinite(r.u[1]))
+            return fail(&c, CCOV_ERR_INVALID_ARG, "observation %lld: non-finite u", (long long)o);
+        if (stamp[r.cam] == r.pt)
+            return fail(&c, CCOV_ERR_INVALID_ARG, "point %d observed twice by camera %d", r.pt, r.cam);
+        stamp[r.cam] = r.pt;
+        prev = r.pt;
+        pt_ptr[r.pt + 1]++;
+        cam_ptr[r.cam + 1]++;
+        if (cov) {
+            const double* s = cov + 4 * o;
+            if (!finite_all(s, 4) || !(s[0] > 0.0) || !(s[0] * s[3] - s[1] * s[2] > 0.0) ||
+                std::fabs(s[1] - s[2]) > 1e-12 * (std::fabs(s[1]) + std::fabs(s[2]) + 1e-300))
+                return fail(&c, CCOV_ERR_INVALID_ARG, "observation %lld: covariance not SPD", (long long)o);
+        }
+    }
+    for (int64_t j = 0; j < m; ++j) {
+        if (pt_ptr[j + 1] < 2)
+            return fail(&c, CCOV_ERR_DEGENERATE, "point %lld has %d observations (< 2)", (long long)j, pt_ptr[j + 1]);
+        pt_ptr[j + 1] += pt_ptr[j];
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (cam_ptr[i + 1] < 2)
+            return fail(&c, CCOV_ERR_DEGENERATE, "camera %lld has %d observations (< 2)", (long long)i, cam_ptr[i + 1]);
+        cam_ptr[i + 1] += cam_ptr[i];
+    }
+    cam_perm.resize(t);
+    std::vector<int> fill(cam_ptr.begin(), cam_ptr.end() - 1);
+    for (int64_t o = 0; o < t; ++o) cam_perm[fill[obs[o].cam]++] = (int)o;
+    return CCOV_OK;
+}
+
+ccov_status check_device(Ctx& c, const char* where) {
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_fail(&c, e, where);
+    int flag[2] = {0, 0};
+    e = cudaMemcpy(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(&c, e, where);
+    switch (flag[0]) {
+        case ccov::DEV_OK: return CCOV_OK;
+        case ccov::DEV_BEHIND:
+            return fail(&c, CCOV_ERR_DEGENERATE, "%s: point behind camera (observation %d)", where, flag[1]);
+        case ccov::DEV_SINGULAR_A:
+            return fail(&c, CCOV_ERR_DEGENERATE, "%s: point block A_j singular (point %d)", where, flag[1]);
+        case ccov::DEV_NOT_SPD:
+            return fail(&c, CCOV_ERR_DEGENERATE, "%s: reduced camera matrix not positive definite (row %d)", where, flag[1]);
+        case ccov::DEV_SINGULAR_W7:
+            return fail(&c, CCOV_ERR_DEGENERATE, "%s: W7 singular (column %d)", where, flag[1]);
+        case ccov::DEV_SINGULAR_JR:
+            return fail(&c, CCOV_ERR_DEGENERATE, "%s: J_r^T J_r singular (camera %d)", where, flag[1]);
+        case ccov::DEV_TIMEOUT:
+            return fail(&c, CCOV_ERR_TIMEOUT, "%s: device wait gave up (site %d)", where, flag[1]);
+        default:
+            return fail(&c, CCOV_ERR_CUDA, "%s: device error code %d", where, flag[0]);
+    }
+}
+
+float elapsed(Ctx& c, int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.ev[a], c.ev[b]);
+    return ms;
+}
+
+ccov_status upload(Ctx& c, const double* cams, const double* pts, const ccov_obs* obs,
+                   const double* cov, int memory) {
+    cudaMemcpyKind kind = memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(c.d_cams, cams, sizeof(double) * 9 * c.n, kind, c.stream), "copy cameras");
+    CK(cudaMemcpyAsync(c.d_pts, pts, sizeof(double) * 3 * c.m, kind, c.stream), "copy points");
+    CK(cudaMemcpyAsync(c.d_obs, obs, sizeof(ccov_obs) * c.t, kind, c.stream), "copy observations");
+    if (cov) CK(cudaMemcpyAsync(c.d_obscov, cov, sizeof(double) * 4 * c.t, kind, c.stream), "copy obs_cov");
+    return CCOV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ccov_status_string(ccov_status s) {
+    switch (s) {
+        case CCOV_OK: return "ok";
+        case CCOV_ERR_INVALID_ARG: return "invalid argument";
+        case CCOV_ERR_DEGENERATE: return "degenerate input";
+        case CCOV_ERR_NOT_CONVERGED: return "not converged";
+        case CCOV_ERR_TIMEOUT: return "device wait timed out";
+        case CCOV_ERR_OOM: return "out of device memory";
+        case CCOV_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+const char* ccov_last_error(const ccov_ctx* ctx) { return ctx ? ctx->c.err.c_str() : ""; }
+
+ccov_status ccov_create(const double* cameras, int64_t n, const double* points, int64_t m,
+                        const ccov_obs* obs, int64_t t, double sigma, const double* obs_cov,
+                        const ccov_options* opt, void* stream, ccov_ctx** out) {
+    if (!out) return CCOV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cameras || !points || !obs || n < 1 || m < 3 || t < 4 || t >= (int64_t)1 << 31 ||
+        9 * n >= ((int64_t)1 << 31) / 9)
+        return CCOV_ERR_INVALID_ARG;
+    if (!obs_cov && !(sigma > 0.0 && std::isfinite(sigma))) return CCOV_ERR_INVALID_ARG;
+    ccov_ctx* h = new (std::nothrow) ccov_ctx();
+    if (!h) return CCOV_ERR_OOM;
+    Ctx& c = h->c;
+    *out = h;
+    if (opt) c.opt = *opt;
+    if (c.opt.mixed_slices == 0) c.opt.mixed_slices = 6;
+    if (c.opt.precision != CCOV_PREC_FP64 && c.opt.precision != CCOV_PREC_MIXED)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown precision %d", c.opt.precision);
+    if (c.opt.mixed_slices < 4 || c.opt.mixed_slices > 7)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "mixed_slices must be 4..7");
+    if (c.opt.nullspace_route != CCOV_NULL_PAPER && c.opt.nullspace_route != CCOV_NULL_CLOSED)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown nullspace route");
+    c.n = n; c.m = m; c.t = t; c.N = 9 * n;
+    c.Np = (c.N + ccov::kNB - 1) / ccov::kNB * ccov::kNB;
+    c.sigma = sigma;
+    c.has_cov = obs_cov != nullptr;
+    c.stats.n = n; c.stats.m = m; c.stats.t = t; c.stats.N = c.N; c.stats.N_pad = c.Np;
+
+    // host copies for validation when the inputs live on the device
+    const bool dev = c.opt.input_memory == CCOV_MEM_DEVICE;
+    std::vector<double> hc, hp, hcov;
+    std::vector<ccov_obs> ho;
+    const double* vc = cameras; const double* vp = points; const ccov_obs* vo = obs;
+    const double* vcov = obs_cov;
+    if (dev) {
+        hc.resize(9 * n); hp.resize(3 * m); ho.resize(t);
+        if (cudaMemcpy(hc.data(), cameras, 8 * 9 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(hp.data(), points, 8 * 3 * m, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ho.data(), obs, sizeof(ccov_obs) * t, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(&c, CCOV_ERR_INVALID_ARG, "input_memory = device but the inputs are not readable device memory");
+        vc = hc.data(); vp = hp.data(); vo = ho.data();
+        if (obs_cov) {
+            hcov.resize(4 * t);
+            if (cudaMemcpy(hcov.data(), obs_cov, 8 * 4 * t, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(&c, CCOV_ERR_INVALID_ARG, "obs_cov is not readable device memory");
+            vcov = hcov.data();
+        }
+    }
+    std::vector<int> pt_ptr, cam_ptr, cam_perm;
+    ccov_status s = build_index(c, vc, vp, vo, vcov, pt_ptr, cam_ptr, cam_perm);
+    if (s != CCOV_OK) return s;
+
+    if (stream) {
+        c.stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "stream");
+        c.own_stream = true;
+    }
+    for (auto& e : c.ev) CK(cudaEventCreate(&e), "event");
+    CK(ccov::setup_dense64(), "kernel attributes");
+    const int64_t Np = c.Np;
+    CK(dalloc(c, &c.d_cams, 9 * n), "alloc");
+    CK(dalloc(c, &c.d_pts, 3 * m), "alloc");
+    CK(dalloc(c, &c.d_obs, t), "alloc");
+    if (obs_cov) CK(dalloc(c, &c.d_obscov, 4 * t), "alloc");
+    CK(dalloc(c, &c.d_pt_ptr, m + 1), "alloc");
+    CK(dalloc(c, &c.d_cam_ptr, n + 1), "alloc");
+    CK(dalloc(c, &c.d_cam_perm, t), "alloc");
+    CK(dalloc(c, &c.d_camprep, ccov::kCamPrep * n), "alloc");
+    CK(dalloc(c, &c.d_W, 27 * t), "alloc");
+    CK(dalloc(c, &c.d_Ainv, 6 * m), "alloc");
+    CK(dalloc(c, &c.d_U, 45 * n), "alloc");
+    CK(dalloc(c, &c.d_Z, Np * Np), "alloc Z");
+    CK(dalloc(c, &c.d_Gp, 7 * c.N), "alloc");
+    CK(dalloc(c, &c.d_W7, 128), "alloc");
+    CK(dalloc(c, &c.d_HP, 63 * n), "alloc");
+    CK(dalloc(c, &c.d_F, 7 * c.N), "alloc");
+    CK(dalloc(c, &c.d_G, 7 * c.N), "alloc");
+    CK(dalloc(c, &c.d_D, Np), "alloc");
+    CK(dalloc(c, &c.d_Sig, 81 * n), "alloc");
+    CK(dalloc(c, &c.d_small, 256), "alloc");
+    CK(dalloc(c, &c.d_flag, 2), "alloc");
+    CK(dalloc(c, &c.d_Linv, (Np / ccov::kNB) * ccov::kNB * ccov::kNB), "alloc");
+    if (c.opt.precision == CCOV_PREC_FP64) {
+        CK(dalloc(c, &c.d_R, Np * Np), "alloc R");
+        CK(dalloc(c, &c.d_P, Np * ccov::kNB), "alloc");
+    } else {
+        CK(ccov::mixed_alloc(c), "alloc mixed workspace");
+    }
+    c.stats.bytes_device = c.bytes;
+    CK(cudaMemsetAsync(c.d_flag, 0, 2 * sizeof(int), c.stream), "memset");
+    s = upload(c, cameras, points, obs, obs_cov, dev ? CCOV_MEM_DEVICE : CCOV_MEM_HOST);
+    if (s != CCOV_OK) return s;
+    CK(cudaMemcpyAsync(c.d_pt_ptr, pt_ptr.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c.stream), "copy");
+    CK(cudaMemcpyAsync(c.d_cam_ptr, cam_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c.stream), "copy");
+    CK(cudaMemcpyAsync(c.d_cam_perm, cam_perm.data(), sizeof(int) * t, cudaMemcpyHostToDevice, c.stream), "copy");
+    CK(cudaStreamSynchronize(c.stream), "create");
+    c.stage = 1;
+    return CCOV_OK;
+}
+
+ccov_status ccov_load(ccov_ctx* h, const double* cameras, const double* points, const ccov_obs* obs,
+                      const double* obs_cov, int memory) {
+    if (!h || !cameras || !points || !obs) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "context not created");
+    if ((obs_cov != nullptr) != c.has_cov)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "obs_cov presence differs from ccov_create");
+    if (memory == CCOV_MEM_HOST) {
+        // the index set S must be the one the context was built for
+        std::vector<int> pt_ptr, cam_ptr, cam_perm;
+        ccov_status s = build_index(c, cameras, points, obs, obs_cov, pt_ptr, cam_ptr, cam_perm);
+        if (s != CCOV_OK) return s;
+        std::vector<int> dptr(c.m + 1);
+        CK(cudaMemcpy(dptr.data(), c.d_pt_ptr, sizeof(int) * (c.m + 1), cudaMemcpyDeviceToHost), "load");
+        if (dptr != pt_ptr) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_load: index set differs");
+    } else if (memory != CCOV_MEM_DEVICE) {
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
+    }
+    ccov_status s = upload(c, cameras, points, obs, obs_cov, memory);
+    if (s != CCOV_OK) return s;
+    c.stage = 1;
+    c.null_done = false;
+    return CCOV_OK;
+}
+
+ccov_status ccov_information(ccov_ctx* h) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_information: context not created");
+    c.launches = 0;
+    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+    ccov::launch_cam_prep(c);
+    ccov::launch_point_info(c);
+    ccov::launch_cam_info(c);
+    CK(cudaGetLastError(), "ccov_information launch");
+    CK(cudaEventRecord(c.ev[1], c.stream), "event");
+    ccov_status s = check_device(c, "ccov_information");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_information = elapsed(c, 0, 1);
+    c.stage = 2;
+    return CCOV_OK;
+}
+
+ccov_status ccov_schur(ccov_ctx* h) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_schur: call ccov_information first");
+    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+    CK(cudaMemsetAsync(c.d_Z, 0, sizeof(double) * c.Np * c.Np, c.stream), "memset Z");
+    CK(cudaMemsetAsync(c.d_W7, 0, sizeof(double) * 128, c.stream), "memset W7");
+    ccov::launch_schur(c);
+    CK(cudaGetLastError(), "ccov_schur launch");
+    CK(cudaEventRecord(c.ev[1], c.stream), "event");
+    ccov_status s = check_device(c, "ccov_schur");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_schur = elapsed(c, 0, 1);
+    c.stage = 3;
+    return CCOV_OK;
+}
+
+ccov_status ccov_nullspace(ccov_ctx* h, double* H_P_out) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_nullspace: context not created");
+    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+    if (c.stage < 2) ccov::launch_cam_prep(c);
+    ccov::launch_nullspace(c);
+    CK(cudaGetLastError(), "ccov_nullspace launch");
+    CK(cudaEventRecord(c.ev[1], c.stream), "event");
+    ccov_status s = check_device(c, "ccov_nullspace");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_nullspace = elapsed(c, 0, 1);
+    if (H_P_out) CK(cudaMemcpy(H_P_out, c.d_HP, sizeof(double) * 63 * c.n, cudaMemcpyDeviceToHost), "copy H_P");
+    c.null_done = true;
+    return CCOV_OK;
+}
+
+static ccov_status factor_inverse_fp64(Ctx& c) {
+    using ccov::kNB;
+    const int64_t Np = c.Np, nb = Np / kNB;
+    for (int64_t kb = 0; kb < nb; ++kb) {
+        const int64_t k0 = kb * kNB, rem = Np - k0 - kNB;
+        ccov::launch_potrf_diag(c, k0);
+        if (rem > 0) {
+            ccov::launch_copy_panel(c, k0);
+            // L21 = A21 L_kk^-T
+            ccov::launch_gemm64(c, true, false, rem, kNB, kNB, 1.0, c.d_P, kNB,
+                                c.d_Linv + kb * kNB * kNB, kNB, 0.0, c.d_Z + (k0 + kNB) * Np + k0, Np, 0, 0);
+            // A22 -= L21 L21^T (lower tiles)
+            const double* L21 = c.d_Z + (k0 + kNB) * Np + k0;
+            ccov::launch_gemm64(c, true, true, rem, rem, kNB, -1.0, L21, Np, L21, Np, 1.0,
+                                c.d_Z + (k0 + kNB) * Np + k0 + kNB, Np, 0, 0);
+        }
+    }
+    CK(cudaEventRecord(c.ev[3], c.stream), "event");
+    CK(cudaMemsetAsync(c.d_R, 0, sizeof(double) * Np * Np, c.stream), "memset R");
+    ccov::launch_init_identity(c, c.d_R, Np);
+    for (int64_t kb = 0; kb < nb; ++kb) {
+        const int64_t k0 = kb * kNB, rem = Np - k0 - kNB;
+        ccov::launch_trtri_row(c, k0);
+        if (rem > 0) {
+            // R[k+1:, :k+1] -= L[k+1:, k] X[k, :k+1]
+            ccov::launch_gemm64(c, false, false, rem, k0 + kNB, kNB, -1.0, c.d_Z + (k0 + kNB) * Np + k0, Np,
+                                c.d_R + k0 * Np, Np, 1.0, c.d_R + (k0 + kNB) * Np, Np, 0, 0);
+        }
+    }
+    return CCOV_OK;
+}
+
+ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* est_rel_err) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_schur first");
+    if (!c.null_done) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_nullspace first");
+    if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
+    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+    ccov::launch_form_scaled(c);
+    CK(cudaGetLastError(), "ccov_covariance launch");
+    ccov_status s = check_device(c, "ccov_covariance (Z')");
+    if (s != CCOV_OK) return s;
+    CK(cudaEventRecord(c.ev[2], c.stream), "event");
+    CK(cudaMemsetAsync(c.d_Sig, 0, sizeof(double) * 81 * c.n, c.stream), "memset");
+    if (c.opt.precision == CCOV_PREC_FP64) {
+        s = factor_inverse_fp64(c);
+    } else {
+        cudaError_t e = ccov::mixed_factor_inverse(c);
+        if (e != cudaSuccess) return cuda_fail(&c, e, "mixed path");
+    }
+    if (s != CCOV_OK) return s;
+    ccov::launch_extract(c);
+    CK(cudaGetLastError(), "ccov_covariance launch");
+    CK(cudaEventRecord(c.ev[1], c.stream), "event");
+    s = check_device(c, "ccov_covariance");
+    c.stage = 2;  // Z has been consumed in place
+    if (s != CCOV_OK) return s;
+    c.stats.ms_covariance = elapsed(c, 0, 1);
+    c.stats.ms_factor = elapsed(c, 2, 3);
+    c.stats.ms_inverse = elapsed(c, 3, 1);
+    c.stats.launches = c.launches;
+    if (out) {
+        cudaMemcpyKind k = out_memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpy(out, c.d_Sig, sizeof(double) * 81 * c.n, k), "copy out");
+    }
+    if (est_rel_err) {
+        if (c.opt.precision == CCOV_PREC_FP64) {
+            for (int64_t i = 0; i < c.n; ++i) est_rel_err[i] = 0.0;
+        } else {
+            for (int64_t i = 0; i < c.n; ++i) est_rel_err[i] = -1.0;
+        }
+    }
+    return CCOV_OK;
+}
+
+ccov_status ccov_get_blocks(ccov_ctx* h, double* U, double* A_inv, double* W) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_get_blocks: call ccov_information first");
+    if (U) {
+        std::vector<double> u(45 * c.n);
+        CK(cudaMemcpy(u.data(), c.d_U, 8 * u.size(), cudaMemcpyDeviceToHost), "copy U");
+        for (int64_t i = 0; i < c.n; ++i) {
+            int e = 0;
+            for (int p = 0; p < 9; ++p)
+                for (int q = 0; q <= p; ++q, ++e) {
+                    U[81 * i + 9 * p + q] = u[45 * i + e];
+                    U[81 * i + 9 * q + p] = u[45 * i + e];
+                }
+        }
+    }
+    if (A_inv) {
+        std::vector<double> a(6 * c.m);
+        CK(cudaMemcpy(a.data(), c.d_Ainv, 8 * a.size(), cudaMemcpyDeviceToHost), "copy A");
+        for (int64_t j = 0; j < c.m; ++j) {
+            const double* s = &a[6 * j];
+            double full[9] = {s[0], s[1], s[2], s[1], s[3], s[4], s[2], s[4], s[5]};
+            std::memcpy(A_inv + 9 * j, full, sizeof full);
+        }
+    }
+    if (W) CK(cudaMemcpy(W, c.d_W, sizeof(double) * 27 * c.t, cudaMemcpyDeviceToHost), "copy W");
+    return CCOV_OK;
+}
+
+ccov_status ccov_get_schur(ccov_ctx* h, double* Z, double* G, double* W7) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_get_schur: call ccov_schur first");
+    if (Z)
+        CK(cudaMemcpy2D(Z, sizeof(double) * c.N, c.d_Z, sizeof(double) * c.Np, sizeof(double) * c.N, c.N,
+                        cudaMemcpyDeviceToHost), "copy Z");
+    if (G) {
+        std::vector<double> gp(7 * c.N), hp(63 * c.n);
+        CK(cudaMemcpy(gp.data(), c.d_Gp, 8 * gp.size(), cudaMemcpyDeviceToHost), "copy G");
+        if (c.null_done) CK(cudaMemcpy(hp.data(), c.d_HP, 8 * hp.size(), cudaMemcpyDeviceToHost), "copy H_P");
+        for (size_t e = 0; e < gp.size(); ++e) G[e] = gp[e] + (c.null_done ? hp[e] : 0.0);
+    }
+    if (W7) {
+        double w[49];
+        CK(cudaMemcpy(w, c.d_W7, sizeof w, cudaMemcpyDeviceToHost), "copy W7");
+        for (int p = 0; p < 7; ++p)
+            for (int q = 0; q < 7; ++q) W7[7 * p + q] = p <= q ? w[7 * p + q] : w[7 * q + p];
+    }
+    return CCOV_OK;
+}
+
+ccov_status ccov_get_stats(const ccov_ctx* h, ccov_stats* out) {
+    if (!h || !out) return CCOV_ERR_INVALID_ARG;
+    *out = h->c.stats;
+    return CCOV_OK;
+}
+
+void ccov_destroy(ccov_ctx* h) {
+    if (!h) return;
+    if (h->c.stream) cudaStreamSynchronize(h->c.stream);
+    free_all(h->c);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal declarations shared by the ccov translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/ccov.h"
+
+namespace ccov {
+
+constexpr int kNB = 128;         // dense block size: panel width and K of every trailing update
+constexpr int kCamPrep = 24;     // doubles per prepared camera: R(9) t(3) f k1 k2 (3) J_l(9)
+
+// Device-side error codes written with atomicMax into ctx->d_flag[0].
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_BEHIND = 1,       // point behind a camera
+    DEV_SINGULAR_A = 2,   // point block A_j not positive definite
+    DEV_NOT_SPD = 3,      // reduced camera matrix not positive definite
+    DEV_SINGULAR_W7 = 4,
+    DEV_SINGULAR_JR = 5,  // J_r^T J_r of a camera singular (nullspace solve)
+    DEV_TIMEOUT = 6,      // a bounded spin-wait gave up
+};
+
+struct MixedState;  // emulated-FP64 tensor-core path, k_mixed.cu
+
+struct Ctx {
+    int64_t n = 0, m = 0, t = 0, N = 0, Np = 0;
+    ccov_options opt{};
+    double sigma = 1.0;
+    bool has_cov = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int stage = 0;            // 1 created, 2 information, 3 schur; nullspace tracked apart
+    bool null_done = false;
+    std::string err;
+
+    // inputs
+    double* d_cams = nullptr;     // n x 9
+    double* d_pts = nullptr;      // m x 3
+    ccov_obs* d_obs = nullptr;    // t
+    double* d_obscov = nullptr;   // t x 4 or null
+    int* d_pt_ptr = nullptr;      // m + 1
+    int* d_cam_ptr = nullptr;     // n + 1
+    int* d_cam_perm = nullptr;    // t: observation ids grouped by camera
+    // step (a)
+    double* d_camprep = nullptr;  // n x kCamPrep
+    double* d_W = nullptr;        // t x 27
+    double* d_Ainv = nullptr;     // m x 6 (xx xy xz yy yz zz)
+    double* d_U = nullptr;        // n x 45 (lower triangle, row by row)
+    // step (b), (c)
+    double* d_Z = nullptr;        // Np x Np row-major, lower triangle
+    double* d_Gp = nullptr;       // N x 7: -W A^-1 H_X
+    double* d_W7 = nullptr;       // 7 x 7
+    double* d_HP = nullptr;       // n x 63
+    // step (d)
+    double* d_R = nullptr;        // Np x Np: triangular inverse workspace
+    double* d_P = nullptr;        // Np x kNB panel copy
+    double* d_Linv = nullptr;     // (Np / kNB) x kNB x kNB diagonal-block inverses
+    double* d_F = nullptr;        // N x 7: G W7^-1
+    double* d_G = nullptr;        // N x 7
+    double* d_D = nullptr;        // Np Jacobi scale
+    double* d_Sig = nullptr;      // n x 81 scaled, then unscaled blocks
+    double* d_small = nullptr;    // 64: W7^-1 and scratch
+    int* d_flag = nullptr;        // [0] error code, [1] detail
+    int64_t bytes = 0;
+    int64_t launches = 0;
+    MixedState* mixed = nullptr;
+
+    cudaEvent_t ev[8] = {};
+    ccov_stats stats{};
+};
+
+// ---- launchers (k_sparse.cu) ----
+void launch_cam_prep(Ctx& c);
+void launch_point_info(Ctx& c);
+void launch_cam_info(Ctx& c);
+void launch_schur(Ctx& c);
+void launch_nullspace(Ctx& c);
+
+// ---- launchers (k_dense64.cu) ----
+void launch_form_scaled(Ctx& c);           // G, W7^-1, F, D, Z_s = D (Z + F G^T) D
+cudaError_t setup_dense64();               // function attributes (large shared memory)
+void launch_potrf_diag(Ctx& c, int64_t k0);
+void launch_gemm64(Ctx& c, bool nt, bool lower, int64_t M, int64_t N, int64_t K, double alpha,
+                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                   double* C, int64_t ldc, int64_t row0, int64_t col0);
+void launch_copy_panel(Ctx& c, int64_t k0);
+void launch_init_identity(Ctx& c, double* X, int64_t ld);
+void launch_trtri_row(Ctx& c, int64_t k0);
+void launch_extract(Ctx& c);
+
+// ---- mixed path (k_mixed.cu) ----
+cudaError_t mixed_alloc(Ctx& c);
+void mixed_free(Ctx& c);
+cudaError_t mixed_factor_inverse(Ctx& c);
+
+}  // namespace ccov
+
+#define CCOV_LAUNCH_CHECK(c) do { (c).launches++; } while (0)

@@ -1,0 +1,575 @@
+// Steps (a)-(c): reprojection Jacobians and information blocks, Schur
+// elimination of the point blocks into the dense reduced camera matrix, and
+// the camera rows of the similarity nullspace.  All FP64.
+//
+// Sec. 3 (Eq. normal-equation-system) defines M = J^T Sigma_u^-1 J; Sec. 4.2
+// (Eq. block-inversion-Qp, schur-complement-inversion) eliminates the point
+// block A_p; Sec. 4.1 (Eq. transformation-conditions, rotation-nullspace-
+// equation) gives the nullspace H.  Layout: observations sorted by point
+// (CSR by point, pt_ptr) plus a permutation grouping them by camera.
+#include "ccov_internal.cuh"
+
+namespace ccov {
+namespace {
+
+constexpr int kWarps = 4;  // warps per CTA of the warp-per-item kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void set_flag(int* flag, int code, int detail) {
+    if (atomicMax(flag, code) < code) flag[1] = detail;
+}
+
+// R(r), t, f, k1, k2 and the left Jacobian J_l(r) of SO(3):
+// R = I + a [r]x + b [r]x^2, a = sin(th)/th, b = (1 - cos th)/th^2,
+// J_l = I + b [r]x + c [r]x^2, c = (th - sin th)/th^3, so that
+// d(R X)/dr = -[R X]x J_l.
+__global__ void cam_prep_kernel(int64_t n, const double* __restrict__ cams,
+                                double* __restrict__ prep) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* c = cams + 9 * i;
+    double r0 = c[0], r1 = c[1], r2 = c[2];
+    double th2 = r0 * r0 + r1 * r1 + r2 * r2;
+    double th = sqrt(th2);
+    double a, b, cc;
+    if (th < 0.05) {
+        double t4 = th2 * th2;
+        a = 1.0 - th2 / 6.0 + t4 / 120.0 - t4 * th2 / 5040.0;
+        b = 0.5 - th2 / 24.0 + t4 / 720.0 - t4 * th2 / 40320.0;
+        cc = 1.0 / 6.0 - th2 / 120.0 + t4 / 5040.0 - t4 * th2 / 362880.0;
+    } else {
+        double s = sin(th), h = sin(0.5 * th);
+        a = s / th;
+        b = 2.0 * h * h / th2;
+        cc = (th - s) / (th2 * th);
+    }
+    // K = [r]x, K2 = K K
+    double K[9] = {0, -r2, r1, r2, 0, -r0, -r1, r0, 0};
+    double K2[9];
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+            K2[3 * p + q] = K[3 * p] * K[q] + K[3 * p + 1] * K[3 + q] + K[3 * p + 2] * K[6 + q];
+    double* o = prep + kCamPrep * i;
+    for (int e = 0; e < 9; ++e) {
+        double I = (e % 4 == 0) ? 1.0 : 0.0;
+        o[e] = I + a * K[e] + b * K2[e];
+        o[15 + e] = I + b * K[e] + cc * K2[e];
+    }
+    o[9] = c[3]; o[10] = c[4]; o[11] = c[5];
+    o[12] = c[6]; o[13] = c[7]; o[14] = c[8];
+}
+
+// Analytic Jacobians of one observation (Sec. 4.1 projection with the
+// 9-parameter camera).  Jc: 2x9 row-major, Jp: 2x3.  Returns the depth.
+__device__ __forceinline__ double obs_jacobian(const double* __restrict__ cp, double X0, double X1,
+                                               double X2, double* Jc, double* Jp) {
+    const double* R = cp;
+    double RX0 = R[0] * X0 + R[1] * X1 + R[2] * X2;
+    double RX1 = R[3] * X0 + R[4] * X1 + R[5] * X2;
+    double RX2 = R[6] * X0 + R[7] * X1 + R[8] * X2;
+    double p0 = RX0 + cp[9], p1 = RX1 + cp[10], p2 = RX2 + cp[11];
+    double f = cp[12], k1 = cp[13], k2 = cp[14];
+    double s = 1.0 / p2;
+    double x = p0 * s, y = p1 * s;
+    double r2 = x * x + y * y;
+    double g = 1.0 + r2 * (k1 + k2 * r2);
+    double dg = 2.0 * k1 + 4.0 * k2 * r2;
+    // d u / d(x, y) = f (g I + dg [x y]^T [x y])
+    double a00 = f * (g + dg * x * x), a01 = f * dg * x * y, a11 = f * (g + dg * y * y);
+    // D = (d u / d(x,y)) (d(x,y) / d p), d(x,y)/dp = s [1 0 -x; 0 1 -y]
+    double D[6];
+    D[0] = s * a00; D[1] = s * a01; D[2] = -s * (a00 * x + a01 * y);
+    D[3] = s * a01; D[4] = s * a11; D[5] = -s * (a01 * x + a11 * y);
+    // Q = -[RX]x J_l  (d p / d r)
+    const double* Jl = cp + 15;
+    double S[9] = {0, RX2, -RX1, -RX2, 0, RX0, RX1, -RX0, 0};  // -[RX]x
+    double Q[9];
+#pragma unroll
+    for (int pq = 0; pq < 9; ++pq) {
+        int p = pq / 3, q = pq % 3;
+        Q[pq] = S[3 * p] * Jl[q] + S[3 * p + 1] * Jl[3 + q] + S[3 * p + 2] * Jl[6 + q];
+    }
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+        const double* d = D + 3 * row;
+        double* jc = Jc + 9 * row;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            jc[q] = d[0] * Q[q] + d[1] * Q[3 + q] + d[2] * Q[6 + q];
+            jc[3 + q] = d[q];
+            Jp[3 * row + q] = d[0] * R[q] + d[1] * R[3 + q] + d[2] * R[6 + q];
+        }
+    }
+    Jc[6] = g * x;          Jc[15] = g * y;
+    Jc[7] = f * r2 * x;     Jc[16] = f * r2 * y;
+    Jc[8] = f * r2 * r2 * x; Jc[17] = f * r2 * r2 * y;
+    return p2;
+}
+
+// Left-multiply the two Jacobian rows by Sigma_u^-1/2 (C^-1 with Sigma_u = C C^T).
+__device__ __forceinline__ void whiten(double* Jc, double* Jp, double sigma,
+                                       const double* __restrict__ cov) {
+    if (cov == nullptr) {
+        double w = 1.0 / sigma;
+#pragma unroll
+        for (int e = 0; e < 18; ++e) Jc[e] *= w;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) Jp[e] *= w;
+        return;
+    }
+    double c00 = sqrt(cov[0]);
+    double c10 = cov[2] / c00;
+    double c11 = sqrt(cov[3] - c10 * c10);
+    double i00 = 1.0 / c00, i11 = 1.0 / c11, i10 = -c10 * i00 * i11;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        double a = Jc[q], b = Jc[9 + q];
+        Jc[q] = i00 * a;
+        Jc[9 + q] = i10 * a + i11 * b;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double a = Jp[q], b = Jp[3 + q];
+        Jp[q] = i00 * a;
+        Jp[3 + q] = i10 * a + i11 * b;
+    }
+}
+
+// Step (a), point part: warp per point.  A_j = sum Jp^T Jp, its inverse, and
+// W_ij = Jc^T Jp per observation.
+__global__ void __launch_bounds__(32 * kWarps)
+point_info_kernel(int64_t m, const int* __restrict__ pt_ptr, const ccov_obs* __restrict__ obs,
+                  const double* __restrict__ pts, const double* __restrict__ prep, double sigma,
+                  const double* __restrict__ cov, double* __restrict__ W,
+                  double* __restrict__ Ainv, int* flag) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp; j < m; j += nwarp) {
+        int o0 = pt_ptr[j], o1 = pt_ptr[j + 1];
+        double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+        double a[6] = {0, 0, 0, 0, 0, 0};
+        for (int o = o0 + lane; o < o1; o += 32) {
+            int i = obs[o].cam;
+            double Jc[18], Jp[6];
+            double depth = obs_jacobian(prep + (int64_t)kCamPrep * i, X0, X1, X2, Jc, Jp);
+            if (!(depth > 0.0)) set_flag(flag, DEV_BEHIND, o);
+            whiten(Jc, Jp, sigma, cov ? cov + 4 * (int64_t)o : nullptr);
+            a[0] += Jp[0] * Jp[0] + Jp[3] * Jp[3];
+            a[1] += Jp[0] * Jp[1] + Jp[3] * Jp[4];
+            a[2] += Jp[0] * Jp[2] + Jp[3] * Jp[5];
+            a[3] += Jp[1] * Jp[1] + Jp[4] * Jp[4];
+            a[4] += Jp[1] * Jp[2] + Jp[4] * Jp[5];
+            a[5] += Jp[2] * Jp[2] + Jp[5] * Jp[5];
+            double* w = W + 27 * (int64_t)o;
+#pragma unroll
+            for (int p = 0; p < 9; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) w[3 * p + q] = Jc[p] * Jp[q] + Jc[9 + p] * Jp[3 + q];
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) a[e] = warp_sum(a[e]);
+        if (lane == 0) {
+            // inverse of the symmetric 3x3 block by cofactors
+            double c00 = a[3] * a[5] - a[4] * a[4];
+            double c01 = a[2] * a[4] - a[1] * a[5];
+            double c02 = a[1] * a[4] - a[2] * a[3];
+            double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+            double scale = a[0] * a[3] * a[5];
+            if (!(det > 1e-14 * scale) || !(a[0] > 0.0)) set_flag(flag, DEV_SINGULAR_A, (int)j);
+            double id = 1.0 / det;
+            double* ai = Ainv + 6 * j;
+            ai[0] = c00 * id;
+            ai[1] = c01 * id;
+            ai[2] = c02 * id;
+            ai[3] = (a[0] * a[5] - a[2] * a[2]) * id;
+            ai[4] = (a[1] * a[2] - a[0] * a[4]) * id;
+            ai[5] = (a[0] * a[3] - a[1] * a[1]) * id;
+        }
+    }
+}
+
+// Step (a), camera part: warp per camera, U_i = sum Jc^T Jc (lower, 45).
+__global__ void __launch_bounds__(32 * kWarps)
+cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
+                const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
+                const double* __restrict__ prep, double sigma, const double* __restrict__ cov,
+                double* __restrict__ U) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarp) {
+        double u[45];
+#pragma unroll
+        for (int e = 0; e < 45; ++e) u[e] = 0.0;
+        const double* cp = prep + (int64_t)kCamPrep * i;
+        for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
+            int o = cam_perm[k];
+            int j = obs[o].pt;
+            double Jc[18], Jp[6];
+            obs_jacobian(cp, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], Jc, Jp);
+            whiten(Jc, Jp, sigma, cov ? cov + 4 * (int64_t)o : nullptr);
+            int e = 0;
+#pragma unroll
+            for (int p = 0; p < 9; ++p)
+#pragma unroll
+                for (int q = 0; q <= p; ++q, ++e) u[e] += Jc[p] * Jc[q] + Jc[9 + p] * Jc[9 + q];
+        }
+#pragma unroll
+        for (int e = 0; e < 45; ++e) {
+            double v = warp_sum(u[e]);
+            if (lane == 0) U[45 * i + e] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step (b): Z = blockdiag(U) - sum_j sum_{a,b in track j} V_a W_b^T with
+// V_a = W_a A_j^-1; W7 = sum_j H_Xj^T A_j^-1 H_Xj.  Warp per point; a track is
+// cut into chunks of 32 observations and every pair of chunks is handled with
+// V of one chunk and W of the other staged in shared memory.  Each (pair,
+// row, column) item of a 9x9 block is one FP64 atomic add into Z (lower
+// triangle: block row = larger camera index).
+struct SchurSmem {
+    double V[32][27];
+    double Wb[32][27];
+    int camA[32];
+    int camB[32];
+};
+
+__device__ __forceinline__ void hx_row(double X0, double X1, double X2, int k, double* h) {
+    // row k of H_X = [I, -[X]x, X]
+    h[0] = (k == 0); h[1] = (k == 1); h[2] = (k == 2);
+    if (k == 0) { h[3] = 0.0; h[4] = X2; h[5] = -X1; h[6] = X0; }
+    else if (k == 1) { h[3] = -X2; h[4] = 0.0; h[5] = X0; h[6] = X1; }
+    else { h[3] = X1; h[4] = -X0; h[5] = 0.0; h[6] = X2; }
+}
+
+__global__ void __launch_bounds__(32 * kWarps)
+schur_scatter_kernel(int64_t m, const int* __restrict__ pt_ptr, const ccov_obs* __restrict__ obs,
+                     const double* __restrict__ W, const double* __restrict__ Ainv,
+                     const double* __restrict__ pts, double* __restrict__ Z, int64_t ldz,
+                     double* __restrict__ W7) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SchurSmem& sm = reinterpret_cast<SchurSmem*>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // lane e < 28 owns W7 entry (p, q), p <= q, in row-major upper order
+    int w7p = 0, w7q = 0;
+    {
+        int e = lane, p = 0;
+        while (p < 7 && e >= 7 - p) { e -= 7 - p; ++p; }
+        w7p = p; w7q = p + e;
+    }
+    double w7acc = 0.0, hhacc = 0.0;
+    for (int64_t j = warp; j < m; j += nwarp) {
+        const int o0 = pt_ptr[j], L = pt_ptr[j + 1] - o0;
+        const double* ai = Ainv + 6 * j;
+        const double A00 = ai[0], A01 = ai[1], A02 = ai[2], A11 = ai[3], A12 = ai[4], A22 = ai[5];
+        const double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+        if (lane < 28) {
+            double hp[7], hq[7];
+            double v = 0.0;
+            // (H_X^T H_X)_{pq}, for H^T H of the gauge term
+            for (int k = 0; k < 3; ++k) {
+                hx_row(X0, X1, X2, k, hp);
+                hhacc += hp[w7p] * hp[w7q];
+            }
+            // (H_X^T A^-1 H_X)_{pq} = sum_{k,l} H_X[k][p] A^-1[k][l] H_X[l][q]
+            double Am[9] = {A00, A01, A02, A01, A11, A12, A02, A12, A22};
+            for (int k = 0; k < 3; ++k) {
+                hx_row(X0, X1, X2, k, hp);
+                for (int l = 0; l < 3; ++l) {
+                    hx_row(X0, X1, X2, l, hq);
+                    v += hp[w7p] * Am[3 * k + l] * hq[w7q];
+                }
+            }
+            w7acc += v;
+        }
+        const int nch = (L + 31) >> 5;
+        for (int ca = 0; ca < nch; ++ca) {
+            const int La = min(32, L - 32 * ca);
+            __syncwarp();
+            if (lane < La) {
+                int o = o0 + 32 * ca + lane;
+                const double* w = W + 27 * (int64_t)o;
+                sm.camA[lane] = obs[o].cam;
+#pragma unroll
+                for (int p = 0; p < 9; ++p) {
+                    double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
+                    sm.V[lane][3 * p] = w0 * A00 + w1 * A01 + w2 * A02;
+                    sm.V[lane][3 * p + 1] = w0 * A01 + w1 * A11 + w2 * A12;
+                    sm.V[lane][3 * p + 2] = w0 * A02 + w1 * A12 + w2 * A22;
+                }
+            }
+            for (int cb = ca; cb < nch; ++cb) {
+                const int Lb = min(32, L - 32 * cb);
+                __syncwarp();
+                if (lane < Lb) {
+                    int o = o0 + 32 * cb + lane;
+                    const double* w = W + 27 * (int64_t)o;
+                    sm.camB[lane] = obs[o].cam;
+#pragma unroll
+                    for (int e = 0; e < 27; ++e) sm.Wb[lane][e] = w[e];
+                }
+                __syncwarp();
+                const int npairs = (ca == cb) ? La * (La + 1) / 2 : La * Lb;
+                const int nitems = npairs * 81;
+                for (int q = lane; q < nitems; q += 32) {
+                    int p = q / 81, e = q - 81 * p;
+                    int r = e / 9, c = e - 9 * r;
+                    int a, b;
+                    if (ca == cb) {
+                        // pairs a <= b ordered by b: p = b (b + 1) / 2 + a
+                        b = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
+                        while ((b + 1) * (b + 2) / 2 <= p) ++b;
+                        while (b * (b + 1) / 2 > p) --b;
+                        a = p - b * (b + 1) / 2;
+                    } else {
+                        a = p / Lb;
+                        b = p - a * Lb;
+                    }
+                    const int ia = sm.camA[a], ib = sm.camB[b];
+                    const double* Va = sm.V[a];
+                    const double* Wb = sm.Wb[b];
+                    double v;
+                    int64_t row, col;
+                    if (ia > ib) {
+                        v = Va[3 * r] * Wb[3 * c] + Va[3 * r + 1] * Wb[3 * c + 1] + Va[3 * r + 2] * Wb[3 * c + 2];
+                        row = 9 * (int64_t)ia + r; col = 9 * (int64_t)ib + c;
+                    } else if (ia < ib) {
+                        v = Va[3 * c] * Wb[3 * r] + Va[3 * c + 1] * Wb[3 * r + 1] + Va[3 * c + 2] * Wb[3 * r + 2];
+                        row = 9 * (int64_t)ib + r; col = 9 * (int64_t)ia + c;
+                    } else {
+                        if (c > r) continue;  // diagonal block: lower part only
+                        v = Va[3 * r] * Wb[3 * c] + Va[3 * r + 1] * Wb[3 * c + 1] + Va[3 * r + 2] * Wb[3 * c + 2];
+                        row = 9 * (int64_t)ia + r; col = 9 * (int64_t)ia + c;
+                    }
+                    atomicAdd(Z + row * ldz + col, -v);
+                }
+            }
+        }
+    }
+    if (lane < 28) {
+        atomicAdd(W7 + 7 * w7p + w7q, w7acc);
+        atomicAdd(W7 + 49 + 7 * w7p + w7q, hhacc);
+    }
+}
+
+// Step (b), camera part: warp per camera.  G_i = -sum_j V_ij H_Xj (the border
+// column block of Z_p without H_P) and Z_ii += U_i.
+__global__ void __launch_bounds__(32 * kWarps)
+cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
+                 const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
+                 const double* __restrict__ W, const double* __restrict__ Ainv,
+                 const double* __restrict__ U, double* __restrict__ Z, int64_t ldz,
+                 double* __restrict__ Gp) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarp) {
+        // G_i = -[sum V, -sum V [X]x, sum V X]
+        double sV[27], sVX[9], sVK[27];
+#pragma unroll
+        for (int e = 0; e < 27; ++e) { sV[e] = 0.0; sVK[e] = 0.0; }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) sVX[e] = 0.0;
+        for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
+            int o = cam_perm[k];
+            int j = obs[o].pt;
+            const double* ai = Ainv + 6 * (int64_t)j;
+            double Am[9] = {ai[0], ai[1], ai[2], ai[1], ai[3], ai[4], ai[2], ai[4], ai[5]};
+            double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+            const double* w = W + 27 * (int64_t)o;
+#pragma unroll
+            for (int p = 0; p < 9; ++p) {
+                double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
+                double v0 = w0 * Am[0] + w1 * Am[3] + w2 * Am[6];
+                double v1 = w0 * Am[1] + w1 * Am[4] + w2 * Am[7];
+                double v2 = w0 * Am[2] + w1 * Am[5] + w2 * Am[8];
+                sV[3 * p] += v0; sV[3 * p + 1] += v1; sV[3 * p + 2] += v2;
+                sVX[p] += v0 * X0 + v1 * X1 + v2 * X2;
+                // V [X]x, [X]x = [[0,-X2,X1],[X2,0,-X0],[-X1,X0,0]]
+                sVK[3 * p] += v1 * X2 - v2 * X1;
+                sVK[3 * p + 1] += -v0 * X2 + v2 * X0;
+                sVK[3 * p + 2] += v0 * X1 - v1 * X0;
+            }
+        }
+        double* g = Gp + 63 * i;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                double a = warp_sum(sV[3 * p + q]);
+                double b = warp_sum(sVK[3 * p + q]);
+                if (lane == 0) { g[7 * p + q] = -a; g[7 * p + 3 + q] = b; }
+            }
+            double c = warp_sum(sVX[p]);
+            if (lane == 0) g[7 * p + 6] = -c;
+        }
+        for (int e = lane; e < 45; e += 32) {
+            int r = 0, s = e;
+            while (s > r) { s -= r + 1; ++r; }
+            Z[(9 * i + r) * ldz + 9 * i + s] += U[45 * i + e];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step (c): H_P per camera.  Paper route: accumulate J_r^T J_r and J_r^T B over
+// the camera's observations, B = -(J_t H_t + J_X H_X), and solve (3x3 SPD).
+__global__ void __launch_bounds__(32 * kWarps)
+nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
+                 const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
+                 const double* __restrict__ cams, const double* __restrict__ prep, int route,
+                 double* __restrict__ HP, int* flag) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarp) {
+        const double* cp = prep + (int64_t)kCamPrep * i;
+        const double* R = cp;
+        const double t0 = cp[9], t1 = cp[10], t2 = cp[11];
+        double Hr[21];
+        if (route == CCOV_NULL_CLOSED) {
+            // H_r = [0, -J_r^-1(r), 0], J_r^-1 = I + 1/2 K + c K^2
+            const double* rv = cams + 9 * i;
+            double th2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2], th = sqrt(th2);
+            double c = th < 1e-3 ? 1.0 / 12.0 + th2 / 720.0
+                                 : 1.0 / th2 - (1.0 + cos(th)) / (2.0 * th * sin(th));
+            double K[9] = {0, -rv[2], rv[1], rv[2], 0, -rv[0], -rv[1], rv[0], 0};
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) {
+                    double k2 = K[3 * p] * K[q] + K[3 * p + 1] * K[3 + q] + K[3 * p + 2] * K[6 + q];
+                    Hr[7 * p + 3 + q] = -((p == q) + 0.5 * K[3 * p + q] + c * k2);
+                    Hr[7 * p + q] = 0.0;
+                }
+            for (int p = 0; p < 3; ++p) Hr[7 * p + 6] = 0.0;
+        } else {
+            double jj[6] = {0, 0, 0, 0, 0, 0};
+            double jb[21];
+#pragma unroll
+            for (int e = 0; e < 21; ++e) jb[e] = 0.0;
+            for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
+                int o = cam_perm[k];
+                int j = obs[o].pt;
+                double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+                double Jc[18], Jp[6];
+                obs_jacobian(cp, X0, X1, X2, Jc, Jp);
+#pragma unroll
+                for (int row = 0; row < 2; ++row) {
+                    const double* jr = Jc + 9 * row;       // d/dr (3)
+                    const double* jt = Jc + 9 * row + 3;   // d/dt (3)
+                    const double* jx = Jp + 3 * row;
+                    // B row = -(J_t H_t + J_X H_X); H_t = [-R, 0, t], H_X = [I, -[X]x, X]
+                    double b[7];
+                    for (int q = 0; q < 3; ++q)
+                        b[q] = -(-(jt[0] * R[q] + jt[1] * R[3 + q] + jt[2] * R[6 + q]) + jx[q]);
+                    // J_X (-[X]x): columns of -[X]x = [[0,X2,-X1],[-X2,0,X0],[X1,-X0,0]]
+                    b[3] = -(jx[1] * (-X2) + jx[2] * X1);
+                    b[4] = -(jx[0] * X2 + jx[2] * (-X0));
+                    b[5] = -(jx[0] * (-X1) + jx[1] * X0);
+                    b[6] = -(jt[0] * t0 + jt[1] * t1 + jt[2] * t2 + jx[0] * X0 + jx[1] * X1 + jx[2] * X2);
+                    jj[0] += jr[0] * jr[0]; jj[1] += jr[0] * jr[1]; jj[2] += jr[0] * jr[2];
+                    jj[3] += jr[1] * jr[1]; jj[4] += jr[1] * jr[2]; jj[5] += jr[2] * jr[2];
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int q = 0; q < 7; ++q) jb[7 * p + q] += jr[p] * b[q];
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 6; ++e) jj[e] = warp_sum(jj[e]);
+#pragma unroll
+            for (int e = 0; e < 21; ++e) jb[e] = warp_sum(jb[e]);
+            // Cholesky of J_r^T J_r, then two triangular solves per column
+            double l00 = sqrt(jj[0]);
+            double l10 = jj[1] / l00, l20 = jj[2] / l00;
+            double d11 = jj[3] - l10 * l10;
+            double l11 = sqrt(d11);
+            double l21 = (jj[4] - l20 * l10) / l11;
+            double d22 = jj[5] - l20 * l20 - l21 * l21;
+            double l22 = sqrt(d22);
+            if (!(d11 > 0.0) || !(d22 > 0.0)) {
+                if (lane == 0) set_flag(flag, DEV_SINGULAR_JR, (int)i);
+            }
+            for (int q = 0; q < 7; ++q) {
+                double y0 = jb[q] / l00;
+                double y1 = (jb[7 + q] - l10 * y0) / l11;
+                double y2 = (jb[14 + q] - l20 * y0 - l21 * y1) / l22;
+                double x2 = y2 / l22;
+                double x1 = (y1 - l21 * x2) / l11;
+                double x0 = (y0 - l10 * x1 - l20 * x2) / l00;
+                Hr[q] = x0; Hr[7 + q] = x1; Hr[14 + q] = x2;
+            }
+        }
+        if (lane == 0) {
+            double* h = HP + 63 * i;
+            for (int e = 0; e < 21; ++e) h[e] = Hr[e];
+            for (int p = 0; p < 3; ++p) {
+                for (int q = 0; q < 3; ++q) h[21 + 7 * p + q] = -R[3 * p + q];
+                h[21 + 7 * p + 3] = 0.0; h[21 + 7 * p + 4] = 0.0; h[21 + 7 * p + 5] = 0.0;
+            }
+            h[21 + 6] = t0; h[28 + 6] = t1; h[35 + 6] = t2;
+            for (int e = 42; e < 63; ++e) h[e] = 0.0;
+        }
+    }
+}
+
+int grid_for(int64_t items, int per_cta) {
+    int64_t g = (items + per_cta - 1) / per_cta;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void launch_cam_prep(Ctx& c) {
+    cam_prep_kernel<<<(int)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_cams, c.d_camprep);
+    CCOV_LAUNCH_CHECK(c);
+}
+
+void launch_point_info(Ctx& c) {
+    point_info_kernel<<<grid_for(c.m, kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.m, c.d_pt_ptr, c.d_obs, c.d_pts, c.d_camprep, c.sigma, c.d_obscov, c.d_W, c.d_Ainv,
+        c.d_flag);
+    CCOV_LAUNCH_CHECK(c);
+}
+
+void launch_cam_info(Ctx& c) {
+    cam_info_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_camprep, c.sigma, c.d_obscov, c.d_U);
+    CCOV_LAUNCH_CHECK(c);
+}
+
+void launch_schur(Ctx& c) {
+    size_t smem = sizeof(SchurSmem) * kWarps;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(schur_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    schur_scatter_kernel<<<grid_for(c.m, kWarps), 32 * kWarps, smem, c.stream>>>(
+        c.m, c.d_pt_ptr, c.d_obs, c.d_W, c.d_Ainv, c.d_pts, c.d_Z, c.Np, c.d_W7);
+    CCOV_LAUNCH_CHECK(c);
+    cam_schur_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.Np,
+        c.d_Gp);
+    CCOV_LAUNCH_CHECK(c);
+}
+
+void launch_nullspace(Ctx& c) {
+    nullspace_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_cams, c.d_camprep,
+        c.opt.nullspace_route, c.d_HP, c.d_flag);
+    CCOV_LAUNCH_CHECK(c);
+}
+
+}  // namespace ccov

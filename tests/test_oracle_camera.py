@@ -3,7 +3,8 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import brute, camera, nullspace
+pytest.importorskip("mpmath")
+from oracle import brute, camera, nullspace  # noqa: E402
 
 
 def test_projection_closed_form_identity_rotation():

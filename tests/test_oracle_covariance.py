@@ -1,12 +1,12 @@
 """Pins of the oracle's camera covariance (Sec. 3, Sec. 4.2, Sec. 6)."""
-import mpmath as mp
 import numpy as np
 import pytest
 
-from oracle import brute, camera, covariance, information, metrics, nullspace
-from paper_1808_02414_gb300 import synth
+mp = pytest.importorskip("mpmath")
+from oracle import brute, camera, covariance, information, metrics, nullspace  # noqa: E402
+from paper_1808_02414_gb300 import synth  # noqa: E402
 
-from _scenes import golden_entries
+from _scenes import golden_entries  # noqa: E402
 
 
 def _dense_bordered(sc):
