@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of camera covariance propagation on one GB300 (or N replicas).
+
+A step is one pass of the whole path on one scene: ccov_information ->
+ccov_schur -> ccov_nullspace -> ccov_covariance (steps (a)-(d)).  The
+workload is the synthetic 4000-camera shell scene (400k points, track length
+1 + Geometric(1/7), about 3.2M observations, reduced camera matrix
+36000 x 36000).  `value` = cameras / s with the inputs resident on the device;
+`e2e` = the same through the C ABI with host buffers (host-to-device upload and
+the device-to-host copy of the 9x9 blocks inside every timed step).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead, on a bounded sub-scene of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "camera covariances/s (4k-cam scene), mixed vs FP64 GPU at ≤1e-6 rel error"
+UNIT = "camera covariances/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), nominal
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="shell4k")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--cpu-sample-cams", type=int, default=150)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel_tag)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["dram_bytes_per_launch"] if h == rec["source_sha"] else None
+
+
+def dist_init(n_gpus: int):
+    import torch
+    if n_gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", 0))
+    return 0, 1, 0
+
+
+def barrier_max(x: float, world: int):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_sample(scene, k: int):
+    """The oracle as it stands on a k-camera sub-scene (a bounded sample)."""
+    import numpy as np
+
+    from oracle import covariance
+    from paper_1808_02414_gb300 import synth
+
+    sub = synth.subscene(scene, np.arange(min(k, scene.n)))
+    t0 = time.perf_counter()
+    covariance.camera_covariance(sub)
+    dt = time.perf_counter() - t0
+    return sub, dt
+
+
+def run_reference(args):
+    rank, world, local = dist_init(args.gpus)
+    if rank != 0:
+        return
+    from paper_1808_02414_gb300 import synth
+    scene = synth.workload(args.workload)
+    times = []
+    sub = None
+    for i in range(args.warmup + args.steps):
+        sub, dt = cpu_oracle_sample(scene, args.cpu_sample_cams)
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = sub.n / (ms / 1e3)
+    cores = os.cpu_count()
+    sample = (f"{sub.n}-camera sub-scene ({sub.m} points, {sub.t} observations) of the "
+              f"{args.workload} workload, full oracle route (bordered Schur + LU), per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "cameras": scene.n, "points": scene.m,
+                       "observations": scene.t, "sample_cameras": sub.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1808_02414_gb300 import ccov, synth
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene = synth.workload(args.workload)
+    prec = ccov.CCOV_PREC_MIXED if args.precision == "mixed" else ccov.CCOV_PREC_FP64
+    stream = torch.cuda.current_stream(dev)
+
+    # inputs resident in HBM
+    cams = torch.from_numpy(scene.cams).to(dev)
+    pts = torch.from_numpy(scene.pts).to(dev)
+    rec = scene.obs_records()
+    obs = torch.from_numpy(rec.view(np.uint8)).to(dev)
+    out = torch.empty((scene.n, 9, 9), dtype=torch.float64, device=dev)
+    ctx = ccov.Context(cams, pts, obs, scene.sigma, precision=prec, stream=stream.cuda_stream,
+                       profile=True)
+
+    def step():
+        ctx.ccov_information()
+        ctx.ccov_schur()
+        ctx.ccov_nullspace()
+        ctx.ccov_covariance(out=out)
+        return ctx.ccov_get_stats()
+
+    for _ in range(args.warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        stats.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_total = barrier_max(e0.elapsed_time(e1), world)
+    ms_step = ms_total / args.steps
+    value = scene.n * args.steps * world / (ms_total / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned)
+    h_cams = torch.from_numpy(scene.cams).pin_memory()
+    h_pts = torch.from_numpy(scene.pts).pin_memory()
+    h_obs = torch.from_numpy(rec.view(np.uint8)).pin_memory()
+    h_out = torch.empty((scene.n, 9, 9), dtype=torch.float64).pin_memory()
+    ctx_h = ccov.Context(scene.cams, scene.pts, rec, scene.sigma, precision=prec,
+                         stream=stream.cuda_stream)
+    h2d = scene.cams.nbytes + scene.pts.nbytes + rec.nbytes
+    d2h = scene.n * 81 * 8
+    np_cams, np_pts = h_cams.numpy(), h_pts.numpy()
+    np_obs = h_obs.numpy().view(rec.dtype)
+    np_out = h_out.numpy()
+    barrier(world)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        ctx_h.ccov_load(np_cams, np_pts, np_obs)
+        ctx_h.ccov_information()
+        ctx_h.ccov_schur()
+        ctx_h.ccov_nullspace()
+        ccov.load().ccov_covariance(ctx_h._h, np_out.ctypes.data, ccov.CCOV_MEM_HOST, None)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = barrier_max(f0.elapsed_time(f1), world) / args.e2e_steps
+    e2e_value = scene.n * world / (ms_e2e / 1e3)
+    ctx_h.close()
+
+    # roofline of the dominant kernel family: the trailing-update GEMMs of step (d)
+    pk, src = peaks()
+    gemm_ms = statistics.mean(s["ms_gemm"] for s in stats)
+    gemm_flops = statistics.mean(s["gemm_flops"] for s in stats)
+    gemm_launches = int(statistics.mean(s["gemm_launches"] for s in stats))
+    if prec == ccov.CCOV_PREC_FP64:
+        achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
+        peak = FP64_NOMINAL_GFLOPS / 1e3
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for("gemm64"),
+                "kernel": "gemm64_kernel (FP64 trailing updates)", "peak_source": "nominal FP64",
+                "launches_per_step": gemm_launches, "ms_per_step": gemm_ms,
+                "share_of_step": gemm_ms / ms_step}
+        dtype = "f64"
+    else:
+        achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for("ozaki_gemm"),
+                "kernel": "ozaki_gemm (split-bf16 tcgen05 trailing updates)",
+                "peak_source": f"bf16 sustained ({src})", "launches_per_step": gemm_launches,
+                "ms_per_step": gemm_ms, "share_of_step": gemm_ms / ms_step}
+        dtype = "bf16"
+    last = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "cameras": scene.n, "points": scene.m,
+                       "observations": scene.t, "N": 9 * scene.n, "precision": args.precision,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set > L2: the dense reduced matrix alone is "
+                             f"{(9 * scene.n) ** 2 * 8 / 1e9:.1f} GB"},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+            "gpu_launches": int(sum(s["launches"] for s in stats)),
+            "roofline": roof,
+            "phases_ms": {k: last[k] for k in ("ms_information", "ms_schur", "ms_nullspace",
+                                                "ms_covariance", "ms_factor", "ms_inverse")}}
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sub, dt = cpu_oracle_sample(scene, args.cpu_sample_cams)
+        line["cpu_baseline"] = {"value": sub.n / dt, "unit": UNIT, "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"{sub.n}-camera sub-scene ({sub.m} points, {sub.t} "
+                                          f"observations) of {args.workload}, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -80,7 +80,9 @@ typedef struct {
                              CCOV_NULL_CLOSED: -J_r^-1(r) in closed form */
     int input_memory;     /* where ccov_create's / ccov_load's arrays live:
                              CCOV_MEM_HOST (default) or CCOV_MEM_DEVICE */
-    int reserved[8];      /* set to zero */
+    int profile;          /* 1: bracket every dense trailing-update GEMM with CUDA
+                             events and report their time in ccov_stats */
+    int reserved[7];      /* set to zero */
 } ccov_options;
 
 /* Per-context counters of the last calls (device times from CUDA events). */
@@ -90,6 +92,11 @@ typedef struct {
     double ms_factor, ms_inverse;       /* parts of ms_covariance */
     int64_t bytes_device;               /* device workspace held by the context */
     int64_t launches;                   /* kernels launched by the last four calls */
+    double ms_gemm;                     /* profile = 1: summed device time of the
+                                           trailing-update GEMMs of the last ccov_covariance */
+    double gemm_flops;                  /* their algorithmic flops (lower-triangle
+                                           updates counted once) */
+    int64_t gemm_launches;
 } ccov_stats;
 
 /* Create a context for one scene and copy its inputs to the device.

@@ -37,7 +37,7 @@ class CcovError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("mixed_slices", C.c_int), ("nullspace_route", C.c_int),
-                ("input_memory", C.c_int), ("reserved", C.c_int * 8)]
+                ("input_memory", C.c_int), ("profile", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class Stats(C.Structure):
@@ -45,7 +45,8 @@ class Stats(C.Structure):
                 ("N_pad", C.c_int64), ("ms_information", C.c_double), ("ms_schur", C.c_double),
                 ("ms_nullspace", C.c_double), ("ms_covariance", C.c_double),
                 ("ms_factor", C.c_double), ("ms_inverse", C.c_double),
-                ("bytes_device", C.c_int64), ("launches", C.c_int64)]
+                ("bytes_device", C.c_int64), ("launches", C.c_int64), ("ms_gemm", C.c_double),
+                ("gemm_flops", C.c_double), ("gemm_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,7 +117,7 @@ class Context:
     """One scene on the device (ccov_ctx).  Method names follow the C ABI."""
 
     def __init__(self, cameras, points, obs, sigma=1.0, obs_cov=None, precision=CCOV_PREC_FP64,
-                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None):
+                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None, profile=False):
         L = load()
         dev = _is_device(cameras)
         if not dev:
@@ -127,7 +128,7 @@ class Context:
         n, m = int(cameras.shape[0]), int(points.shape[0])
         t = int(obs.shape[0]) if not dev else int(obs.numel() // 24)
         opt = Options(precision, mixed_slices, nullspace_route,
-                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST)
+                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST, 1 if profile else 0)
         h = C.c_void_p()
         s = L.ccov_create(_ptr(cameras), n, _ptr(points), m, _ptr(obs), t, float(sigma),
                           _ptr(obs_cov), C.byref(opt), stream, C.byref(h))

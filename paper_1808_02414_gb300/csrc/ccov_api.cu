@@ -57,6 +57,8 @@ void free_all(Ctx& c) {
     ccov::mixed_free(c);
     for (auto& e : c.ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : c.prof_ev)
+        if (e) cudaEventDestroy(e);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
 }
 
@@ -158,6 +160,24 @@ ccov_status upload(Ctx& c, const double* cams, const double* pts, const ccov_obs
 }
 
 }  // namespace
+
+namespace ccov {
+void prof_begin(Ctx& c) {
+    if (!c.opt.profile) return;
+    while (c.prof_ev.size() < c.prof_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c.prof_ev.push_back(e);
+    }
+    cudaEventRecord(c.prof_ev[c.prof_used], c.stream);
+}
+void prof_end(Ctx& c, double flops) {
+    if (!c.opt.profile || c.prof_ev.size() < c.prof_used + 2) return;
+    cudaEventRecord(c.prof_ev[c.prof_used + 1], c.stream);
+    c.prof_used += 2;
+    c.prof_flops += flops;
+}
+}  // namespace ccov
 
 extern "C" {
 
@@ -362,12 +382,16 @@ static ccov_status factor_inverse_fp64(Ctx& c) {
         if (rem > 0) {
             ccov::launch_copy_panel(c, k0);
             // L21 = A21 L_kk^-T
+            ccov::prof_begin(c);
             ccov::launch_gemm64(c, true, false, rem, kNB, kNB, 1.0, c.d_P, kNB,
                                 c.d_Linv + kb * kNB * kNB, kNB, 0.0, c.d_Z + (k0 + kNB) * Np + k0, Np, 0, 0);
+            ccov::prof_end(c, 2.0 * rem * kNB * kNB);
             // A22 -= L21 L21^T (lower tiles)
             const double* L21 = c.d_Z + (k0 + kNB) * Np + k0;
+            ccov::prof_begin(c);
             ccov::launch_gemm64(c, true, true, rem, rem, kNB, -1.0, L21, Np, L21, Np, 1.0,
                                 c.d_Z + (k0 + kNB) * Np + k0 + kNB, Np, 0, 0);
+            ccov::prof_end(c, (double)rem * (rem + 1) * kNB);
         }
     }
     CK(cudaEventRecord(c.ev[3], c.stream), "event");
@@ -378,8 +402,10 @@ static ccov_status factor_inverse_fp64(Ctx& c) {
         ccov::launch_trtri_row(c, k0);
         if (rem > 0) {
             // R[k+1:, :k+1] -= L[k+1:, k] X[k, :k+1]
+            ccov::prof_begin(c);
             ccov::launch_gemm64(c, false, false, rem, k0 + kNB, kNB, -1.0, c.d_Z + (k0 + kNB) * Np + k0, Np,
                                 c.d_R + k0 * Np, Np, 1.0, c.d_R + (k0 + kNB) * Np, Np, 0, 0);
+            ccov::prof_end(c, 2.0 * rem * (k0 + kNB) * kNB);
         }
     }
     return CCOV_OK;
@@ -399,6 +425,8 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     if (s != CCOV_OK) return s;
     CK(cudaEventRecord(c.ev[2], c.stream), "event");
     CK(cudaMemsetAsync(c.d_Sig, 0, sizeof(double) * 81 * c.n, c.stream), "memset");
+    c.prof_used = 0;
+    c.prof_flops = 0.0;
     if (c.opt.precision == CCOV_PREC_FP64) {
         s = factor_inverse_fp64(c);
     } else {
@@ -416,6 +444,17 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     c.stats.ms_factor = elapsed(c, 2, 3);
     c.stats.ms_inverse = elapsed(c, 3, 1);
     c.stats.launches = c.launches;
+    if (c.opt.profile) {
+        double ms = 0.0;
+        for (size_t k = 0; k + 1 < c.prof_used; k += 2) {
+            float e = 0.f;
+            cudaEventElapsedTime(&e, c.prof_ev[k], c.prof_ev[k + 1]);
+            ms += e;
+        }
+        c.stats.ms_gemm = ms;
+        c.stats.gemm_flops = c.prof_flops;
+        c.stats.gemm_launches = (int64_t)(c.prof_used / 2);
+    }
     if (out) {
         cudaMemcpyKind k = out_memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         CK(cudaMemcpy(out, c.d_Sig, sizeof(double) * 81 * c.n, k), "copy out");

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/ccov.h"
 
@@ -70,7 +71,15 @@ struct Ctx {
 
     cudaEvent_t ev[8] = {};
     ccov_stats stats{};
+    // profile = 1: event pairs around the dense trailing-update GEMMs
+    std::vector<cudaEvent_t> prof_ev;
+    size_t prof_used = 0;
+    double prof_flops = 0.0;
 };
+
+// Bracket one GEMM launch with events when profiling (see ccov_options.profile).
+void prof_begin(Ctx& c);
+void prof_end(Ctx& c, double flops);
 
 // ---- launchers (k_sparse.cu) ----
 void launch_cam_prep(Ctx& c);
