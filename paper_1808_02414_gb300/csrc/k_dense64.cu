@@ -371,10 +371,14 @@ void launch_form_scaled(Ctx& c) {
     gauge_kernel<<<1, 256, 0, c.stream>>>(c.N, c.d_G, c.d_HP, c.d_Z, c.Np, c.d_W7, c.d_small, c.d_flag);
     fd_kernel<<<(int)((c.Np + 255) / 256), 256, 0, c.stream>>>(c.N, c.Np, c.d_small, c.d_Z, c.d_G, c.d_F,
                                                                 c.d_D, c.d_flag);
-    int64_t nt = (c.Np + 31) / 32;
-    zscale_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(32, 32), 0, c.stream>>>(c.N, c.Np, c.d_Z,
-                                                                                  c.d_F, c.d_G, c.d_D);
-    c.launches += 4;
+    c.launches += 3;
+    if (c.opt.precision == CCOV_PREC_FP64) {
+        // the mixed path writes Z_s as fixed point itself
+        int64_t nt = (c.Np + 31) / 32;
+        zscale_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(32, 32), 0, c.stream>>>(c.N, c.Np, c.d_Z,
+                                                                                      c.d_F, c.d_G, c.d_D);
+        c.launches++;
+    }
 }
 
 void launch_potrf_diag(Ctx& c, int64_t k0) {

@@ -1,0 +1,106 @@
+"""The tensor-core (digit-split, emulated FP64) path of step (d).
+
+The GEMM kernel is checked bit-exactly against the integer definition of
+its output; the full mixed path against the oracle at the 1e-6 relative
+Frobenius bar per camera block, and against the FP64 GPU path."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import covariance, metrics
+from paper_1808_02414_gb300 import ccov, synth
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+
+
+def _bf16_bits(d):
+    f = d.astype(np.float32)
+    return (f.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def _expected(dA, eA, dB, eB, s, Fc, sub, lower, C0):
+    M, N = dA.shape[1], dB.shape[1]
+    S = np.zeros((M, N), dtype=np.int64)
+    for g in range(s):
+        P = np.zeros((M, N), dtype=np.int64)
+        for a in range(g + 1):
+            P += dA[a] @ dB[g - a].T
+        sh = eA[:, None] + eB[None, :] + Fc - 14 - 8 * g
+        pos = sh >= 0
+        with np.errstate(over="ignore"):
+            left = P << np.where(pos, sh, 0)
+            rs = np.where(pos, 0, -sh)
+            right = (P + (np.int64(1) << np.maximum(rs - 1, 0))) >> rs
+            S += np.where(pos, left, np.where(rs > 0, right, P))
+    out = C0 - S if sub else S
+    if lower:
+        ti = np.arange(M)[:, None] // 128
+        tj = np.arange(N)[None, :] // 64
+        keep = tj * 64 <= ti * 128 + 127
+        out = np.where(keep, out, C0)
+    return out
+
+
+def _run(s, M, N, Fc, sub, lower, seed, with_exp=True):
+    rng = np.random.default_rng(seed)
+    dA = rng.integers(-128, 129, size=(s, M, 128)).astype(np.int64)
+    dB = rng.integers(-128, 129, size=(s, N, 128)).astype(np.int64)
+    eA = rng.integers(-3, 4, size=M).astype(np.int32) if with_exp else np.zeros(M, np.int32)
+    eB = rng.integers(-3, 4, size=N).astype(np.int32) if with_exp else np.zeros(N, np.int32)
+    C0 = rng.integers(-(1 << 50), 1 << 50, size=(M, N)).astype(np.int64)
+    Cg = C0.copy()
+    L = ccov.load()
+    fn = L.ccov_test_ozaki_gemm
+    fn.restype = C.c_int
+    ba, bb = _bf16_bits(dA), _bf16_bits(dB)
+    st = fn(s, M, N, ba.ctypes.data, eA.ctypes.data if with_exp else None, bb.ctypes.data,
+            eB.ctypes.data if with_exp else None, Fc, sub, lower, Cg.ctypes.data)
+    assert st == 0
+    want = _expected(dA, eA.astype(np.int64), dB, eB.astype(np.int64), s, Fc, sub, lower, C0)
+    return Cg, want
+
+
+@pytest.mark.parametrize("s", [4, 5, 6, 7])
+def test_ozaki_gemm_single_tile_bit_exact(s):
+    got, want = _run(s, 128, 64, 60, 1, 0, seed=s, with_exp=False)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("sub,Fc", [(1, 60), (0, 42)])
+def test_ozaki_gemm_with_exponents_bit_exact(sub, Fc):
+    got, want = _run(5, 256, 192, Fc, sub, 0, seed=11 + sub)
+    assert np.array_equal(got, want)
+
+
+def test_ozaki_gemm_many_tiles_persistent_bit_exact():
+    # 16 x 20 = 320 tiles: every CTA runs several tiles through the smem ring
+    got, want = _run(5, 2048, 1280, 60, 1, 0, seed=5, with_exp=False)
+    assert np.array_equal(got, want)
+
+
+def test_ozaki_gemm_lower_tiles_bit_exact():
+    got, want = _run(6, 640, 640, 60, 1, 1, seed=7, with_exp=False)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("case", ["ring20", "shell100", "shell300"])
+def test_mixed_covariance_vs_oracle(case):
+    if case == "ring20":
+        sc = synth.workload("ring20")
+    elif case == "shell100":
+        sc = synth.shell_scene(n=100, m=10000, seed=5)
+    else:
+        sc = synth.shell_scene(n=300, m=30000, seed=6)
+    want = covariance.camera_covariance(sc)
+    got = ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED)
+    assert metrics.rel_fro(got, want).max() < MIXED_TOL
+
+
+def test_mixed_six_digits_tighter():
+    sc = synth.shell_scene(n=100, m=10000, seed=5)
+    want = ccov.camera_covariances(sc)
+    got = ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED, mixed_slices=6)
+    assert metrics.rel_fro(got, want).max() < 1e-8
