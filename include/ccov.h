@@ -74,7 +74,7 @@ enum { CCOV_NULL_PAPER = 0, CCOV_NULL_CLOSED = 1 };
 
 typedef struct {
     int precision;        /* CCOV_PREC_FP64 (default) or CCOV_PREC_MIXED */
-    int mixed_slices;     /* MIXED only: 8-bit digit slices per operand, 4..7; 0 = 6 */
+    int mixed_slices;     /* MIXED only: 8-bit digit slices per operand, 4..6; 0 = 5 */
     int nullspace_route;  /* CCOV_NULL_PAPER: rotation rows from J_r H_r = B (Sec. 4.1,
                              Eq. rotation-nullspace-equation), default;
                              CCOV_NULL_CLOSED: -J_r^-1(r) in closed form */

@@ -12,9 +12,10 @@ extern "C" {
 
 /* One call of the digit-split tensor-core GEMM used by the mixed path of step
  * (d) (the trailing updates of the blocked factorisation and inverse).
- *   digA  host, s planes of M x 128 bf16 bit patterns (plane-major), integer
+ *   s     digit planes, 4..6;  K  digits per row, 128 or 256
+ *   digA  host, s planes of M x K bf16 bit patterns (plane-major), integer
  *         digits in [-128, 128]; row i of A = 2^expA[i] sum_a d_a 2^-(7+8a)
- *   digB  host, s planes of N x 128, the same for the rows of B
+ *   digB  host, s planes of N x K, the same for the rows of B
  *   expA, expB  host int arrays (M, N) or NULL for all zero
  *   C     host int64 M x N row-major fixed point Q(Fc), updated in place:
  *         sub = 1: C -= A B^T, sub = 0: C = A B^T; products of digit orders
@@ -22,7 +23,7 @@ extern "C" {
  *   lower 1: only tiles of 128 x 64 that reach the diagonal (M == N)
  * M must be a multiple of 128 and N of 64.  Returns TIMEOUT if a bounded
  * device wait gave up. */
-CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int M, int N, const uint16_t* digA, const int* expA,
+CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N, const uint16_t* digA, const int* expA,
                                           const uint16_t* digB, const int* expB, int Fc, int sub, int lower,
                                           long long* C);
 

@@ -78,6 +78,7 @@ def load() -> C.CDLL:
         "ccov_destroy": ([P], None),
         "ccov_status_string": ([I], C.c_char_p),
         "ccov_last_error": ([P], C.c_char_p),
+        "ccov_test_ozaki_gemm": ([I, I, I, I, P, P, P, P, I, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

@@ -210,11 +210,11 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     Ctx& c = h->c;
     *out = h;
     if (opt) c.opt = *opt;
-    if (c.opt.mixed_slices == 0) c.opt.mixed_slices = 6;
+    if (c.opt.mixed_slices == 0) c.opt.mixed_slices = 5;
     if (c.opt.precision != CCOV_PREC_FP64 && c.opt.precision != CCOV_PREC_MIXED)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown precision %d", c.opt.precision);
-    if (c.opt.mixed_slices < 4 || c.opt.mixed_slices > 7)
-        return fail(&c, CCOV_ERR_INVALID_ARG, "mixed_slices must be 4..7");
+    if (c.opt.mixed_slices < 4 || c.opt.mixed_slices > 6)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "mixed_slices must be 4..6");
     if (c.opt.nullspace_route != CCOV_NULL_PAPER && c.opt.nullspace_route != CCOV_NULL_CLOSED)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown nullspace route");
     c.n = n; c.m = m; c.t = t; c.N = 9 * n;

@@ -1,21 +1,24 @@
 // Mixed-precision step (d): the Cholesky factorisation and triangular inverse
 // of the Jacobi-scaled reduced camera matrix with every O(N^3) trailing
 // update on the 5th-generation tensor cores (tcgen05, bf16 operands, fp32
-// accumulation in TMEM, operands staged by TMA).
+// accumulation in TMEM, operands and result tiles moved by TMA).
 //
 // Accuracy is kept by an error-free split of the operands into 8-bit digits
 // (after Ozaki et al., "Error-free transformations of matrix multiplication
 // by using fast routines of matrix multiplication and its applications",
 // 2012): a row with exponent e holds v = 2^e sum_a d_a 2^-(7 + 8(a-1)),
 // d_a integers in [-128, 128] that bf16 represents exactly.  A product of two
-// digits has at most 14 bits, a sum of K = 128 of them at most 21, and the
-// products of one digit order g = a + b (at most s of them) stay below 2^24,
-// so each order accumulates exactly in one fp32 TMEM accumulator.  Orders
-// above s - 1 are dropped (relative truncation ~2^-(8 s)).  The working
-// matrices are held in int64 fixed point (Q60 for the factor, whose entries
-// are bounded by 1 after Jacobi scaling; Q42 for the inverse), where every
-// exact partial product is added by integer shifts: no FP64 arithmetic in the
-// O(N^3) part at all.  The residual rounding is that of the digit split.
+// digits has at most 14 bits and a sum of K of them at most 14 + log2 K, so
+// 1024 / K digit products of one order g = a + b sum exactly in one fp32
+// TMEM accumulator (below 2^24); an order with more products gets a second
+// accumulator.  Orders above s - 1 are dropped (relative truncation about
+// 2^-(8 s)).  The working matrices are held in int64 fixed point (Q60 for
+// the factor, whose entries are bounded by 1 after Jacobi scaling; Q42 for
+// the inverse), where the exact partial products are added by integer
+// shifts: no FP64 arithmetic in the O(N^3) part.
+//
+// Blocking: 128-column sub-panels factored and inverted one at a time, with
+// the big trailing updates applied for two sub-panels at once (K = 256).
 //
 // Paper counterpart: the dense inversion of Z_p (Sec. 4.2); the paper runs it
 // in double precision with LAPACK on a CPU.
@@ -28,22 +31,28 @@
 
 namespace ccov {
 
-constexpr int kBM = 128, kBN = 64, kBK = 32, kChunks = kNB / kBK;  // K = 128 per update
-constexpr int kAPlane = kBM * kBK * 2;                              // 8 KB per digit plane
-constexpr int kBPlane = kBN * kBK * 2;                              // 4 KB
-constexpr int kFX = 42;                                             // fixed point of X = L^-1
-constexpr int kFL = 60;                                             // fixed point of Z_s and L
-constexpr unsigned long long kWaitNs = 1000000000ull;               // 1 s per barrier wait
+constexpr int kBM = 128, kBN = 64, kKS = 16;              // tile M x N, K per pipeline stage
+constexpr int kAPl = kBM * kKS * 2;                        // 4 KB: one digit plane of A per stage
+constexpr int kBPl = kBN * kKS * 2;                        // 2 KB
+constexpr int kCBox = kBM * 16 * 8;                        // 16 KB: 16 int64 columns x 128 rows
+constexpr int kCTile = 4 * kCBox;                          // 64 KB result tile staged for TMA
+constexpr int kFX = 42;                                    // fixed point of X = L^-1
+constexpr int kFL = 60;                                    // fixed point of Z_s and L
+constexpr int kKMax = 256;
+constexpr unsigned long long kWaitNs = 1000000000ull;      // 1 s per barrier wait
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;              // producer, MMA, epilogue warps
 
 struct MixedState {
     int s = 5;
-    int stages = 3;
-    __nv_bfloat16* digP = nullptr;   // [s][Np][128] first-operand digits
-    __nv_bfloat16* digQ = nullptr;   // [s][Np][128] second-operand digits
+    __nv_bfloat16* digP = nullptr;   // [s][Np][K] digit planes, row stride K (128 or 256)
+    __nv_bfloat16* digQ = nullptr;
     int* expP = nullptr;             // Np
     int* expQ = nullptr;             // Np
     long long* R = nullptr;          // Np x Np, Q42
-    CUtensorMap mapP128, mapP64, mapQ128, mapQ64;
+    // [buffer P/Q][K 128/256][box rows 128/64]
+    CUtensorMap dig[2][2][2];
+    CUtensorMap mapZ, mapR;          // int64 result maps
     int64_t tiles_done = 0;
 };
 
@@ -86,7 +95,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after kWaitNs, records DEV_TIMEOUT with the site.
+// Bounded wait: gives up after kWaitNs and records DEV_TIMEOUT with the site.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag, int site) {
     if (mbar_try(bar, parity)) return true;
     unsigned long long t0 = globaltimer();
@@ -106,15 +115,27 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// K-major operand tile in shared memory written by TMA with 64-byte swizzle:
-// rows of 64 bytes (32 bf16 along K), 8-row atoms of 512 bytes.
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];"
+                 ::"l"(map), "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
+
+// K-major operand tile written by TMA with 32-byte swizzle: one 32-byte row
+// (16 bf16 along K) per M/N row, 8-row atoms of 256 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
     d |= (uint64_t)1 << 16;                    // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: next 8-row atom
+    d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset: next 8-row atom
     d |= (uint64_t)1 << 46;                    // descriptor version
-    d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+    d |= (uint64_t)6 << 61;                    // 32-byte swizzle
     return d;
 }
 
@@ -135,23 +156,44 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Accumulator slots of the digit orders: order g has g + 1 digit products;
+// at most 1024 / K of them share one fp32 accumulator exactly.
+template <int S, int K>
+struct Slots {
+    static constexpr int cap = 1024 / K;
+    static constexpr int count(int g) { return (g + 1 + cap - 1) / cap; }
+    static constexpr int first(int g) {
+        int f = 0;
+        for (int x = 0; x < g; ++x) f += count(x);
+        return f;
+    }
+    static constexpr int total = first(S);
+    static_assert(total * kBN <= 512, "TMEM columns");
+};
+
 // Tile schedule: M tiles of 128 rows x N tiles of 64 columns; `lower` keeps
 // only tiles that reach the diagonal of a square region (tj*64 <= ti*128+127).
+__host__ __device__ __forceinline__ int64_t tile_count(int tiles_m, int tiles_n, int lower) {
+    if (!lower) return (int64_t)tiles_m * tiles_n;
+    int T0 = tiles_n / 2;
+    return tiles_m <= T0 ? (int64_t)tiles_m * tiles_m + tiles_m
+                         : (int64_t)T0 * T0 + T0 + (int64_t)(tiles_m - T0) * tiles_n;
+}
+
 __device__ __forceinline__ void tile_coords(int64_t t, int tiles_n, int lower, int& ti, int& tj) {
     if (!lower) {
         ti = (int)(t / tiles_n);
@@ -176,50 +218,51 @@ __device__ __forceinline__ void tile_coords(int64_t t, int tiles_n, int lower, i
 
 struct GemmArgs {
     int M, N;             // rows of A and of B (multiples of 128 and 64)
-    int s;                // digit planes
-    int plane_rows;       // rows per digit plane in the buffers (Np)
+    int plane_rows;       // rows per digit plane in the operand buffers (Np)
     int a_row0, b_row0;   // first row of the operands inside their planes
+    int c_x0, c_y0;       // origin of C in its map (column, row)
     int lower;            // keep only tiles touching the lower triangle
     int sub;              // 1: C -= A B^T, 0: C = A B^T
     int shift0;           // F_C - 14
     const int* expA;      // per row of A (nullptr = 0)
     const int* expB;      // per row of B (nullptr = 0)
-    long long* C;         // int64 fixed point
-    int64_t ldc;
     int stages;
     int* flag;
 };
 
-// Persistent warp-specialised kernel.  Warp 0 lane 0: TMA producer.  Warp 1:
-// TMEM allocation, lane 0 issues tcgen05.mma.  Warps 2-5: epilogue (warp w
-// reads TMEM lanes 32 (w % 4) .. +31).  s accumulators of 128 x 64 fp32.
-template <int S>
-__global__ void __launch_bounds__(192, 1)
+__device__ __forceinline__ long long shift_round(long long p, int sh) {
+    if (sh >= 0) return (long long)((unsigned long long)p << (sh > 62 ? 62 : sh));
+    if (sh <= -62) return 0;
+    return (p + (1ll << (-sh - 1))) >> (-sh);
+}
+
+// Persistent warp-specialised kernel.  Warp 0 lane 0: TMA producer of the
+// digit tiles.  Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps
+// 2..9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one half of
+// the 64 columns, and the result tile goes through shared memory with TMA
+// (load of C overlapped with the MMAs of the same tile, store asynchronous).
+template <int S, int K>
+__global__ void __launch_bounds__(kThreads, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                  GemmArgs g) {
+                  const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
+    using SL = Slots<S, K>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned tile area
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int stage_bytes = S * (kAPlane + kBPlane);
-    unsigned char* tiles = base;
-    uint64_t* bars = (uint64_t*)(base + g.stages * stage_bytes);
-    uint64_t* full = bars;                 // [stages]
-    uint64_t* empty = bars + g.stages;     // [stages]
+    constexpr int stage_bytes = S * (kAPl + kBPl);
+    unsigned char* ctile = base;
+    unsigned char* tiles = base + kCTile;
+    uint64_t* bars = (uint64_t*)(tiles + g.stages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + g.stages;
     uint64_t* accf = bars + 2 * g.stages;
     uint64_t* acce = accf + 1;
     uint64_t* drain = acce + 1;
-    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    uint64_t* cfull = drain + 1;
+    uint32_t* tmem_slot = (uint32_t*)(cfull + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_m = g.M / kBM, tiles_n = g.N / kBN;
-    int64_t ntiles;
-    if (g.lower) {
-        int T0 = tiles_n / 2;
-        int64_t tri = (int64_t)T0 * T0 + T0;
-        ntiles = tiles_m <= T0 ? (int64_t)tiles_m * tiles_m + tiles_m : tri + (int64_t)(tiles_m - T0) * tiles_n;
-    } else {
-        ntiles = (int64_t)tiles_m * tiles_n;
-    }
+    const int tiles_n = g.N / kBN;
+    const int64_t ntiles = tile_count(g.M / kBM, tiles_n, g.lower);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < g.stages; ++i) {
@@ -227,8 +270,9 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             mbar_init(empty + i, 1);
         }
         mbar_init(accf, 1);
-        mbar_init(acce, 128);
+        mbar_init(acce, 32 * kEpiWarps);
         mbar_init(drain, 1);
+        mbar_init(cfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -246,55 +290,50 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            const uint32_t tx = (uint32_t)stage_bytes;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 int ti, tj;
                 tile_coords(t, tiles_n, g.lower, ti, tj);
-                for (int c = 0; c < kChunks && ok; ++c) {
+                for (int ks = 0; ks < K / kKS; ++ks) {
                     if (!mbar_wait(empty + stage, phase ^ 1, g.flag, 1)) { ok = false; break; }
                     unsigned char* st = tiles + stage * stage_bytes;
-                    mbar_expect_tx(full + stage, tx);
+                    mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
+#pragma unroll
                     for (int p = 0; p < S; ++p) {
-                        tma_load_2d(st + p * kAPlane, &mapA, full + stage, c * kBK,
+                        tma_load_2d(st + p * kAPl, &mapA, full + stage, ks * kKS,
                                     p * g.plane_rows + g.a_row0 + ti * kBM);
-                        tma_load_2d(st + S * kAPlane + p * kBPlane, &mapB, full + stage, c * kBK,
+                        tma_load_2d(st + S * kAPl + p * kBPl, &mapB, full + stage, ks * kKS,
                                     p * g.plane_rows + g.b_row0 + tj * kBN);
                     }
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
             }
-            // Every stage armed here is waited on by the MMA issuer before it
-            // finishes (normal path), so no copy is in flight at exit; after a
-            // timeout the copies issued earlier have long landed.
         }
     } else if (warp == 1) {
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0, acc_phase = 0;
-            bool ok = true;
-            const uint32_t idesc = idesc_bf16(kBM, kBN);
-            bool issued = false;
+            bool ok = true, issued = false;
+            constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                if (!mbar_wait(acce, acc_phase ^ 1, g.flag, 2)) { ok = false; break; }
+                if (!mbar_wait(acce, acc_phase ^ 1, g.flag, 2)) break;
                 tc_fence_after();
-                for (int c = 0; c < kChunks && ok; ++c) {
+                for (int ks = 0; ks < K / kKS; ++ks) {
                     if (!mbar_wait(full + stage, phase, g.flag, 3)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(tiles + stage * stage_bytes);
-                    const uint32_t sb = sa + S * kAPlane;
+                    const uint32_t sb = sa + S * kAPl;
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                    for (int gi = 0; gi < S; ++gi) {
 #pragma unroll
-                        for (int gi = 0; gi < S; ++gi) {
-                            // orders g = a + b <= S - 1 only
-                            const int a0 = 0;
-                            const int a1 = gi;
+                        for (int k = 0; k < SL::count(gi); ++k) {
+                            const int slot = SL::first(gi) + k;
+                            const int a0 = k * SL::cap;
+                            const int a1 = (k + 1) * SL::cap - 1 < gi ? (k + 1) * SL::cap - 1 : gi;
+#pragma unroll
                             for (int a = a0; a <= a1; ++a) {
                                 const int b = gi - a;
-                                const uint64_t da = smem_desc_sw64(sa + a * kAPlane + kk * 32);
-                                const uint64_t db = smem_desc_sw64(sb + b * kBPlane + kk * 32);
-                                const int acc = (c == 0 && kk == 0 && a == a0) ? 0 : 1;
-                                mma_bf16(tmem + (uint32_t)(gi * kBN), da, db, idesc, acc);
+                                mma_bf16(tmem + (uint32_t)(slot * kBN), smem_desc_sw32(sa + a * kAPl),
+                                         smem_desc_sw32(sb + b * kBPl), idesc, (ks == 0 && a == a0) ? 0 : 1);
                                 issued = true;
                             }
                         }
@@ -307,55 +346,77 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                 acc_phase ^= 1;
             }
             if (issued) {
-                // all issued MMAs complete before TMEM can be released
+                // every issued MMA completes before TMEM is released
                 mma_commit(drain);
                 mbar_wait(drain, 0, g.flag, 4);
             }
         }
     } else {
-        // epilogue: warps 2..5
-        const int sub = warp & 3;
-        const int row_in_tile = 32 * sub + lane;
-        uint32_t acc_phase = 0;
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int r = 32 * quarter + lane;  // row in the tile = TMEM lane
+        const bool leader = (warp == 2 && lane == 0);
+        uint32_t acc_phase = 0, c_phase = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int ti, tj;
             tile_coords(t, tiles_n, g.lower, ti, tj);
-            if (!mbar_wait(accf, acc_phase, g.flag, 5)) break;
+            const int cx = g.c_x0 + tj * kBN, cy = g.c_y0 + ti * kBM;
+            if (leader) {
+                bulk_wait_read0();  // the previous tile's store has left shared memory
+                if (g.sub) {
+                    mbar_expect_tx(cfull, kCTile);
+                    for (int b = 0; b < 4; ++b) tma_load_2d(ctile + b * kCBox, &mapC, cfull, cx + 16 * b, cy);
+                }
+            }
+            epi_bar();
+            bool ok = true;
+            if (g.sub) {
+                ok = mbar_wait(cfull, c_phase, g.flag, 6);
+                c_phase ^= 1;
+            }
+            ok = mbar_wait(accf, acc_phase, g.flag, 5) && ok;
+            if (!ok) break;
             tc_fence_after();
-            const int i = ti * kBM + row_in_tile;
-            const int eA = g.expA ? g.expA[g.a_row0 + i] : 0;
-            long long* crow = g.C + (int64_t)i * g.ldc + (int64_t)tj * kBN;
-            const uint32_t trow = tmem + ((uint32_t)(32 * sub) << 16);
-            for (int cc = 0; cc < kBN / 16; ++cc) {
-                float v[S][16];
+            const int eA = g.expA ? g.expA[g.a_row0 + ti * kBM + r] : 0;
+            const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll 1
+            for (int cc = 0; cc < 4; ++cc) {
+                const int col0 = 32 * half + 8 * cc;  // column within the tile
+                float v[SL::total][8];
 #pragma unroll
-                for (int gi = 0; gi < S; ++gi) tmem_ld16(trow + (uint32_t)(gi * kBN + cc * 16), v[gi]);
+                for (int sl = 0; sl < SL::total; ++sl) tmem_ld8(trow + (uint32_t)(sl * kBN + col0), v[sl]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = tj * kBN + cc * 16 + j;
-                    const int eB = g.expB ? g.expB[g.b_row0 + col] : 0;
+                for (int j = 0; j < 8; ++j) {
+                    const int col = col0 + j;
+                    const int eB = g.expB ? g.expB[g.b_row0 + tj * kBN + col] : 0;
                     const int sh0 = eA + eB + g.shift0;
                     long long acc = 0;
 #pragma unroll
                     for (int gi = 0; gi < S; ++gi) {
-                        const long long p = (long long)__float2int_rn(v[gi][j]);
-                        const int sh = sh0 - 8 * gi;
-                        if (sh >= 0) {
-                            acc += (long long)((unsigned long long)p << (sh > 62 ? 62 : sh));
-                        } else if (sh > -62) {
-                            acc += (p + (1ll << (-sh - 1))) >> (-sh);
-                        }
+                        int p = __float2int_rn(v[SL::first(gi)][j]);
+                        if (SL::count(gi) > 1) p += __float2int_rn(v[SL::first(gi) + 1][j]);
+                        acc += shift_round((long long)p, sh0 - 8 * gi);
                     }
-                    long long* cp = crow + cc * 16 + j;
+                    // 128-byte swizzle: 16-byte chunk index XOR (row % 8)
+                    const int box = col >> 4, jj = col & 15;
+                    long long* cp = (long long*)(ctile + box * kCBox + r * 128 +
+                                                 ((((jj >> 1) ^ (r & 7)) << 4) | ((jj & 1) << 3)));
                     if (g.sub) *cp -= acc;
                     else *cp = acc;
                 }
             }
+            fence_proxy_async();
             tc_fence_before();
+            epi_bar();
+            if (leader) {
+                for (int b = 0; b < 4; ++b) tma_store_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
+                bulk_commit();
+            }
             mbar_arrive(acce);
             acc_phase ^= 1;
         }
+        if (leader) bulk_wait0();
     }
     tc_fence_before();
     __syncthreads();
@@ -366,11 +427,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
-// Digit split of int64 fixed-point rows (Q(F)), K = 128 values per row, one
-// warp per row.  exp_mode 0: the row exponent is `fixed_exp`; 1: the smallest
-// e with |v| < 2^e (from the row maximum).  Writes s bf16 planes and expo[].
+// Digit split.  For a value v with row exponent e (|v| < 2^e, or <= 1 for the
+// fixed exponent 0 of the factor) w = round(v 2^(T - e)), T = 7 + 8 (s - 1),
+// is cut into balanced base-256 digits from the least significant one.
 __device__ __forceinline__ void split_digits(long long w, int s, float* d) {
-    // balanced base-256 digits from the least significant; top digit in [-128, 128]
     for (int a = s - 1; a > 0; --a) {
         long long lo = ((w + 128) & 255) - 128;
         d[a] = (float)lo;
@@ -385,62 +445,50 @@ __device__ __forceinline__ long long round_shift(long long v, int sh) {
     return (v + (1ll << (-sh - 1))) >> (-sh);
 }
 
-__global__ void slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int exp_mode,
-                                  int fixed_exp, int s, int plane_rows, __nv_bfloat16* __restrict__ dst,
-                                  int* __restrict__ expo) {
+// Rows of an int64 Q(F) matrix, K = 128 or 256 values per row, exponent 0
+// (entries of the scaled factor are bounded by 1).  One warp per row.
+template <int K>
+__global__ void slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s,
+                                  int plane_rows, __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
-    long long v[4];
-    unsigned long long mx = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        v[q] = src[(int64_t)r * ld + lane + 32 * q];
-        unsigned long long a = (unsigned long long)(v[q] < 0 ? -v[q] : v[q]);
-        mx = a > mx ? a : mx;
-    }
-    int e = fixed_exp;
-    if (exp_mode == 1) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
-            mx = t > mx ? t : mx;
-        }
-        e = mx == 0 ? 0 : (64 - __clzll((long long)mx)) - F;
-    }
-    if (lane == 0) expo[r] = e;
+    if (lane == 0) expo[r] = 0;
     const int T = 7 + 8 * (s - 1);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < K / 32; ++q) {
         float d[7];
-        split_digits(round_shift(v[q], T - e - F), s, d);
+        split_digits(round_shift(src[(int64_t)r * ld + lane + 32 * q], T - F), s, d);
         for (int a = 0; a < s; ++a)
-            dst[((int64_t)a * plane_rows + r) * kNB + lane + 32 * q] = __float2bfloat16_rn(d[a]);
+            dst[((int64_t)a * plane_rows + r) * K + lane + 32 * q] = __float2bfloat16_rn(d[a]);
     }
 }
 
-// Column split: a 128-row block of an int64 Q(F) matrix, columns [0, ncols),
-// transposed into digit rows (row = column of the source, K = source row),
-// per-column exponent from the column maximum.  One warp per column.
-__global__ void slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s,
-                                  int plane_rows, __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
-    __shared__ long long tile[kNB][33];
+// Column split: a K-row block (K = 128 or 256) of an int64 Q(F) matrix,
+// columns [0, ncols), transposed into digit rows (row = source column,
+// K = source rows), per-column exponent from the column maximum.
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
+                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
+    extern __shared__ __align__(16) long long tile[];   // [K][33]
     const int c0 = blockIdx.x * 32;
-    const int tid = threadIdx.x;  // 256 threads
-    for (int e = tid; e < kNB * 32; e += 256) {
-        int r = e >> 5, c = e & 31;
-        tile[r][c] = (c0 + c < ncols) ? src[(int64_t)r * ld + c0 + c] : 0;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < K * 32; e += 256) {
+        int rr = e >> 5, c = e & 31;
+        tile[rr * 33 + c] = (c0 + c < ncols) ? src[(int64_t)rr * ld + c0 + c] : 0;
     }
     __syncthreads();
     const int lane = tid & 31, w = tid >> 5;
+    const int T = 7 + 8 * (s - 1);
     for (int c = w; c < 32; c += 8) {
         const int col = c0 + c;
         if (col >= ncols) break;
-        long long v[4];
+        long long v[K / 32];
         unsigned long long mx = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            v[q] = tile[lane + 32 * q][c];
+        for (int q = 0; q < K / 32; ++q) {
+            v[q] = tile[(lane + 32 * q) * 33 + c];
             unsigned long long a = (unsigned long long)(v[q] < 0 ? -v[q] : v[q]);
             mx = a > mx ? a : mx;
         }
@@ -451,19 +499,18 @@ __global__ void slice_cols_kernel(int ncols, const long long* __restrict__ src, 
         }
         const int e = mx == 0 ? 0 : (64 - __clzll((long long)mx)) - F;
         if (lane == 0) expo[col] = e;
-        const int T = 7 + 8 * (s - 1);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < K / 32; ++q) {
             float d[7];
             split_digits(round_shift(v[q], T - e - F), s, d);
             for (int a = 0; a < s; ++a)
-                dst[((int64_t)a * plane_rows + col) * kNB + lane + 32 * q] = __float2bfloat16_rn(d[a]);
+                dst[((int64_t)a * plane_rows + col) * K + lane + 32 * q] = __float2bfloat16_rn(d[a]);
         }
     }
 }
 
 // Rows of a 128 x 128 FP64 matrix (the inverse of a diagonal block), per-row
-// exponent; w = round(v 2^(T - e)) is exact in double (|w| <= 2^T <= 2^55).
+// exponent; w = round(v 2^(T - e)) is exact in double (|w| <= 2^T <= 2^47).
 __global__ void slice_f64_kernel(const double* __restrict__ src, int s, int plane_rows,
                                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
     const int lane = threadIdx.x & 31;
@@ -479,16 +526,13 @@ __global__ void slice_f64_kernel(const double* __restrict__ src, int s, int plan
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
-    if (mx > 0.0) {
-        frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
-    }
+    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
     if (lane == 0) expo[r] = e;
     const int T = 7 + 8 * (s - 1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         float d[7];
-        long long w = llrint(ldexp(v[q], T - e));
-        split_digits(w, s, d);
+        split_digits(llrint(ldexp(v[q], T - e)), s, d);
         for (int a = 0; a < s; ++a)
             dst[((int64_t)a * plane_rows + r) * kNB + lane + 32 * q] = __float2bfloat16_rn(d[a]);
     }
@@ -513,56 +557,64 @@ __global__ void zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, c
     *q = llrint(ldexp(D[i] * v * D[j], kFL));
 }
 
-// Cholesky of the 128 x 128 diagonal block from Q60, in FP64 shared memory;
-// writes L back as Q60 and its inverse (FP64) to Linv.
-__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
-
+// Cholesky of the 128 x 128 diagonal block from Q60 in FP64 shared memory
+// (L in the lower triangle, its inverse transposed in the upper one), L
+// written back as Q60, the inverse as FP64 (full, zero above the diagonal).
+constexpr int kLD = kNB + 1;
 __global__ void __launch_bounds__(512)
 potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, double* __restrict__ Linv, int* flag) {
-    extern __shared__ __align__(16) double sh[];
-    double* S = sh;
-    double* Xs = sh + kNB * (kNB + 1) / 2;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    extern __shared__ __align__(16) double S[];   // 128 x 129, then 128 inverse diagonal
+    double* invd = S + kNB * kLD;
+    const int tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;  // 32 x 16
     const double sc = ldexp(1.0, -kFL);
-    for (int e = tid; e < kNB * kNB; e += nt) {
-        int i = e / kNB, j = e % kNB;
-        if (j <= i) S[pk(i, j)] = (double)Z[(k0 + i) * ld + k0 + j] * sc;
+    for (int e = tid; e < kNB * kNB; e += 512) {
+        int i = e >> 7, j = e & 127;
+        if (j <= i) S[i * kLD + j] = (double)Z[(k0 + i) * ld + k0 + j] * sc;
     }
     __syncthreads();
     for (int j = 0; j < kNB; ++j) {
         if (tid == 0) {
-            double d = S[pk(j, j)];
+            double d = S[j * kLD + j];
             if (!(d > 0.0)) { set_flag(flag, DEV_NOT_SPD, (int)(k0 + j)); d = 1.0; }
-            S[pk(j, j)] = sqrt(d);
+            double l = sqrt(d);
+            S[j * kLD + j] = l;
+            invd[j] = 1.0 / l;
         }
         __syncthreads();
-        double inv = 1.0 / S[pk(j, j)];
-        for (int i = j + 1 + tid; i < kNB; i += nt) S[pk(i, j)] *= inv;
+        const double iv = invd[j];
+        for (int i = j + 1 + tid; i < kNB; i += 512) S[i * kLD + j] *= iv;
         __syncthreads();
-        for (int i = j + 1 + warp; i < kNB; i += nw) {
-            double lij = S[pk(i, j)];
-            for (int l = j + 1 + lane; l <= i; l += 32) S[pk(i, l)] -= lij * S[pk(l, j)];
+        for (int i = j + 1 + ty; i < kNB; i += 16) {
+            const double lij = S[i * kLD + j];
+            for (int l = j + 1 + tx; l <= i; l += 32) S[i * kLD + l] -= lij * S[l * kLD + j];
         }
         __syncthreads();
     }
-    for (int e = tid; e < kNB * kNB; e += nt) {
-        int i = e / kNB, j = e % kNB;
-        if (j <= i) Z[(k0 + i) * ld + k0 + j] = llrint(ldexp(S[pk(i, j)], kFL));
+    for (int e = tid; e < kNB * kNB; e += 512) {
+        int i = e >> 7, j = e & 127;
+        if (j <= i) Z[(k0 + i) * ld + k0 + j] = llrint(ldexp(S[i * kLD + j], kFL));
     }
-    if (tid < kNB) {
-        const int c = tid;
-        Xs[pk(c, c)] = 1.0 / S[pk(c, c)];
-        for (int i = c + 1; i < kNB; ++i) {
-            double s = 0.0;
-            for (int k = c; k < i; ++k) s += S[pk(i, k)] * Xs[pk(k, c)];
-            Xs[pk(i, c)] = -s / S[pk(i, i)];
+    // X = L^-1 row by row: X[i][c] = -(sum_{k=c}^{i-1} L[i][k] X[k][c]) / L[i][i],
+    // X[k][c] kept at S[c][k] (upper triangle); 4 threads per column c
+    const int c = tid >> 2, part = tid & 3;
+    for (int i = 1; i < kNB; ++i) {
+        double sum = 0.0;
+        if (c < i) {
+            for (int k = c + part; k < i; k += 4) {
+                const double xkc = (k == c) ? invd[c] : S[c * kLD + k];
+                sum += S[i * kLD + k] * xkc;
+            }
         }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        __syncthreads();
+        if (c < i && part == 0) S[c * kLD + i] = -sum * invd[i];
+        __syncthreads();
     }
-    __syncthreads();
-    for (int e = tid; e < kNB * kNB; e += nt) {
-        int i = e / kNB, j = e % kNB;
-        Linv[e] = (j <= i) ? Xs[pk(i, j)] : 0.0;
+    for (int e = tid; e < kNB * kNB; e += 512) {
+        int i = e >> 7, j = e & 127;
+        Linv[e] = (j < i) ? S[j * kLD + i] : (j == i ? invd[i] : 0.0);
     }
 }
 
@@ -611,61 +663,128 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t plane_rows, int box_rows) {
+// Digit planes: [s * plane_rows][K] bf16, box 16 x box_rows, 32-byte swizzle.
+bool make_digit_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t plane_rows, int K, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)kNB, (cuuint64_t)(s * plane_rows)};
-    cuuint64_t strides[1] = {(cuuint64_t)kNB * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)(s * plane_rows)};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, buf, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, buf, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// int64 result matrix rows x cols (row stride ld elements), box 16 x 128, 128-byte swizzle.
+bool make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, int64_t ld) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+    cuuint32_t box[2] = {16, (cuuint32_t)kBM};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 size_t gemm_smem(int s, int stages) {
-    return 1024 + (size_t)stages * s * (kAPlane + kBPlane) + 8 * (2 * stages + 3) + 16;
+    return 1024 + (size_t)kCTile + (size_t)stages * s * (kAPl + kBPl) + 8 * (2 * stages + 4) + 16;
+}
+
+int pick_stages(int s) {
+    int st = 8;
+    while (st > 2 && gemm_smem(s, st) > 227 * 1024) --st;
+    return st;
 }
 
 int g_num_sms = 0;
 
-template <int S>
-void set_gemm_attr(size_t smem) {
-    cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int S, int K>
+cudaError_t set_attr() {
+    return cudaFuncSetAttribute(ozaki_gemm_kernel<S, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_smem(S, pick_stages(S)));
 }
 
-void launch_ozaki(Ctx& c, const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int a_row0, int b_row0,
-                  int lower, int sub, int Fc, const int* expA, const int* expB, long long* C, int64_t ldc) {
+enum Buf { BUF_P = 0, BUF_Q = 1 };
+
+// C op= A B^T with A = rows [a_row0, a_row0 + M) of digit buffer `ba`, B =
+// rows [b_row0, b_row0 + N) of buffer `bb`, both with K digits per row.
+void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, int N, const CUtensorMap& mapC,
+                  int c_x0, int c_y0, int lower, int sub, int Fc, const int* expA, const int* expB) {
     MixedState& st = *c.mixed;
     GemmArgs g;
-    g.M = M; g.N = N; g.s = st.s; g.plane_rows = (int)c.Np; g.a_row0 = a_row0; g.b_row0 = b_row0;
-    g.lower = lower; g.sub = sub; g.shift0 = Fc - 14; g.expA = expA; g.expB = expB; g.C = C; g.ldc = ldc;
-    g.stages = st.stages; g.flag = c.d_flag;
-    const int tiles_m = M / kBM, tiles_n = N / kBN;
-    int64_t ntiles;
-    if (lower) {
-        int T0 = tiles_n / 2;
-        ntiles = tiles_m <= T0 ? (int64_t)tiles_m * tiles_m + tiles_m
-                               : (int64_t)T0 * T0 + T0 + (int64_t)(tiles_m - T0) * tiles_n;
-    } else {
-        ntiles = (int64_t)tiles_m * tiles_n;
-    }
-    int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
+    g.M = M; g.N = N; g.plane_rows = (int)c.Np; g.a_row0 = a_row0; g.b_row0 = b_row0;
+    g.c_x0 = c_x0; g.c_y0 = c_y0; g.lower = lower; g.sub = sub; g.shift0 = Fc - 14;
+    g.expA = expA; g.expB = expB; g.stages = pick_stages(st.s); g.flag = c.d_flag;
+    const int ki = K == 256 ? 1 : 0;
+    const CUtensorMap& mA = st.dig[ba][ki][0];
+    const CUtensorMap& mB = st.dig[bb][ki][1];
+    const int64_t ntiles = tile_count(M / kBM, N / kBN, lower);
+    const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
     if (grid < 1) return;
     // executed tensor-core work: every kept tile, every digit product
-    const double flops = (double)ntiles * 2.0 * kBM * kBN * kNB * (st.s * (st.s + 1) / 2);
-    const size_t smem = gemm_smem(st.s, st.stages);
+    const double flops = (double)ntiles * 2.0 * kBM * kBN * K * (st.s * (st.s + 1) / 2);
+    const size_t smem = gemm_smem(st.s, g.stages);
     prof_begin(c);
-    switch (st.s) {
-        case 4: ozaki_gemm_kernel<4><<<grid, 192, smem, c.stream>>>(mA, mB, g); break;
-        case 5: ozaki_gemm_kernel<5><<<grid, 192, smem, c.stream>>>(mA, mB, g); break;
-        case 6: ozaki_gemm_kernel<6><<<grid, 192, smem, c.stream>>>(mA, mB, g); break;
-        default: ozaki_gemm_kernel<7><<<grid, 192, smem, c.stream>>>(mA, mB, g); break;
+#define CCOV_OZ(S_, K_) ozaki_gemm_kernel<S_, K_><<<grid, kThreads, smem, c.stream>>>(mA, mB, mapC, g)
+    if (K == 256) {
+        switch (st.s) {
+            case 4: CCOV_OZ(4, 256); break;
+            case 5: CCOV_OZ(5, 256); break;
+            default: CCOV_OZ(6, 256); break;
+        }
+    } else {
+        switch (st.s) {
+            case 4: CCOV_OZ(4, 128); break;
+            case 5: CCOV_OZ(5, 128); break;
+            default: CCOV_OZ(6, 128); break;
+        }
     }
+#undef CCOV_OZ
     prof_end(c, flops);
     c.launches++;
     st.tiles_done += ntiles;
+}
+
+void slice_rows(Ctx& c, int K, int rows, const long long* src, Buf b) {
+    MixedState& st = *c.mixed;
+    __nv_bfloat16* dst = b == BUF_P ? st.digP : st.digQ;
+    int* ex = b == BUF_P ? st.expP : st.expQ;
+    const int grid = (rows + 7) / 8;
+    if (K == 256)
+        slice_rows_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex);
+    else
+        slice_rows_kernel<128><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex);
+    c.launches++;
+}
+
+void slice_cols(Ctx& c, int K, int ncols, const long long* src, Buf b) {
+    MixedState& st = *c.mixed;
+    __nv_bfloat16* dst = b == BUF_P ? st.digP : st.digQ;
+    int* ex = b == BUF_P ? st.expP : st.expQ;
+    const int grid = (ncols + 31) / 32;
+    const size_t smem = (size_t)K * 33 * 8;
+    if (K == 256)
+        slice_cols_kernel<256><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex);
+    else
+        slice_cols_kernel<128><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex);
+    c.launches++;
+}
+
+void slice_linv(Ctx& c, const double* Linv, Buf b) {
+    MixedState& st = *c.mixed;
+    slice_f64_kernel<<<kNB / 8, 256, 0, c.stream>>>(Linv, st.s, (int)c.Np, b == BUF_P ? st.digP : st.digQ,
+                                                     b == BUF_P ? st.expP : st.expQ);
+    c.launches++;
+}
+
+void potrf_block(Ctx& c, int64_t blk) {
+    long long* Zq = reinterpret_cast<long long*>(c.d_Z);
+    potrf_diag_q_kernel<<<1, 512, sizeof(double) * (kNB * kLD + kNB), c.stream>>>(
+        Zq, c.Np, blk * kNB, c.d_Linv + blk * kNB * kNB, c.d_flag);
+    c.launches++;
 }
 
 }  // namespace
@@ -674,8 +793,9 @@ cudaError_t mixed_alloc(Ctx& c) {
     c.mixed = new MixedState();
     MixedState& st = *c.mixed;
     st.s = c.opt.mixed_slices;
+    if (st.s > 6) return cudaErrorInvalidValue;
     const int64_t Np = c.Np;
-    size_t plane = (size_t)st.s * Np * kNB;
+    const size_t plane = (size_t)st.s * Np * kKMax;
     cudaError_t e;
     if ((e = cudaMalloc(&st.digP, plane * 2)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.digQ, plane * 2)) != cudaSuccess) return e;
@@ -683,22 +803,27 @@ cudaError_t mixed_alloc(Ctx& c) {
     if ((e = cudaMalloc(&st.expQ, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.R, Np * Np * sizeof(long long))) != cudaSuccess) return e;
     c.bytes += (int64_t)(plane * 4 + Np * 8 + Np * Np * 8);
-    if ((e = cudaMemset(st.digP, 0, plane * 2)) != cudaSuccess) return e;
-    if ((e = cudaMemset(st.digQ, 0, plane * 2)) != cudaSuccess) return e;
-    if (!make_map(&st.mapP128, st.digP, st.s, Np, kBM) || !make_map(&st.mapP64, st.digP, st.s, Np, kBN) ||
-        !make_map(&st.mapQ128, st.digQ, st.s, Np, kBM) || !make_map(&st.mapQ64, st.digQ, st.s, Np, kBN))
-        return cudaErrorInvalidValue;
-    size_t budget = 227 * 1024;
-    st.stages = 4;
-    while (st.stages > 2 && gemm_smem(st.s, st.stages) > budget) --st.stages;
-    if (gemm_smem(st.s, st.stages) > budget) return cudaErrorInvalidConfiguration;
-    set_gemm_attr<4>(gemm_smem(st.s, st.stages));
-    set_gemm_attr<5>(gemm_smem(st.s, st.stages));
-    set_gemm_attr<6>(gemm_smem(st.s, st.stages));
-    set_gemm_attr<7>(gemm_smem(st.s, st.stages));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // on the context's stream (it need not synchronise with the legacy stream)
+    if ((e = cudaMemsetAsync(st.digP, 0, plane * 2, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(st.digQ, 0, plane * 2, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    __nv_bfloat16* bufs[2] = {st.digP, st.digQ};
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 2; ++k)
+            for (int r = 0; r < 2; ++r)
+                if (!make_digit_map(&st.dig[b][k][r], bufs[b], st.s, Np, k ? 256 : 128, r ? kBN : kBM))
+                    return cudaErrorInvalidValue;
+    if (c.d_Z && !make_c_map(&st.mapZ, reinterpret_cast<long long*>(c.d_Z), Np, Np, Np)) return cudaErrorInvalidValue;
+    if (!make_c_map(&st.mapR, st.R, Np, Np, Np)) return cudaErrorInvalidValue;
+    cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
+                        set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
+    for (cudaError_t x : a)
+        if (x != cudaSuccess) return x;
     if ((e = cudaFuncSetAttribute(potrf_diag_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(double) * kNB * (kNB + 1)))) != cudaSuccess)
+                                  (int)(sizeof(double) * (kNB * kLD + kNB)))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(slice_cols_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  256 * 33 * 8)) != cudaSuccess)
         return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -716,12 +841,12 @@ void mixed_free(Ctx& c) {
     c.mixed = nullptr;
 }
 
-// Z_s (lower triangle, FP64 from the shared preparation) -> Q60, then the
-// blocked Cholesky and the blocked triangular inverse on the tensor cores.
+// Z_s -> Q60, blocked Cholesky, blocked triangular inverse (both with the big
+// trailing updates for pairs of 128-column sub-panels, K = 256) and the
+// camera Gram blocks of the inverse.
 cudaError_t mixed_factor_inverse(Ctx& c) {
     MixedState& st = *c.mixed;
     const int64_t Np = c.Np, nb = Np / kNB;
-    const int s = st.s;
     long long* Zq = reinterpret_cast<long long*>(c.d_Z);
     {
         int64_t nt = (Np + 31) / 32;
@@ -729,52 +854,69 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
                                                                                        c.d_G, c.d_D);
         c.launches++;
     }
-    for (int64_t kb = 0; kb < nb; ++kb) {
-        const int64_t k0 = kb * kNB, rem = Np - k0 - kNB;
-        double* Linv = c.d_Linv + kb * kNB * kNB;
-        potrf_diag_q_kernel<<<1, 512, sizeof(double) * kNB * (kNB + 1), c.stream>>>(Zq, Np, k0, Linv, c.d_flag);
-        c.launches++;
-        if (rem <= 0) continue;
-        // panel: L21 = A21 L_kk^-T (A21 bounded by 1: exponent 0)
-        slice_rows_kernel<<<(int)((rem + 7) / 8), 256, 0, c.stream>>>(
-            (int)rem, Zq + (k0 + kNB) * Np + k0, Np, kFL, 0, 0, s, (int)Np, st.digP, st.expP);
-        slice_f64_kernel<<<kNB / 8, 256, 0, c.stream>>>(Linv, s, (int)Np, st.digQ, st.expQ);
-        c.launches += 2;
-        launch_ozaki(c, st.mapP128, st.mapQ64, (int)rem, kNB, 0, 0, 0, 0, kFL, nullptr, st.expQ,
-                     Zq + (k0 + kNB) * Np + k0, Np);
-        // trailing update A22 -= L21 L21^T on lower tiles
-        slice_rows_kernel<<<(int)((rem + 7) / 8), 256, 0, c.stream>>>(
-            (int)rem, Zq + (k0 + kNB) * Np + k0, Np, kFL, 0, 0, s, (int)Np, st.digP, st.expP);
-        c.launches++;
-        launch_ozaki(c, st.mapP128, st.mapP64, (int)rem, (int)rem, 0, 0, 1, 1, kFL, nullptr, nullptr,
-                     Zq + (k0 + kNB) * Np + k0 + kNB, Np);
+    auto Zat = [&](int64_t row, int64_t col) { return Zq + row * Np + col; };
+    auto Rat = [&](int64_t row, int64_t col) { return st.R + row * Np + col; };
+    // ---- Cholesky ----
+    for (int64_t p = 0; p < nb; p += 2) {
+        const int64_t q = p + 1;
+        const int64_t kp = p * kNB, remP = Np - kp - kNB;
+        potrf_block(c, p);
+        if (remP <= 0) break;
+        // L[rows > p, p] = A[rows > p, p] L_pp^-T
+        slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
+        slice_linv(c, c.d_Linv + p * kNB * kNB, BUF_Q);
+        launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_Q, 0, kNB, st.mapZ, (int)kp, (int)(kp + kNB), 0, 0, kFL,
+                     nullptr, st.expQ);
+        // column strip q: A[rows >= q, q] -= L[rows >= q, p] L[q, p]^T
+        slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
+        launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_P, 0, kNB, st.mapZ, (int)(q * kNB), (int)(q * kNB), 0, 1,
+                     kFL, nullptr, nullptr);
+        potrf_block(c, q);
+        const int64_t kq = q * kNB, remQ = Np - kq - kNB;
+        if (remQ <= 0) break;
+        slice_rows(c, 128, (int)remQ, Zat(kq + kNB, kq), BUF_P);
+        slice_linv(c, c.d_Linv + q * kNB * kNB, BUF_Q);
+        launch_ozaki(c, 128, BUF_P, 0, (int)remQ, BUF_Q, 0, kNB, st.mapZ, (int)kq, (int)(kq + kNB), 0, 0, kFL,
+                     nullptr, st.expQ);
+        // trailing update with both sub-panels: A22 -= L[:, p:q] L[:, p:q]^T (lower tiles)
+        slice_rows(c, 256, (int)remQ, Zat(kq + kNB, kp), BUF_P);
+        launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_P, 0, (int)remQ, st.mapZ, (int)(kq + kNB), (int)(kq + kNB),
+                     1, 1, kFL, nullptr, nullptr);
     }
     cudaEventRecord(c.ev[3], c.stream);
-    // triangular inverse X = L^-1 in Q42, row block by row block
+    // ---- triangular inverse X = L^-1 (Q42), row blocks of 128 ----
     cudaError_t e = cudaMemsetAsync(st.R, 0, sizeof(long long) * Np * Np, c.stream);
     if (e != cudaSuccess) return e;
     identity_q_kernel<<<(int)((Np + 255) / 256), 256, 0, c.stream>>>(Np, st.R);
     c.launches++;
-    for (int64_t kb = 0; kb < nb; ++kb) {
-        const int64_t k0 = kb * kNB, rem = Np - k0 - kNB, nc = k0 + kNB;
-        const double* Linv = c.d_Linv + kb * kNB * kNB;
-        // X[k, :nc] = L_kk^-1 R[k, :nc]
-        slice_cols_kernel<<<(int)((nc + 31) / 32), 256, 0, c.stream>>>((int)nc, st.R + k0 * Np, Np, kFX, s,
-                                                                        (int)Np, st.digQ, st.expQ);
-        slice_f64_kernel<<<kNB / 8, 256, 0, c.stream>>>(Linv, s, (int)Np, st.digP, st.expP);
-        c.launches += 2;
-        launch_ozaki(c, st.mapP128, st.mapQ64, kNB, (int)nc, 0, 0, 0, 0, kFX, st.expP, st.expQ, st.R + k0 * Np, Np);
+    auto finalize = [&](int64_t blk) {
+        const int64_t k0 = blk * kNB, nc = k0 + kNB;
+        // X[blk, :nc] = L_blk^-1 R[blk, :nc]
+        slice_cols(c, 128, (int)nc, Rat(k0, 0), BUF_Q);
+        slice_linv(c, c.d_Linv + blk * kNB * kNB, BUF_P);
+        launch_ozaki(c, 128, BUF_P, 0, kNB, BUF_Q, 0, (int)nc, st.mapR, 0, (int)k0, 0, 0, kFX, st.expP, st.expQ);
         gram_q_kernel<<<(int)((nc + kGW - 1) / kGW), 128, 0, c.stream>>>(c.n, Np, k0, nc, st.R, c.d_Sig);
         c.launches++;
-        if (rem <= 0) continue;
-        // R[k+1:, :nc] -= L[k+1:, k] X[k, :nc]
-        slice_cols_kernel<<<(int)((nc + 31) / 32), 256, 0, c.stream>>>((int)nc, st.R + k0 * Np, Np, kFX, s,
-                                                                        (int)Np, st.digQ, st.expQ);
-        slice_rows_kernel<<<(int)((rem + 7) / 8), 256, 0, c.stream>>>(
-            (int)rem, Zq + (k0 + kNB) * Np + k0, Np, kFL, 0, 0, s, (int)Np, st.digP, st.expP);
-        c.launches += 2;
-        launch_ozaki(c, st.mapP128, st.mapQ64, (int)rem, (int)nc, 0, 0, 0, 1, kFX, nullptr, st.expQ,
-                     st.R + (k0 + kNB) * Np, Np);
+    };
+    for (int64_t p = 0; p < nb; p += 2) {
+        const int64_t q = p + 1;
+        const int64_t kp = p * kNB;
+        finalize(p);
+        if (q >= nb) break;
+        const int64_t kq = q * kNB;
+        // R[q, :kp+128] -= L[q, p] X[p, :kp+128]
+        slice_cols(c, 128, (int)(kp + kNB), Rat(kp, 0), BUF_Q);
+        slice_rows(c, 128, kNB, Zat(kq, kp), BUF_P);
+        launch_ozaki(c, 128, BUF_P, 0, kNB, BUF_Q, 0, (int)(kp + kNB), st.mapR, 0, (int)kq, 0, 1, kFX, nullptr,
+                     st.expQ);
+        finalize(q);
+        const int64_t remQ = Np - kq - kNB, nc = kq + kNB;
+        if (remQ <= 0) break;
+        // R[rows > q, :nc] -= L[rows > q, p:q] X[p:q, :nc]  (K = 256)
+        slice_cols(c, 256, (int)nc, Rat(kp, 0), BUF_Q);
+        slice_rows(c, 256, (int)remQ, Zat(kq + kNB, kp), BUF_P);
+        launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_Q, 0, (int)nc, st.mapR, 0, (int)(kq + kNB), 0, 1, kFX,
+                     nullptr, st.expQ);
     }
     return cudaGetLastError();
 }
@@ -783,11 +925,12 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
 
 // Test hook (include/ccov_testing.h): one call of the digit-split tensor-core
 // GEMM on caller data, with its own temporary workspace.
-extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int M, int N, const uint16_t* digA, const int* expA,
-                                                    const uint16_t* digB, const int* expB, int Fc, int sub,
-                                                    int lower, long long* C) {
+extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N, const uint16_t* digA,
+                                                    const int* expA, const uint16_t* digB, const int* expB,
+                                                    int Fc, int sub, int lower, long long* C) {
     using namespace ccov;
-    if (s < 4 || s > 7 || M <= 0 || N <= 0 || M % kBM || N % kBN || !digA || !digB || !C)
+    if (s < 4 || s > 6 || (K != 128 && K != 256) || M <= 0 || N <= 0 || M % kBM || N % kBN || !digA || !digB ||
+        !C)
         return CCOV_ERR_INVALID_ARG;
     if (lower && N != M) return CCOV_ERR_INVALID_ARG;
     Ctx c;
@@ -806,16 +949,21 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int M, int N, const 
         if (cudaMalloc(&c.d_flag, 2 * sizeof(int)) != cudaSuccess) { st = CCOV_ERR_OOM; break; }
         cudaMemset(c.d_flag, 0, 2 * sizeof(int));
         for (int a = 0; a < s; ++a) {
-            cudaMemcpy(ms.digP + (size_t)a * c.Np * kNB, digA + (size_t)a * M * kNB, (size_t)M * kNB * 2,
+            cudaMemcpy(ms.digP + (size_t)a * c.Np * K, digA + (size_t)a * M * K, (size_t)M * K * 2,
                        cudaMemcpyHostToDevice);
-            cudaMemcpy(ms.digQ + (size_t)a * c.Np * kNB, digB + (size_t)a * N * kNB, (size_t)N * kNB * 2,
+            cudaMemcpy(ms.digQ + (size_t)a * c.Np * K, digB + (size_t)a * N * K, (size_t)N * K * 2,
                        cudaMemcpyHostToDevice);
         }
         if (expA) { cudaMalloc(&dEA, M * sizeof(int)); cudaMemcpy(dEA, expA, M * sizeof(int), cudaMemcpyHostToDevice); }
         if (expB) { cudaMalloc(&dEB, N * sizeof(int)); cudaMemcpy(dEB, expB, N * sizeof(int), cudaMemcpyHostToDevice); }
         if (cudaMalloc(&dC, (size_t)M * N * 8) != cudaSuccess) { st = CCOV_ERR_OOM; break; }
         cudaMemcpy(dC, C, (size_t)M * N * 8, cudaMemcpyHostToDevice);
-        launch_ozaki(c, ms.mapP128, ms.mapQ64, M, N, 0, 0, lower, sub, Fc, dEA, dEB, dC, N);
+        CUtensorMap mapC;
+        if (!make_c_map(&mapC, dC, M, N, N)) { st = CCOV_ERR_CUDA; break; }
+        // the copies above ran on the legacy stream; the kernel's stream does not
+        // wait for them by itself
+        if (cudaDeviceSynchronize() != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
+        launch_ozaki(c, K, BUF_P, 0, M, BUF_Q, 0, N, mapC, 0, 0, lower, sub, Fc, dEA, dEB);
         if (cudaStreamSynchronize(c.stream) != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         int flag[2];
         cudaMemcpy(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost);
