@@ -50,8 +50,6 @@ struct MixedState {
     int* expP = nullptr;             // Np
     int* expQ = nullptr;             // Np
     long long* R = nullptr;          // Np x Np, Q42
-    // [buffer P/Q][K 128/256][box rows 128/64]
-    CUtensorMap dig[2][2][2];
     CUtensorMap mapZ, mapR;          // int64 result maps
     int64_t tiles_done = 0;
 };
@@ -127,16 +125,32 @@ __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
-// K-major operand tile written by TMA with 32-byte swizzle: one 32-byte row
-// (16 bf16 along K) per M/N row, 8-row atoms of 256 bytes.
-__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+// Digit planes are stored in the order the tensor cores read K-major
+// operands without swizzle: per plane, per 16-wide slice of K and per block of
+// 128 rows, one contiguous 4 KB block of 16 groups of 8 rows, each group two
+// 8 x 8 core matrices (8 rows x 16 bytes) along K.  A stage of the pipeline
+// is then a handful of contiguous bulk copies.
+__host__ __device__ __forceinline__ int64_t blk_off(int plane, int r, int k, int K, int plane_rows) {
+    const int64_t rb = plane_rows / 128;
+    return ((((int64_t)plane * (K / 16) + (k >> 4)) * rb + (r >> 7)) << 11) + (((r & 127) >> 3) << 7) +
+           (((k & 15) >> 3) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// K-major operand tile in that layout: core matrices 128 bytes apart along K
+// (leading byte offset) and 256 bytes apart along M/N (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-    d |= (uint64_t)1 << 16;                    // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset: next 8-row atom
-    d |= (uint64_t)1 << 46;                    // descriptor version
-    d |= (uint64_t)6 << 61;                    // 32-byte swizzle
+    d |= (uint64_t)(128 >> 4) << 16;           // leading byte offset
+    d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                    // descriptor version; no swizzle
     return d;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 // kind::f16 instruction descriptor: bf16 x bf16 -> f32, both K-major, M x N.
@@ -217,6 +231,8 @@ __device__ __forceinline__ void tile_coords(int64_t t, int tiles_n, int lower, i
 }
 
 struct GemmArgs {
+    const __nv_bfloat16* digA;  // digit planes of A and B (layout of blk_off)
+    const __nv_bfloat16* digB;
     int M, N;             // rows of A and of B (multiples of 128 and 64)
     int plane_rows;       // rows per digit plane in the operand buffers (Np)
     int a_row0, b_row0;   // first row of the operands inside their planes
@@ -243,8 +259,7 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
 // (load of C overlapped with the MMAs of the same tile, store asynchronous).
 template <int S, int K>
 __global__ void __launch_bounds__(kThreads, 1)
-ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                  const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
     using SL = Slots<S, K>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -299,10 +314,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                     mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
 #pragma unroll
                     for (int p = 0; p < S; ++p) {
-                        tma_load_2d(st + p * kAPl, &mapA, full + stage, ks * kKS,
-                                    p * g.plane_rows + g.a_row0 + ti * kBM);
-                        tma_load_2d(st + S * kAPl + p * kBPl, &mapB, full + stage, ks * kKS,
-                                    p * g.plane_rows + g.b_row0 + tj * kBN);
+                        bulk_load(st + p * kAPl, g.digA + blk_off(p, g.a_row0 + ti * kBM, ks * kKS, K, g.plane_rows),
+                                  kAPl, full + stage);
+                        bulk_load(st + S * kAPl + p * kBPl,
+                                  g.digB + blk_off(p, g.b_row0 + tj * kBN, ks * kKS, K, g.plane_rows), kBPl,
+                                  full + stage);
                     }
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
@@ -332,8 +348,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
 #pragma unroll
                             for (int a = a0; a <= a1; ++a) {
                                 const int b = gi - a;
-                                mma_bf16(tmem + (uint32_t)(slot * kBN), smem_desc_sw32(sa + a * kAPl),
-                                         smem_desc_sw32(sb + b * kBPl), idesc, (ks == 0 && a == a0) ? 0 : 1);
+                                mma_bf16(tmem + (uint32_t)(slot * kBN), smem_desc_kmajor(sa + a * kAPl),
+                                         smem_desc_kmajor(sb + b * kBPl), idesc, (ks == 0 && a == a0) ? 0 : 1);
                                 issued = true;
                             }
                         }
@@ -369,17 +385,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                 }
             }
             epi_bar();
-            bool ok = true;
-            if (g.sub) {
-                ok = mbar_wait(cfull, c_phase, g.flag, 6);
-                c_phase ^= 1;
-            }
-            ok = mbar_wait(accf, acc_phase, g.flag, 5) && ok;
-            if (!ok) break;
+            if (!mbar_wait(accf, acc_phase, g.flag, 5)) break;
             tc_fence_after();
+            // phase 1: drain the accumulators into exact int64 sums (registers),
+            // then release TMEM so that the next tile's MMAs start at once
             const int eA = g.expA ? g.expA[g.a_row0 + ti * kBM + r] : 0;
             const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
-#pragma unroll 1
+            long long res[32];
+#pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 const int col0 = 32 * half + 8 * cc;  // column within the tile
                 float v[SL::total][8];
@@ -388,8 +401,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int col = col0 + j;
-                    const int eB = g.expB ? g.expB[g.b_row0 + tj * kBN + col] : 0;
+                    const int eB = g.expB ? g.expB[g.b_row0 + tj * kBN + col0 + j] : 0;
                     const int sh0 = eA + eB + g.shift0;
                     long long acc = 0;
 #pragma unroll
@@ -398,23 +410,33 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                         if (SL::count(gi) > 1) p += __float2int_rn(v[SL::first(gi) + 1][j]);
                         acc += shift_round((long long)p, sh0 - 8 * gi);
                     }
-                    // 128-byte swizzle: 16-byte chunk index XOR (row % 8)
-                    const int box = col >> 4, jj = col & 15;
-                    long long* cp = (long long*)(ctile + box * kCBox + r * 128 +
-                                                 ((((jj >> 1) ^ (r & 7)) << 4) | ((jj & 1) << 3)));
-                    if (g.sub) *cp -= acc;
-                    else *cp = acc;
+                    res[8 * cc + j] = acc;
                 }
             }
-            fence_proxy_async();
             tc_fence_before();
+            mbar_arrive(acce);
+            acc_phase ^= 1;
+            // phase 2: combine with C in the staged tile and store it
+            if (g.sub) {
+                if (!mbar_wait(cfull, c_phase, g.flag, 6)) break;
+                c_phase ^= 1;
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int col = 32 * half + q;
+                // 128-byte swizzle: 16-byte chunk index XOR (row % 8)
+                const int box = col >> 4, jj = col & 15;
+                long long* cp = (long long*)(ctile + box * kCBox + r * 128 +
+                                             ((((jj >> 1) ^ (r & 7)) << 4) | ((jj & 1) << 3)));
+                if (g.sub) *cp -= res[q];
+                else *cp = res[q];
+            }
+            fence_proxy_async();
             epi_bar();
             if (leader) {
                 for (int b = 0; b < 4; ++b) tma_store_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
                 bulk_commit();
             }
-            mbar_arrive(acce);
-            acc_phase ^= 1;
         }
         if (leader) bulk_wait0();
     }
@@ -460,7 +482,7 @@ __global__ void slice_rows_kernel(int rows, const long long* __restrict__ src, i
         float d[7];
         split_digits(round_shift(src[(int64_t)r * ld + lane + 32 * q], T - F), s, d);
         for (int a = 0; a < s; ++a)
-            dst[((int64_t)a * plane_rows + r) * K + lane + 32 * q] = __float2bfloat16_rn(d[a]);
+            dst[blk_off(a, r, lane + 32 * q, K, plane_rows)] = __float2bfloat16_rn(d[a]);
     }
 }
 
@@ -504,7 +526,7 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
             float d[7];
             split_digits(round_shift(v[q], T - e - F), s, d);
             for (int a = 0; a < s; ++a)
-                dst[((int64_t)a * plane_rows + col) * K + lane + 32 * q] = __float2bfloat16_rn(d[a]);
+                dst[blk_off(a, col, lane + 32 * q, K, plane_rows)] = __float2bfloat16_rn(d[a]);
         }
     }
 }
@@ -534,7 +556,7 @@ __global__ void slice_f64_kernel(const double* __restrict__ src, int s, int plan
         float d[7];
         split_digits(llrint(ldexp(v[q], T - e)), s, d);
         for (int a = 0; a < s; ++a)
-            dst[((int64_t)a * plane_rows + r) * kNB + lane + 32 * q] = __float2bfloat16_rn(d[a]);
+            dst[blk_off(a, r, lane + 32 * q, kNB, plane_rows)] = __float2bfloat16_rn(d[a]);
     }
 }
 
@@ -663,19 +685,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Digit planes: [s * plane_rows][K] bf16, box 16 x box_rows, 32-byte swizzle.
-bool make_digit_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t plane_rows, int K, int box_rows) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)(s * plane_rows)};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, buf, dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // int64 result matrix rows x cols (row stride ld elements), box 16 x 128, 128-byte swizzle.
 bool make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, int64_t ld) {
     auto fn = encode_fn();
@@ -718,9 +727,8 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     g.M = M; g.N = N; g.plane_rows = (int)c.Np; g.a_row0 = a_row0; g.b_row0 = b_row0;
     g.c_x0 = c_x0; g.c_y0 = c_y0; g.lower = lower; g.sub = sub; g.shift0 = Fc - 14;
     g.expA = expA; g.expB = expB; g.stages = pick_stages(st.s); g.flag = c.d_flag;
-    const int ki = K == 256 ? 1 : 0;
-    const CUtensorMap& mA = st.dig[ba][ki][0];
-    const CUtensorMap& mB = st.dig[bb][ki][1];
+    g.digA = ba == BUF_P ? st.digP : st.digQ;
+    g.digB = bb == BUF_P ? st.digP : st.digQ;
     const int64_t ntiles = tile_count(M / kBM, N / kBN, lower);
     const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
     if (grid < 1) return;
@@ -728,7 +736,7 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     const double flops = (double)ntiles * 2.0 * kBM * kBN * K * (st.s * (st.s + 1) / 2);
     const size_t smem = gemm_smem(st.s, g.stages);
     prof_begin(c);
-#define CCOV_OZ(S_, K_) ozaki_gemm_kernel<S_, K_><<<grid, kThreads, smem, c.stream>>>(mA, mB, mapC, g)
+#define CCOV_OZ(S_, K_) ozaki_gemm_kernel<S_, K_><<<grid, kThreads, smem, c.stream>>>(mapC, g)
     if (K == 256) {
         switch (st.s) {
             case 4: CCOV_OZ(4, 256); break;
@@ -807,12 +815,6 @@ cudaError_t mixed_alloc(Ctx& c) {
     if ((e = cudaMemsetAsync(st.digP, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(st.digQ, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
-    __nv_bfloat16* bufs[2] = {st.digP, st.digQ};
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 2; ++k)
-            for (int r = 0; r < 2; ++r)
-                if (!make_digit_map(&st.dig[b][k][r], bufs[b], st.s, Np, k ? 256 : 128, r ? kBN : kBM))
-                    return cudaErrorInvalidValue;
     if (c.d_Z && !make_c_map(&st.mapZ, reinterpret_cast<long long*>(c.d_Z), Np, Np, Np)) return cudaErrorInvalidValue;
     if (!make_c_map(&st.mapR, st.R, Np, Np, Np)) return cudaErrorInvalidValue;
     cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
@@ -936,7 +938,7 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
     Ctx c;
     c.opt.mixed_slices = s;
     c.opt.precision = CCOV_PREC_MIXED;
-    c.Np = M > N ? M : N;
+    c.Np = ((M > N ? M : N) + 127) / 128 * 128;
     c.N = c.Np;
     if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) return CCOV_ERR_CUDA;
     ccov_status st = CCOV_OK;
@@ -948,11 +950,18 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
         MixedState& ms = *c.mixed;
         if (cudaMalloc(&c.d_flag, 2 * sizeof(int)) != cudaSuccess) { st = CCOV_ERR_OOM; break; }
         cudaMemset(c.d_flag, 0, 2 * sizeof(int));
-        for (int a = 0; a < s; ++a) {
-            cudaMemcpy(ms.digP + (size_t)a * c.Np * K, digA + (size_t)a * M * K, (size_t)M * K * 2,
-                       cudaMemcpyHostToDevice);
-            cudaMemcpy(ms.digQ + (size_t)a * c.Np * K, digB + (size_t)a * N * K, (size_t)N * K * 2,
-                       cudaMemcpyHostToDevice);
+        {
+            // row-major planes from the caller -> the tensor-core block layout
+            std::vector<uint16_t> ha((size_t)s * c.Np * K, 0), hb((size_t)s * c.Np * K, 0);
+            for (int a = 0; a < s; ++a)
+                for (int r = 0; r < c.Np; ++r)
+                    for (int k = 0; k < K; ++k) {
+                        const int64_t o = blk_off(a, r, k, K, (int)c.Np);
+                        if (r < M) ha[o] = digA[((size_t)a * M + r) * K + k];
+                        if (r < N) hb[o] = digB[((size_t)a * N + r) * K + k];
+                    }
+            cudaMemcpy(ms.digP, ha.data(), ha.size() * 2, cudaMemcpyHostToDevice);
+            cudaMemcpy(ms.digQ, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice);
         }
         if (expA) { cudaMalloc(&dEA, M * sizeof(int)); cudaMemcpy(dEA, expA, M * sizeof(int), cudaMemcpyHostToDevice); }
         if (expB) { cudaMalloc(&dEB, N * sizeof(int)); cudaMemcpy(dEB, expB, N * sizeof(int), cudaMemcpyHostToDevice); }
