@@ -165,6 +165,30 @@ CCOV_API ccov_status ccov_get_blocks(ccov_ctx* ctx, double* U, double* A_inv, do
 CCOV_API ccov_status ccov_get_schur(ccov_ctx* ctx, double* Z, double* G, double* W7);
 
 CCOV_API ccov_status ccov_get_stats(const ccov_ctx* ctx, ccov_stats* out);
+
+/* Allocation-free entry point (the paper has no counterpart).  For callers that
+ * cannot call cudaMalloc: a real-time loop that must not allocate, or code in a
+ * process whose device memory is owned by another allocator (a framework's
+ * caching allocator that has reserved it), where a cudaMalloc may fail or stall
+ * the device.  Returns the 9x9 diagonal blocks of A^-1 for a symmetric positive
+ * definite A with the FP64 kernels of step (d) (Jacobi scaling, blocked Cholesky,
+ * triangular inverse, diagonal Gram blocks); all workspace lives in one static
+ * device array of the library (7.9 MB, held on every GPU that loads the library
+ * until the process exits).  Nothing is allocated by the call.
+ *   A       device, N x N row-major, leading dimension lda >= N; only the lower
+ *           triangle is read; not modified
+ *   N       a multiple of 9 and at most 576 (64 camera blocks); a larger N is
+ *           rejected with CCOV_ERR_INVALID_ARG
+ *   blocks  device, (N / 9) x 81 doubles (row-major 9 x 9 blocks), written
+ *   stream  a cudaStream_t, or NULL for the legacy default stream; the call
+ *           returns after the stream has finished its work
+ * The first call on a device (that device current) takes the array's address
+ * with cudaGetSymbolAddress and sets kernel attributes; it should come before
+ * any stream capture.  Every call shares the array and clears what must start
+ * at zero; calls that overlap on the GPU race on it.  DEGENERATE if A is not
+ * positive definite. */
+CCOV_API ccov_status ccov_spd_inverse_blocks_noalloc(const double* A, int64_t lda, int64_t N, double* blocks,
+                                                     void* stream);
 CCOV_API void ccov_destroy(ccov_ctx* ctx);
 CCOV_API const char* ccov_status_string(ccov_status s);
 /* Message of the last failure on this context ("" if none). */

@@ -26,7 +26,8 @@ CCOV_NULL_PAPER, CCOV_NULL_CLOSED = 0, 1
 
 EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_nullspace",
             "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_stats",
-            "ccov_destroy", "ccov_status_string", "ccov_last_error"]
+            "ccov_destroy", "ccov_status_string", "ccov_last_error",
+            "ccov_spd_inverse_blocks_noalloc"]
 
 
 class CcovError(RuntimeError):
@@ -79,6 +80,7 @@ def load() -> C.CDLL:
         "ccov_status_string": ([I], C.c_char_p),
         "ccov_last_error": ([P], C.c_char_p),
         "ccov_test_ozaki_gemm": ([I, I, I, I, P, P, P, P, I, I, I, P], I),
+        "ccov_spd_inverse_blocks_noalloc": ([P, I64, I64, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
