@@ -21,8 +21,8 @@ extern "C" {
  *         sub = 1: C -= A B^T, sub = 0: C = A B^T; products of digit orders
  *         a + b > s - 1 are left out
  *   lower 1: only tiles of 128 x 64 that reach the diagonal (M == N)
- * M must be a multiple of 128 and N of 64.  Returns TIMEOUT if a bounded
- * device wait gave up. */
+ * M and N must be multiples of 128 (tiles of 128 x 64 are worked on in pairs
+ * by two-CTA clusters).  Returns TIMEOUT if a bounded device wait gave up. */
 CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N, const uint16_t* digA, const int* expA,
                                           const uint16_t* digB, const int* expB, int Fc, int sub, int lower,
                                           long long* C);

@@ -68,6 +68,7 @@ struct Ctx {
     int64_t bytes = 0;
     int64_t launches = 0;
     MixedState* mixed = nullptr;
+    bool mixed_bad_launch = false;  // a GEMM launch was refused (odd tile count)
 
     cudaEvent_t ev[8] = {};
     ccov_stats stats{};

@@ -147,6 +147,27 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr) {
     return d;
 }
 
+// Bulk copy delivered to the same shared-memory offset (and barrier) of every
+// CTA of the cluster in `mask`.
+__device__ __forceinline__ void bulk_load_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
@@ -162,6 +183,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
         ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Commit arriving on the barrier at this offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+        ::"r"(smem_u32(bar)), "h"(mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -184,19 +213,20 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Accumulator slots of the digit orders: order g has g + 1 digit products;
-// at most 1024 / K of them share one fp32 accumulator exactly.
+// Accumulators of the digit orders.  Order g = a + b collects the products
+// A_a B_b^T; at most cap = 1024 / K of them sum exactly in one fp32
+// accumulator.  Products of A planes a < cap go to the main accumulator of
+// their order (TMEM columns 64 g), those of planes a >= cap to a second one
+// (columns 64 (S + g - cap)).  With the B planes side by side in shared
+// memory, plane a then meets all B planes in one MMA of N = 64 (S - a)
+// (split at N = 256), whose output columns land on the orders a .. S-1.
 template <int S, int K>
 struct Slots {
     static constexpr int cap = 1024 / K;
-    static constexpr int count(int g) { return (g + 1 + cap - 1) / cap; }
-    static constexpr int first(int g) {
-        int f = 0;
-        for (int x = 0; x < g; ++x) f += count(x);
-        return f;
-    }
-    static constexpr int total = first(S);
+    static constexpr int extra = S > cap ? S - cap : 0;
+    static constexpr int total = S + extra;
     static_assert(total * kBN <= 512, "TMEM columns");
+    static_assert(S <= 2 * cap, "two accumulator levels at most");
 };
 
 // Tile schedule: M tiles of 128 rows x N tiles of 64 columns; `lower` keeps
@@ -252,8 +282,10 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
     return (p + (1ll << (-sh - 1))) >> (-sh);
 }
 
-// Persistent warp-specialised kernel.  Warp 0 lane 0: TMA producer of the
-// digit tiles.  Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps
+// Persistent warp-specialised kernel, launched in clusters of two CTAs that
+// work on the two halves (adjacent 64-column tiles) of one 128 x 128 block:
+// they need the same A tile, and each CTA loads half of its digit planes and
+// multicasts them to both.  Warp 0 lane 0: producer of the digit tiles.  Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps
 // 2..9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one half of
 // the 64 columns, and the result tile goes through shared memory with TMA
 // (load of C overlapped with the MMAs of the same tile, store asynchronous).
@@ -278,11 +310,17 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = g.N / kBN;
     const int64_t ntiles = tile_count(g.M / kBM, tiles_n, g.lower);
+    // tiles come in pairs (2P, 2P + 1) in one row of tiles; CTA `rank` of the
+    // cluster takes tile 2P + rank of every pair P of its cluster
+    const uint32_t rank = cluster_rank();
+    const int64_t npairs = ntiles / 2;
+    const int64_t pair0 = blockIdx.x >> 1, pair_step = gridDim.x >> 1;
+    constexpr uint16_t kBoth = 0x3;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < g.stages; ++i) {
             mbar_init(full + i, 1);
-            mbar_init(empty + i, 1);
+            mbar_init(empty + i, 2);  // released by the MMAs of both CTAs
         }
         mbar_init(accf, 1);
         mbar_init(acce, 32 * kEpiWarps);
@@ -297,6 +335,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -305,7 +344,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int64_t pr = pair0; pr < npairs && ok; pr += pair_step) {
+                const int64_t t = 2 * pr + rank;
                 int ti, tj;
                 tile_coords(t, tiles_n, g.lower, ti, tj);
                 for (int ks = 0; ks < K / kKS; ++ks) {
@@ -314,8 +354,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
                     mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
 #pragma unroll
                     for (int p = 0; p < S; ++p) {
-                        bulk_load(st + p * kAPl, g.digA + blk_off(p, g.a_row0 + ti * kBM, ks * kKS, K, g.plane_rows),
-                                  kAPl, full + stage);
+                        if ((p & 1) == (int)rank)  // A: half of the planes each, to both CTAs
+                            bulk_load_mc(st + p * kAPl,
+                                         g.digA + blk_off(p, g.a_row0 + ti * kBM, ks * kKS, K, g.plane_rows), kAPl,
+                                         full + stage, kBoth);
                         bulk_load(st + S * kAPl + p * kBPl,
                                   g.digB + blk_off(p, g.b_row0 + tj * kBN, ks * kKS, K, g.plane_rows), kBPl,
                                   full + stage);
@@ -329,8 +371,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
             int stage = 0;
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true, issued = false;
-            constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+
+            for (int64_t pr = pair0; pr < npairs && ok; pr += pair_step) {
                 if (!mbar_wait(acce, acc_phase ^ 1, g.flag, 2)) break;
                 tc_fence_after();
                 for (int ks = 0; ks < K / kKS; ++ks) {
@@ -338,23 +380,22 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
                     tc_fence_after();
                     const uint32_t sa = smem_u32(tiles + stage * stage_bytes);
                     const uint32_t sb = sa + S * kAPl;
+                    const uint64_t dA0 = smem_desc_kmajor(sa), dB0 = smem_desc_kmajor(sb);
 #pragma unroll
-                    for (int gi = 0; gi < S; ++gi) {
+                    for (int a = 0; a < S; ++a) {
+                        const bool second = a >= SL::cap;
+                        const int slot0 = second ? S + a - SL::cap : a;  // accumulator of order a
+                        const int first_a = second ? SL::cap : 0;
 #pragma unroll
-                        for (int k = 0; k < SL::count(gi); ++k) {
-                            const int slot = SL::first(gi) + k;
-                            const int a0 = k * SL::cap;
-                            const int a1 = (k + 1) * SL::cap - 1 < gi ? (k + 1) * SL::cap - 1 : gi;
-#pragma unroll
-                            for (int a = a0; a <= a1; ++a) {
-                                const int b = gi - a;
-                                mma_bf16(tmem + (uint32_t)(slot * kBN), smem_desc_kmajor(sa + a * kAPl),
-                                         smem_desc_kmajor(sb + b * kBPl), idesc, (ks == 0 && a == a0) ? 0 : 1);
-                                issued = true;
-                            }
+                        for (int c = 0; 4 * c < S - a; ++c) {
+                            const int nb = (S - a - 4 * c) < 4 ? (S - a - 4 * c) : 4;  // B planes in this MMA
+                            mma_bf16(tmem + (uint32_t)((slot0 + 4 * c) * kBN), dA0 + (uint64_t)(a * (kAPl >> 4)),
+                                     dB0 + (uint64_t)(4 * c * (kBPl >> 4)), idesc_bf16(kBM, kBN * nb),
+                                     (ks == 0 && a == first_a) ? 0 : 1);
+                            issued = true;
                         }
                     }
-                    mma_commit(empty + stage);
+                    mma_commit_mc(empty + stage, kBoth);  // both producers write this stage
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
                 if (!ok) break;
@@ -373,7 +414,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
         const int r = 32 * quarter + lane;  // row in the tile = TMEM lane
         const bool leader = (warp == 2 && lane == 0);
         uint32_t acc_phase = 0, c_phase = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int64_t pr = pair0; pr < npairs; pr += pair_step) {
+            const int64_t t = 2 * pr + rank;
             int ti, tj;
             tile_coords(t, tiles_n, g.lower, ti, tj);
             const int cx = g.c_x0 + tj * kBN, cy = g.c_y0 + ti * kBM;
@@ -402,15 +444,16 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int eB = g.expB ? g.expB[g.b_row0 + tj * kBN + col0 + j] : 0;
-                    const int sh0 = eA + eB + g.shift0;
-                    long long acc = 0;
+                    // T = sum_g P_g 2^(8 (S-1-g)) exactly (|T| < 2^63), then one
+                    // rounding shift to the fixed point of C
+                    long long T = 0;
 #pragma unroll
                     for (int gi = 0; gi < S; ++gi) {
-                        int p = __float2int_rn(v[SL::first(gi)][j]);
-                        if (SL::count(gi) > 1) p += __float2int_rn(v[SL::first(gi) + 1][j]);
-                        acc += shift_round((long long)p, sh0 - 8 * gi);
+                        int p = __float2int_rn(v[gi][j]);
+                        if (gi >= SL::cap) p += __float2int_rn(v[S + gi - SL::cap][j]);
+                        T = (long long)((unsigned long long)T << 8) + p;
                     }
-                    res[8 * cc + j] = acc;
+                    res[8 * cc + j] = shift_round(T, eA + eB + g.shift0 - 8 * (S - 1));
                 }
             }
             tc_fence_before();
@@ -442,6 +485,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
     }
     tc_fence_before();
     __syncthreads();
+    __syncwarp();
+    cluster_sync();  // no multicast or remote arrival is still aimed at this CTA
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -729,14 +774,31 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     g.expA = expA; g.expB = expB; g.stages = pick_stages(st.s); g.flag = c.d_flag;
     g.digA = ba == BUF_P ? st.digP : st.digQ;
     g.digB = bb == BUF_P ? st.digP : st.digQ;
-    const int64_t ntiles = tile_count(M / kBM, N / kBN, lower);
-    const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
-    if (grid < 1) return;
+    const int64_t ntiles = tile_count(M / kBM, N / kBN, lower);  // even: pairs of tiles
+    if ((ntiles & 1) || (N % (2 * kBN))) {
+        c.mixed_bad_launch = true;  // cannot happen with N a multiple of 128
+        return;
+    }
+    const int64_t npairs = ntiles / 2;
+    const int grid = 2 * (int)(npairs < g_num_sms / 2 ? npairs : g_num_sms / 2);
+    if (grid < 2) return;
     // executed tensor-core work: every kept tile, every digit product
     const double flops = (double)ntiles * 2.0 * kBM * kBN * K * (st.s * (st.s + 1) / 2);
     const size_t smem = gemm_smem(st.s, g.stages);
     prof_begin(c);
-#define CCOV_OZ(S_, K_) ozaki_gemm_kernel<S_, K_><<<grid, kThreads, smem, c.stream>>>(mapC, g)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_>, mapC, g)
     if (K == 256) {
         switch (st.s) {
             case 4: CCOV_OZ(4, 256); break;
@@ -920,6 +982,7 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_Q, 0, (int)nc, st.mapR, 0, (int)(kq + kNB), 0, 1, kFX,
                      nullptr, st.expQ);
     }
+    if (c.mixed_bad_launch) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -931,8 +994,8 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
                                                     const int* expA, const uint16_t* digB, const int* expB,
                                                     int Fc, int sub, int lower, long long* C) {
     using namespace ccov;
-    if (s < 4 || s > 6 || (K != 128 && K != 256) || M <= 0 || N <= 0 || M % kBM || N % kBN || !digA || !digB ||
-        !C)
+    if (s < 4 || s > 6 || (K != 128 && K != 256) || M <= 0 || N <= 0 || M % kBM || N % (2 * kBN) || !digA ||
+        !digB || !C)
         return CCOV_ERR_INVALID_ARG;
     if (lower && N != M) return CCOV_ERR_INVALID_ARG;
     Ctx c;
@@ -973,6 +1036,7 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
         // wait for them by itself
         if (cudaDeviceSynchronize() != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         launch_ozaki(c, K, BUF_P, 0, M, BUF_Q, 0, N, mapC, 0, 0, lower, sub, Fc, dEA, dEB);
+        if (c.mixed_bad_launch) { st = CCOV_ERR_INVALID_ARG; break; }
         if (cudaStreamSynchronize(c.stream) != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         int flag[2];
         cudaMemcpy(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost);

@@ -20,19 +20,24 @@ def _bf16_bits(d):
 
 
 def _expected(dA, eA, dB, eB, s, Fc, sub, lower, C0):
+    """Integer definition of the kernel's result: T = sum_g P_g 2^(8 (s-1-g)),
+    P_g = sum_{a+b=g} A_a B_b^T (exact), shifted once to Q(Fc) with the row
+    and column exponents (round half up on right shifts, wrap-around on left)."""
     M, N = dA.shape[1], dB.shape[1]
-    S = np.zeros((M, N), dtype=np.int64)
+    T = np.zeros((M, N), dtype=np.int64)
     for g in range(s):
         P = np.zeros((M, N), dtype=np.int64)
         for a in range(g + 1):
             P += dA[a] @ dB[g - a].T
-        sh = eA[:, None] + eB[None, :] + Fc - 14 - 8 * g
-        pos = sh >= 0
         with np.errstate(over="ignore"):
-            left = P << np.where(pos, sh, 0)
-            rs = np.where(pos, 0, -sh)
-            right = (P + (np.int64(1) << np.maximum(rs - 1, 0))) >> rs
-            S += np.where(pos, left, np.where(rs > 0, right, P))
+            T = (T << 8) + P
+    sh = eA[:, None] + eB[None, :] + Fc - 14 - 8 * (s - 1)
+    pos = sh >= 0
+    with np.errstate(over="ignore"):
+        left = T << np.where(pos, sh, 0)
+        rs = np.where(pos, 0, -sh)
+        right = (T + (np.int64(1) << np.maximum(rs - 1, 0))) >> rs
+        S = np.where(pos, left, np.where(rs > 0, right, T))
     out = C0 - S if sub else S
     if lower:
         ti = np.arange(M)[:, None] // 128
@@ -62,14 +67,14 @@ def _run(s, M, N, Fc, sub, lower, seed, with_exp=True, K=128):
 @pytest.mark.parametrize("s", [4, 5, 6])
 @pytest.mark.parametrize("K", [128, 256])
 def test_ozaki_gemm_single_tile_bit_exact(s, K):
-    got, want = _run(s, 128, 64, 60, 1, 0, seed=s, with_exp=False, K=K)
+    got, want = _run(s, 128, 128, 60, 1, 0, seed=s, with_exp=False, K=K)
     assert np.array_equal(got, want)
 
 
 def test_ozaki_gemm_extreme_digits_exact():
     """All digits +-128: the largest digit orders reach the fp32 exactness limit."""
     for K in (128, 256):
-        s, M, N = 6, 128, 64
+        s, M, N = 6, 128, 128
         dA = np.full((s, M, K), 128, dtype=np.int64)
         dB = np.full((s, N, K), -128, dtype=np.int64)
         C0 = np.zeros((M, N), dtype=np.int64)
@@ -84,7 +89,7 @@ def test_ozaki_gemm_extreme_digits_exact():
 
 @pytest.mark.parametrize("sub,Fc", [(1, 60), (0, 42)])
 def test_ozaki_gemm_with_exponents_bit_exact(sub, Fc):
-    got, want = _run(5, 256, 192, Fc, sub, 0, seed=11 + sub)
+    got, want = _run(5, 256, 384, Fc, sub, 0, seed=11 + sub)
     assert np.array_equal(got, want)
 
 
@@ -102,7 +107,7 @@ def test_ozaki_gemm_lower_tiles_bit_exact(K):
 
 
 def test_ozaki_gemm_overwrite_with_exponents_k256():
-    got, want = _run(5, 384, 320, 42, 0, 0, seed=21, K=256)
+    got, want = _run(5, 384, 256, 42, 0, 0, seed=21, K=256)
     assert np.array_equal(got, want)
 
 
