@@ -103,9 +103,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel_tag: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source has not changed since the capture (else None)."""
+def traffic_for(kernel_tag: str, flops_per_launch: float):
+    """DRAM bytes per launch from the committed ncu capture (bytes per executed
+    flop there, times this run's flops per launch: the result tile traffic grows
+    with the tiles, as the flops do), if the kernel source has not changed since
+    the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -119,7 +121,9 @@ def traffic_for(kernel_tag: str):
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return rec["dram_bytes_per_launch"] if h == rec["source_sha"] else None
+    if h != rec["source_sha"]:
+        return None
+    return rec["dram_bytes_per_flop"] * flops_per_launch
 
 
 def dist_init(n_gpus: int):
@@ -275,7 +279,7 @@ def run_ours(args):
         achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
         peak = FP64_NOMINAL_GFLOPS / 1e3
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for("gemm64"),
+                "frac": achieved / peak, "traffic": traffic_for("gemm64", gemm_flops / max(gemm_launches, 1)),
                 "kernel": "gemm64_kernel (FP64 trailing updates)", "peak_source": "nominal FP64",
                 "launches_per_step": gemm_launches, "ms_per_step": gemm_ms,
                 "share_of_step": gemm_ms / ms_step}
@@ -284,7 +288,7 @@ def run_ours(args):
         achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for("ozaki_gemm"),
+                "frac": achieved / peak, "traffic": traffic_for("ozaki_gemm", gemm_flops / max(gemm_launches, 1)),
                 "kernel": "ozaki_gemm (split-bf16 tcgen05 trailing updates)",
                 "peak_source": f"bf16 sustained ({src})", "launches_per_step": gemm_launches,
                 "ms_per_step": gemm_ms, "share_of_step": gemm_ms / ms_step}
