@@ -9,6 +9,12 @@ workload is the synthetic 4000-camera shell scene (400k points, track length
 `e2e` = the same through the C ABI with host buffers (host-to-device upload and
 the device-to-host copy of the 9x9 blocks inside every timed step).
 
+`--workload batch256` times the batched form instead: 256 independent
+sub-reconstructions (n ~ U{10..300} cameras, 100 points per camera, track
+length 1 + Geometric(0.2)), all four steps of every scene recorded once as a
+CUDA graph and replayed, one replay per step; `value` = cameras / s over the
+whole batch.
+
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
 instead, on a bounded sub-scene of the same workload.
 """
@@ -41,7 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="shell4k")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--cpu-sample-cams", type=int, default=150)
+    ap.add_argument("--cpu-sample-cams", type=int, default=800)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     return ap.parse_args()
@@ -323,10 +329,173 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+BATCH_K = 256
+
+
+def batch_workload():
+    from paper_1808_02414_gb300 import synth
+    return synth.batch_scenes(k=BATCH_K, n_lo=10, n_hi=300, pts_per_cam=100, p_geom=0.2)
+
+
+def cpu_oracle_batch_sample(scenes, budget_s: float = 12.0):
+    """The oracle as it stands on whole scenes of the batch, in batch order,
+    until about `budget_s` seconds of CPU work (a bounded sample)."""
+    from oracle import covariance
+    cams, t0 = 0, time.perf_counter()
+    used = 0
+    for sc in scenes:
+        covariance.camera_covariance(sc)
+        cams += sc.n
+        used += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return cams, used, time.perf_counter() - t0
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    from paper_1808_02414_gb300 import ccov
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scenes = batch_workload()
+    prec = ccov.CCOV_PREC_MIXED if args.precision == "mixed" else ccov.CCOV_PREC_FP64
+    stream = torch.cuda.current_stream(dev)
+    cams_total = sum(sc.n for sc in scenes)
+
+    # inputs resident in HBM; one context (and stream) per scene
+    ctxs, outs = [], []
+    for sc in scenes:
+        rec = sc.obs_records()
+        ctxs.append(ccov.Context(torch.from_numpy(sc.cams).to(dev), torch.from_numpy(sc.pts).to(dev),
+                                 torch.from_numpy(rec.view(np.uint8)).to(dev), sc.sigma,
+                                 precision=prec))
+        outs.append(torch.empty((sc.n, 9, 9), dtype=torch.float64, device=dev))
+    batch = ccov.Batch(ctxs, outs)
+    for _ in range(args.warmup):
+        batch.run(stream.cuda_stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.run(stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_total = barrier_max(e0.elapsed_time(e1), world)
+    ms_step = ms_total / args.steps
+    value = cams_total * args.steps * world / (ms_total / 1e3)
+    batch.close()
+
+    # the same batch without the graph: direct batched call, then scene by scene
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ccov.ccov_batch_covariance(ctxs, outs)
+    ms_direct = 1e3 * (time.perf_counter() - t0)
+    launches_per_step = sum(c.ccov_get_stats()["launches"] for c in ctxs)  # the graph's kernel nodes
+    t0 = time.perf_counter()
+    for c, o in zip(ctxs, outs):
+        c.run(out=o)
+    ms_serial = 1e3 * (time.perf_counter() - t0)
+
+    # GEMM roofline: one profiled direct pass (events bracket each GEMM launch
+    # while the other scenes run concurrently, so durations are upper bounds)
+    for c in ctxs:
+        c.close()
+    prof = []
+    for sc in scenes:
+        rec = sc.obs_records()
+        prof.append(ccov.Context(torch.from_numpy(sc.cams).to(dev), torch.from_numpy(sc.pts).to(dev),
+                                 torch.from_numpy(rec.view(np.uint8)).to(dev), sc.sigma,
+                                 precision=prec, profile=True))
+    ccov.ccov_batch_covariance(prof, outs)
+    st = [c.ccov_get_stats() for c in prof]
+    for c in prof:
+        c.close()
+    gemm_ms = sum(s["ms_gemm"] for s in st)
+    gemm_flops = sum(s["gemm_flops"] for s in st)
+    gemm_launches = sum(s["gemm_launches"] for s in st)
+    pk, src = peaks()
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
+    if prec == ccov.CCOV_PREC_FP64:
+        peak, bound, dtype, kern, psrc = FP64_NOMINAL_GFLOPS / 1e3, "alu", "f64", "gemm64_kernel", "nominal FP64"
+    else:
+        peak, bound, dtype = pk["bf16_tflops_sustained"], "tensor", "bf16"
+        kern, psrc = "ozaki_gemm (split-bf16 tcgen05 trailing updates)", f"bf16 sustained ({src})"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kern, "peak_source": psrc, "launches_per_step": gemm_launches,
+            "note": "per-launch event durations summed over 256 concurrently running scenes "
+                    "(overlap makes them upper bounds, frac a lower bound)"}
+
+    # end to end: host inputs loaded into every context, host outputs
+    pinned = []
+    e2e_ctx = []
+    for sc in scenes:
+        rec = sc.obs_records()
+        hc = torch.from_numpy(sc.cams).pin_memory()
+        hp = torch.from_numpy(sc.pts).pin_memory()
+        ho = torch.from_numpy(rec.view(np.uint8)).pin_memory()
+        pinned.append((hc.numpy(), hp.numpy(), ho.numpy().view(rec.dtype)))
+        e2e_ctx.append(ccov.Context(sc.cams, sc.pts, rec, sc.sigma, precision=prec))
+    h_outs = [torch.empty((sc.n, 9, 9), dtype=torch.float64).pin_memory().numpy() for sc in scenes]
+    ptrs = (__import__("ctypes").c_void_p * len(scenes))(*[o.ctypes.data for o in h_outs])
+    handles = ccov._handles(e2e_ctx)
+    h2d = sum(sc.cams.nbytes + sc.pts.nbytes + sc.t * 24 for sc in scenes)
+    d2h = cams_total * 81 * 8
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        for c, (a, b, o) in zip(e2e_ctx, pinned):
+            c.ccov_load(a, b, o)
+        ccov._first_error(e2e_ctx, ccov.load().ccov_batch_covariance(handles, len(scenes), ptrs,
+                                                                     ccov.CCOV_MEM_HOST))
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = barrier_max(f0.elapsed_time(f1), world) / args.e2e_steps
+    for c in e2e_ctx:
+        c.close()
+
+    line = {"metric": "camera covariances/s (batched sub-reconstructions)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic",
+            "config": {"workload": "batch256", "scenes": len(scenes), "cameras": cams_total,
+                       "points": sum(sc.m for sc in scenes), "observations": sum(sc.t for sc in scenes),
+                       "precision": args.precision, "form": "one CUDA graph replay per step",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set > L2: the reduced matrices total "
+                             f"{sum((9 * sc.n) ** 2 for sc in scenes) * 8 / 1e9:.1f} GB"},
+            "clocks": clk,
+            "e2e": {"value": cams_total * world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof,
+            "without_graph_ms": {"batched_call": ms_direct, "scene_by_scene": ms_serial}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cams, used, dt = cpu_oracle_batch_sample(scenes)
+        line["cpu_baseline"] = {"value": cams / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"the first {used} scenes of the batch ({cams} cameras), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -166,6 +166,37 @@ CCOV_API ccov_status ccov_get_schur(ccov_ctx* ctx, double* Z, double* G, double*
 
 CCOV_API ccov_status ccov_get_stats(const ccov_ctx* ctx, ccov_stats* out);
 
+/* Batched form, Sec. 5 (uncertainty for sub-reconstructions): the camera
+ * covariances of k independent scenes, e.g. the neighbourhoods of 100-300
+ * cameras into which a large reconstruction is decomposed.  Each ctxs[i] is a
+ * created context (its own scene, options and stream); the call runs steps
+ * (a)-(d) of every context without host synchronisation between them, so the
+ * scenes proceed concurrently on their streams, then waits for all of them.
+ *   ctxs        k contexts (k >= 1), each used by this call alone
+ *   outs        k buffers of n_i*81 float64, on the host or the device as
+ *               `out_memory` says
+ * Returns the first failing status in context order; every context's own
+ * status is left in its ccov_last_error.  Afterwards each context is in the
+ * state ccov_information leaves (its Z has been consumed). */
+CCOV_API ccov_status ccov_batch_covariance(ccov_ctx* const* ctxs, int k, double* const* outs, int out_memory);
+
+/* The same batch recorded once as a CUDA graph and replayed by ccov_batch_run
+ * with a single graph launch.  ccov_batch_create runs the batch once directly
+ * (validating the scenes and preparing every kernel), then captures steps
+ * (a)-(d) of all k contexts, forked from one stream onto the contexts' streams
+ * and joined back.  outs_device: k device buffers of n_i*81 float64 that each
+ * replay writes.  The contexts, their streams and the buffers must outlive the
+ * batch; between create and destroy the contexts belong to the batch (a direct
+ * call on one of them in between is allowed, but changes nothing in the
+ * graph).  Inputs may be replaced with ccov_load (same sizes, device copies
+ * happen on the context stream) and are picked up by the next replay.
+ * ccov_batch_run: stream = a cudaStream_t or NULL for the batch's own stream;
+ * returns after the replay has finished, with the first failing status. */
+typedef struct ccov_batch ccov_batch;
+CCOV_API ccov_status ccov_batch_create(ccov_ctx* const* ctxs, int k, double* const* outs_device, ccov_batch** out);
+CCOV_API ccov_status ccov_batch_run(ccov_batch* batch, void* stream);
+CCOV_API void ccov_batch_destroy(ccov_batch* batch);
+
 /* Allocation-free entry point (the paper has no counterpart).  For callers that
  * cannot call cudaMalloc: a real-time loop that must not allocate, or code in a
  * process whose device memory is owned by another allocator (a framework's

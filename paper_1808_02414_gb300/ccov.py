@@ -27,7 +27,8 @@ CCOV_NULL_PAPER, CCOV_NULL_CLOSED = 0, 1
 EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_nullspace",
             "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_stats",
             "ccov_destroy", "ccov_status_string", "ccov_last_error",
-            "ccov_spd_inverse_blocks_noalloc"]
+            "ccov_spd_inverse_blocks_noalloc", "ccov_batch_covariance", "ccov_batch_create",
+            "ccov_batch_run", "ccov_batch_destroy"]
 
 
 class CcovError(RuntimeError):
@@ -81,6 +82,10 @@ def load() -> C.CDLL:
         "ccov_last_error": ([P], C.c_char_p),
         "ccov_test_ozaki_gemm": ([I, I, I, I, P, P, P, P, I, I, I, P], I),
         "ccov_spd_inverse_blocks_noalloc": ([P, I64, I64, P, P], I),
+        "ccov_batch_covariance": ([P, I, P, I], I),
+        "ccov_batch_create": ([P, I, P, C.POINTER(C.c_void_p)], I),
+        "ccov_batch_run": ([P, P], I),
+        "ccov_batch_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -219,6 +224,65 @@ class Context:
 def from_scene(scene, **kw) -> Context:
     return Context(scene.cams, scene.pts, scene.obs_records(), scene.sigma,
                    None if scene.obs_cov is None else scene.obs_cov.reshape(-1, 4), **kw)
+
+
+def _handles(ctxs):
+    return (C.c_void_p * len(ctxs))(*[c._h.value for c in ctxs])
+
+
+def _first_error(ctxs, s: int):
+    if s != CCOV_OK:
+        L = load()
+        msgs = [L.ccov_last_error(c._h).decode() for c in ctxs]
+        raise CcovError(s, next((m for m in msgs if m), L.ccov_status_string(s).decode()))
+
+
+def ccov_batch_covariance(ctxs, outs=None):
+    """Steps (a)-(d) of every context in `ctxs`, all in flight at once.
+
+    Returns a list of (n_i, 9, 9) host arrays, or fills `outs` (CUDA tensors)."""
+    if outs is None:
+        host = [np.empty((c.n, 9, 9)) for c in ctxs]
+        ptrs = (C.c_void_p * len(ctxs))(*[_ptr(h) for h in host])
+        _first_error(ctxs, load().ccov_batch_covariance(_handles(ctxs), len(ctxs), ptrs, CCOV_MEM_HOST))
+        return host
+    ptrs = (C.c_void_p * len(ctxs))(*[_ptr(o) for o in outs])
+    _first_error(ctxs, load().ccov_batch_covariance(_handles(ctxs), len(ctxs), ptrs, CCOV_MEM_DEVICE))
+    return outs
+
+
+class Batch:
+    """ccov_batch: a batch of contexts recorded once as a CUDA graph."""
+
+    def __init__(self, ctxs, outs_device):
+        self._ctxs = list(ctxs)
+        self._outs = list(outs_device)  # kept alive: the graph writes into them
+        ptrs = (C.c_void_p * len(ctxs))(*[_ptr(o) for o in self._outs])
+        h = C.c_void_p()
+        s = load().ccov_batch_create(_handles(self._ctxs), len(self._ctxs), ptrs, C.byref(h))
+        self._h = h
+        _first_error(self._ctxs, s)
+
+    def run(self, stream=None):
+        _first_error(self._ctxs, load().ccov_batch_run(self._h, stream))
+        return self._outs
+
+    def close(self):
+        if self._h:
+            load().ccov_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def camera_covariances(scene, **kw) -> np.ndarray:

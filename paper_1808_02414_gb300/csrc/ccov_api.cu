@@ -163,7 +163,7 @@ ccov_status upload(Ctx& c, const double* cams, const double* pts, const ccov_obs
 
 namespace ccov {
 void prof_begin(Ctx& c) {
-    if (!c.opt.profile) return;
+    if (!c.opt.profile || c.capturing) return;
     while (c.prof_ev.size() < c.prof_used + 2) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -172,7 +172,7 @@ void prof_begin(Ctx& c) {
     cudaEventRecord(c.prof_ev[c.prof_used], c.stream);
 }
 void prof_end(Ctx& c, double flops) {
-    if (!c.opt.profile || c.prof_ev.size() < c.prof_used + 2) return;
+    if (!c.opt.profile || c.capturing || c.prof_ev.size() < c.prof_used + 2) return;
     cudaEventRecord(c.prof_ev[c.prof_used + 1], c.stream);
     c.prof_used += 2;
     c.prof_flops += flops;
@@ -321,59 +321,44 @@ ccov_status ccov_load(ccov_ctx* h, const double* cameras, const double* points, 
     return CCOV_OK;
 }
 
-ccov_status ccov_information(ccov_ctx* h) {
-    if (!h) return CCOV_ERR_INVALID_ARG;
-    Ctx& c = h->c;
-    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_information: context not created");
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch-only halves of the four steps: no host synchronisation, so that the
+// batched form can run many contexts concurrently or capture them in a graph.
+// Device-side errors land in the sticky flag and are read by check_device.
+namespace {
+
+void rec(Ctx& c, int i) {
+    if (!c.capturing) cudaEventRecord(c.ev[i], c.stream);
+}
+
+ccov_status enq_information(Ctx& c) {
     c.launches = 0;
-    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+    CK(cudaMemsetAsync(c.d_flag, 0, 2 * sizeof(int), c.stream), "memset flag");
     ccov::launch_cam_prep(c);
     ccov::launch_point_info(c);
     ccov::launch_cam_info(c);
     CK(cudaGetLastError(), "ccov_information launch");
-    CK(cudaEventRecord(c.ev[1], c.stream), "event");
-    ccov_status s = check_device(c, "ccov_information");
-    if (s != CCOV_OK) return s;
-    c.stats.ms_information = elapsed(c, 0, 1);
-    c.stage = 2;
     return CCOV_OK;
 }
 
-ccov_status ccov_schur(ccov_ctx* h) {
-    if (!h) return CCOV_ERR_INVALID_ARG;
-    Ctx& c = h->c;
-    if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_schur: call ccov_information first");
-    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+ccov_status enq_schur(Ctx& c) {
     CK(cudaMemsetAsync(c.d_Z, 0, sizeof(double) * c.Np * c.Np, c.stream), "memset Z");
     CK(cudaMemsetAsync(c.d_W7, 0, sizeof(double) * 128, c.stream), "memset W7");
     ccov::launch_schur(c);
     CK(cudaGetLastError(), "ccov_schur launch");
-    CK(cudaEventRecord(c.ev[1], c.stream), "event");
-    ccov_status s = check_device(c, "ccov_schur");
-    if (s != CCOV_OK) return s;
-    c.stats.ms_schur = elapsed(c, 0, 1);
-    c.stage = 3;
     return CCOV_OK;
 }
 
-ccov_status ccov_nullspace(ccov_ctx* h, double* H_P_out) {
-    if (!h) return CCOV_ERR_INVALID_ARG;
-    Ctx& c = h->c;
-    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_nullspace: context not created");
-    CK(cudaEventRecord(c.ev[0], c.stream), "event");
-    if (c.stage < 2) ccov::launch_cam_prep(c);
+ccov_status enq_nullspace(Ctx& c, bool prep) {
+    if (prep) ccov::launch_cam_prep(c);
     ccov::launch_nullspace(c);
     CK(cudaGetLastError(), "ccov_nullspace launch");
-    CK(cudaEventRecord(c.ev[1], c.stream), "event");
-    ccov_status s = check_device(c, "ccov_nullspace");
-    if (s != CCOV_OK) return s;
-    c.stats.ms_nullspace = elapsed(c, 0, 1);
-    if (H_P_out) CK(cudaMemcpy(H_P_out, c.d_HP, sizeof(double) * 63 * c.n, cudaMemcpyDeviceToHost), "copy H_P");
-    c.null_done = true;
     return CCOV_OK;
 }
 
-static ccov_status factor_inverse_fp64(Ctx& c) {
+ccov_status factor_inverse_fp64(Ctx& c) {
     using ccov::kNB;
     const int64_t Np = c.Np, nb = Np / kNB;
     for (int64_t kb = 0; kb < nb; ++kb) {
@@ -394,7 +379,7 @@ static ccov_status factor_inverse_fp64(Ctx& c) {
             ccov::prof_end(c, (double)rem * (rem + 1) * kNB);
         }
     }
-    CK(cudaEventRecord(c.ev[3], c.stream), "event");
+    rec(c, 3);
     CK(cudaMemsetAsync(c.d_R, 0, sizeof(double) * Np * Np, c.stream), "memset R");
     ccov::launch_init_identity(c, c.d_R, Np);
     for (int64_t kb = 0; kb < nb; ++kb) {
@@ -411,35 +396,30 @@ static ccov_status factor_inverse_fp64(Ctx& c) {
     return CCOV_OK;
 }
 
-ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* est_rel_err) {
-    if (!h) return CCOV_ERR_INVALID_ARG;
-    Ctx& c = h->c;
-    if (c.stage < 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_schur first");
-    if (!c.null_done) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_nullspace first");
-    if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
-        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
-    CK(cudaEventRecord(c.ev[0], c.stream), "event");
+ccov_status enq_covariance(Ctx& c, double* out, int out_memory) {
     ccov::launch_form_scaled(c);
     CK(cudaGetLastError(), "ccov_covariance launch");
-    ccov_status s = check_device(c, "ccov_covariance (Z')");
-    if (s != CCOV_OK) return s;
-    CK(cudaEventRecord(c.ev[2], c.stream), "event");
+    rec(c, 2);
     CK(cudaMemsetAsync(c.d_Sig, 0, sizeof(double) * 81 * c.n, c.stream), "memset");
     c.prof_used = 0;
     c.prof_flops = 0.0;
     if (c.opt.precision == CCOV_PREC_FP64) {
-        s = factor_inverse_fp64(c);
+        ccov_status s = factor_inverse_fp64(c);
+        if (s != CCOV_OK) return s;
     } else {
         cudaError_t e = ccov::mixed_factor_inverse(c);
         if (e != cudaSuccess) return cuda_fail(&c, e, "mixed path");
     }
-    if (s != CCOV_OK) return s;
     ccov::launch_extract(c);
     CK(cudaGetLastError(), "ccov_covariance launch");
-    CK(cudaEventRecord(c.ev[1], c.stream), "event");
-    s = check_device(c, "ccov_covariance");
-    c.stage = 2;  // Z has been consumed in place
-    if (s != CCOV_OK) return s;
+    if (out) {
+        cudaMemcpyKind k = out_memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(out, c.d_Sig, sizeof(double) * 81 * c.n, k, c.stream), "copy out");
+    }
+    return CCOV_OK;
+}
+
+void covariance_stats(Ctx& c) {
     c.stats.ms_covariance = elapsed(c, 0, 1);
     c.stats.ms_factor = elapsed(c, 2, 3);
     c.stats.ms_inverse = elapsed(c, 3, 1);
@@ -455,10 +435,73 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
         c.stats.gemm_flops = c.prof_flops;
         c.stats.gemm_launches = (int64_t)(c.prof_used / 2);
     }
-    if (out) {
-        cudaMemcpyKind k = out_memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        CK(cudaMemcpy(out, c.d_Sig, sizeof(double) * 81 * c.n, k), "copy out");
-    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ccov_status ccov_information(ccov_ctx* h) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_information: context not created");
+    rec(c, 0);
+    ccov_status s = enq_information(c);
+    if (s != CCOV_OK) return s;
+    rec(c, 1);
+    s = check_device(c, "ccov_information");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_information = elapsed(c, 0, 1);
+    c.stage = 2;
+    return CCOV_OK;
+}
+
+ccov_status ccov_schur(ccov_ctx* h) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_schur: call ccov_information first");
+    rec(c, 0);
+    ccov_status s = enq_schur(c);
+    if (s != CCOV_OK) return s;
+    rec(c, 1);
+    s = check_device(c, "ccov_schur");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_schur = elapsed(c, 0, 1);
+    c.stage = 3;
+    return CCOV_OK;
+}
+
+ccov_status ccov_nullspace(ccov_ctx* h, double* H_P_out) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_nullspace: context not created");
+    rec(c, 0);
+    ccov_status s = enq_nullspace(c, c.stage < 2);
+    if (s != CCOV_OK) return s;
+    rec(c, 1);
+    s = check_device(c, "ccov_nullspace");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_nullspace = elapsed(c, 0, 1);
+    if (H_P_out) CK(cudaMemcpy(H_P_out, c.d_HP, sizeof(double) * 63 * c.n, cudaMemcpyDeviceToHost), "copy H_P");
+    c.null_done = true;
+    return CCOV_OK;
+}
+
+ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* est_rel_err) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_schur first");
+    if (!c.null_done) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_nullspace first");
+    if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
+    rec(c, 0);
+    ccov_status s = enq_covariance(c, out, out_memory);
+    c.stage = 2;  // Z is consumed in place
+    if (s != CCOV_OK) return s;
+    rec(c, 1);
+    s = check_device(c, "ccov_covariance");
+    if (s != CCOV_OK) return s;
+    covariance_stats(c);
     if (est_rel_err) {
         if (c.opt.precision == CCOV_PREC_FP64) {
             for (int64_t i = 0; i < c.n; ++i) est_rel_err[i] = 0.0;
@@ -468,6 +511,130 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     }
     return CCOV_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent scenes (sub-reconstructions, Sec. 5).
+static ccov_status batch_check_args(ccov_ctx* const* ctxs, int k, double* const* outs) {
+    if (!ctxs || !outs || k < 1) return CCOV_ERR_INVALID_ARG;
+    for (int i = 0; i < k; ++i) {
+        if (!ctxs[i] || !outs[i]) return CCOV_ERR_INVALID_ARG;
+        if (ctxs[i]->c.stage < 1) return fail(&ctxs[i]->c, CCOV_ERR_INVALID_ARG, "batch: context not created");
+    }
+    return CCOV_OK;
+}
+
+static ccov_status batch_enqueue(Ctx& c, double* out, int out_memory) {
+    rec(c, 0);
+    ccov_status s = enq_information(c);
+    if (s == CCOV_OK) s = enq_schur(c);
+    if (s == CCOV_OK) s = enq_nullspace(c, false);
+    if (s == CCOV_OK) s = enq_covariance(c, out, out_memory);
+    rec(c, 1);
+    return s;
+}
+
+ccov_status ccov_batch_covariance(ccov_ctx* const* ctxs, int k, double* const* outs, int out_memory) {
+    ccov_status s = batch_check_args(ctxs, k, outs);
+    if (s != CCOV_OK) return s;
+    if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE) return CCOV_ERR_INVALID_ARG;
+    for (int i = 0; i < k; ++i) {
+        s = batch_enqueue(ctxs[i]->c, outs[i], out_memory);
+        if (s != CCOV_OK) return s;
+    }
+    ccov_status first = CCOV_OK;
+    for (int i = 0; i < k; ++i) {
+        Ctx& c = ctxs[i]->c;
+        ccov_status si = check_device(c, "ccov_batch_covariance");
+        c.stage = 2;
+        c.null_done = true;
+        if (si == CCOV_OK) covariance_stats(c);  // ms_covariance: the whole of steps (a)-(d)
+        if (si != CCOV_OK && first == CCOV_OK) first = si;
+    }
+    return first;
+}
+
+}  // extern "C"
+
+struct ccov_batch {
+    std::vector<ccov_ctx*> ctxs;
+    cudaStream_t master = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_free(ccov_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->joins)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->master) cudaStreamDestroy(b->master);
+    delete b;
+}
+
+extern "C" {
+
+ccov_status ccov_batch_create(ccov_ctx* const* ctxs, int k, double* const* outs_device, ccov_batch** out) {
+    if (!out) return CCOV_ERR_INVALID_ARG;
+    *out = nullptr;
+    // one direct pass validates the scenes and sets every kernel attribute
+    ccov_status s = ccov_batch_covariance(ctxs, k, outs_device, CCOV_MEM_DEVICE);
+    if (s != CCOV_OK) return s;
+    ccov_batch* b = new (std::nothrow) ccov_batch();
+    if (!b) return CCOV_ERR_OOM;
+    b->ctxs.assign(ctxs, ctxs + k);
+    b->joins.assign(k, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < k; ++i)
+        ok = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { batch_free(b); return CCOV_ERR_CUDA; }
+    // capture: fork every context's stream from the master stream, enqueue its
+    // four steps, join back
+    if (cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        batch_free(b);
+        return CCOV_ERR_CUDA;
+    }
+    cudaEventRecord(b->fork, b->master);
+    for (int i = 0; i < k && s == CCOV_OK; ++i) {
+        Ctx& c = ctxs[i]->c;
+        cudaStreamWaitEvent(c.stream, b->fork, 0);
+        c.capturing = true;
+        s = batch_enqueue(c, outs_device[i], CCOV_MEM_DEVICE);
+        c.capturing = false;
+        cudaEventRecord(b->joins[i], c.stream);
+        cudaStreamWaitEvent(b->master, b->joins[i], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(b->master, &b->graph);
+    if (s != CCOV_OK || e != cudaSuccess) { batch_free(b); return s != CCOV_OK ? s : CCOV_ERR_CUDA; }
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) { batch_free(b); return CCOV_ERR_CUDA; }
+    *out = b;
+    return CCOV_OK;
+}
+
+ccov_status ccov_batch_run(ccov_batch* b, void* stream) {
+    if (!b) return CCOV_ERR_INVALID_ARG;
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : b->master;
+    // order the replay after whatever the contexts' streams hold (ccov_load copies)
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        if (cudaEventRecord(b->joins[i], b->ctxs[i]->c.stream) != cudaSuccess ||
+            cudaStreamWaitEvent(st, b->joins[i], 0) != cudaSuccess)
+            return CCOV_ERR_CUDA;
+    }
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return CCOV_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCOV_ERR_CUDA;
+    ccov_status first = CCOV_OK;
+    for (ccov_ctx* h : b->ctxs) {
+        ccov_status si = check_device(h->c, "ccov_batch_run");
+        if (si != CCOV_OK && first == CCOV_OK) first = si;
+    }
+    return first;
+}
+
+void ccov_batch_destroy(ccov_batch* b) { batch_free(b); }
 
 ccov_status ccov_get_blocks(ccov_ctx* h, double* U, double* A_inv, double* W) {
     if (!h) return CCOV_ERR_INVALID_ARG;

@@ -69,6 +69,7 @@ struct Ctx {
     int64_t launches = 0;
     MixedState* mixed = nullptr;
     bool mixed_bad_launch = false;  // a GEMM launch was refused (odd tile count)
+    bool capturing = false;         // launches are being captured into a graph: no timing events
 
     cudaEvent_t ev[8] = {};
     ccov_stats stats{};

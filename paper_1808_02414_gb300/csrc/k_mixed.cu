@@ -947,7 +947,7 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_P, 0, (int)remQ, st.mapZ, (int)(kq + kNB), (int)(kq + kNB),
                      1, 1, kFL, nullptr, nullptr);
     }
-    cudaEventRecord(c.ev[3], c.stream);
+    if (!c.capturing) cudaEventRecord(c.ev[3], c.stream);
     // ---- triangular inverse X = L^-1 (Q42), row blocks of 128 ----
     cudaError_t e = cudaMemsetAsync(st.R, 0, sizeof(long long) * Np * Np, c.stream);
     if (e != cudaSuccess) return e;
