@@ -16,6 +16,8 @@ Modules
   brute        extended-precision ground truth for tiny scenes (Sec. 6: SVD of
                M with exactly seven zero singular values; bordered inverse)
   metrics      per-block error measures, including the paper's err (Sec. 6)
+  surrogate    the learned per-camera covariance predictor (not in the paper):
+               features, targets, bf16-rounding MLP forward/backward, Adam
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 something other than itself (closed forms, complex-step derivatives, dense

@@ -1,0 +1,222 @@
+"""Learned covariance surrogate (oracle; test infrastructure only).
+
+The paper has no learned component.  Its applications of camera covariances
+(Sec. 1: next-best-view selection, detecting badly added cameras, filtering
+unconstrained cameras) motivate a cheap per-camera predictor; this module
+states that predictor in plain numpy so that the CUDA kernels can be checked
+against it.
+
+Model, per camera i of a scene:
+  Z_ii    the 9x9 diagonal block of the reduced camera matrix of Sec. 4.2,
+          Z = U - W A^-1 W^T, i.e. U_i - sum over the camera's observations
+          of W_ij A_j^-1 W_ij^T;
+  d       sqrt(diag Z_ii) (9 values), the Jacobi scale of the block;
+  features (64 values):
+          [0, 36)   C_kl = Z_kl / (d_k d_l) for k < l, row by row
+          [36, 45)  log d_k
+          45        log of the camera's observation count
+          46        mean over its observations of log L_j (L_j = track length)
+          47        fraction of its observations with L_j = 2
+          48        log n (cameras in the scene)
+          49        |c_i - c_mean| / rms radius of the camera centres c = -R^T t
+          [50, 64)  zero
+  target  (45 values): the Cholesky factor L of S = diag(d) Sigma_i diag(d),
+          Sigma_i the exact camera covariance block: [0, 9) log L_kk,
+          [9, 45) L_kl for k > l, row by row;
+  output  Sigma_hat_i = diag(1/d) L_hat L_hat^T diag(1/d), L_hat from a
+          network output in the target's form.
+
+Network: 64 -> 256 -> 256 -> 256 -> 45, ReLU after the three hidden layers,
+inputs and targets standardised with per-column mean and standard deviation
+of the training set (a deviation below 1e-6 is replaced by 1).  Loss: mean
+squared error over the 45 standardised outputs and the batch.  Optimiser:
+Adam (Kingma and Ba, 2015) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8.
+
+Precision: the kernels multiply bf16 operands with fp32 accumulation.  The
+functions below take `quantize`; when it is set, every GEMM operand is
+rounded to bf16 (round to nearest even) at the same points as the kernels:
+the standardised inputs, the weights, the hidden activations after ReLU, and
+the output-side gradients fed to the two backward products.  Biases, the
+output, the loss and every sum stay in float64 here (fp32 on the GPU).  With
+`quantize` off the functions are the exact float64 gradient of the loss.
+
+Parity: forward/backward pinned by finite differences and by torch autograd
+in float64; Adam by torch.optim.Adam; bf16 rounding by torch's conversion;
+features by the dense Schur complement of `covariance` and by brute-force
+counting; targets by the round trip back to Sigma.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import camera, information
+
+F_IN, HIDDEN, F_OUT = 64, 256, 45
+DIMS = (F_IN, HIDDEN, HIDDEN, HIDDEN, F_OUT)
+BETA1, BETA2, EPS = 0.9, 0.999, 1e-8
+_IU = np.triu_indices(9, 1)       # (k, l), k < l, row by row
+_IL = np.tril_indices(9, -1)      # (k, l), k > l, row by row
+
+
+def param_shapes():
+    """[(out, in), (out,)] per layer, in the packing order W1, b1, ..., W4, b4."""
+    out = []
+    for a, b in zip(DIMS[:-1], DIMS[1:]):
+        out += [(b, a), (b,)]
+    return out
+
+
+def n_params() -> int:
+    return sum(int(np.prod(s)) for s in param_shapes())
+
+
+def unpack(flat: np.ndarray) -> list:
+    out, o = [], 0
+    for s in param_shapes():
+        k = int(np.prod(s))
+        out.append(np.asarray(flat[o:o + k], dtype=np.float64).reshape(s))
+        o += k
+    return out
+
+
+def pack(arrs) -> np.ndarray:
+    return np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in arrs])
+
+
+# ---------------------------------------------------------------------------
+# bf16 rounding: keep the 8 leading significand bits of the float32 value,
+# round to nearest, ties to even.
+def bf16(x: np.ndarray) -> np.ndarray:
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    return np.where(np.isfinite(f), out, f.astype(np.float64))
+
+
+# ---------------------------------------------------------------------------
+# Features and targets
+def diagonal_blocks(scene) -> np.ndarray:
+    """Z_ii = U_i - sum_{j seen by i} W_ij A_j^-1 W_ij^T, (n, 9, 9)."""
+    U, A, W, _, _ = information.blocks(scene)
+    Ainv = np.linalg.inv(A)
+    Z = U.copy()
+    for o in range(scene.t):
+        i, j = scene.obs_cam[o], scene.obs_pt[o]
+        Z[i] -= W[o] @ Ainv[j] @ W[o].T
+    return Z
+
+
+def degree_stats(scene) -> np.ndarray:
+    """(n, 3): log #obs, mean log track length, fraction of 2-tracks."""
+    L = np.bincount(scene.obs_pt, minlength=scene.m)
+    out = np.zeros((scene.n, 3))
+    for i in range(scene.n):
+        tr = L[scene.obs_pt[scene.obs_cam == i]]
+        out[i] = [np.log(len(tr)), np.mean(np.log(tr)), np.mean(tr == 2)]
+    return out
+
+
+def centre_distance(scene) -> np.ndarray:
+    c = np.stack([-camera.rotation_matrix(p[:3]).T @ p[3:6] for p in scene.cams])
+    dev = c - c.mean(axis=0)
+    rms = np.sqrt(np.mean(np.sum(dev ** 2, axis=1)))
+    return np.sqrt(np.sum(dev ** 2, axis=1)) / rms
+
+
+def features(scene):
+    """(features (n, 64), scale d (n, 9))."""
+    Z = diagonal_blocks(scene)
+    d = np.sqrt(np.einsum("ikk->ik", Z))
+    C = Z / (d[:, :, None] * d[:, None, :])
+    f = np.zeros((scene.n, F_IN))
+    f[:, :36] = C[:, _IU[0], _IU[1]]
+    f[:, 36:45] = np.log(d)
+    f[:, 45:48] = degree_stats(scene)
+    f[:, 48] = np.log(scene.n)
+    f[:, 49] = centre_distance(scene)
+    return f, d
+
+
+def targets(sigma: np.ndarray, d: np.ndarray) -> np.ndarray:
+    """Cholesky form of S = diag(d) Sigma diag(d), (n, 45)."""
+    S = sigma * d[:, :, None] * d[:, None, :]
+    L = np.linalg.cholesky(S)
+    return np.concatenate([np.log(np.einsum("ikk->ik", L)), L[:, _IL[0], _IL[1]]], axis=1)
+
+
+def covariance_from_output(t: np.ndarray, d: np.ndarray) -> np.ndarray:
+    """Sigma_hat = diag(1/d) L L^T diag(1/d) from outputs in the target form."""
+    n = t.shape[0]
+    L = np.zeros((n, 9, 9))
+    k = np.arange(9)
+    L[:, k, k] = np.exp(t[:, :9])
+    L[:, _IL[0], _IL[1]] = t[:, 9:]
+    S = L @ L.transpose(0, 2, 1)
+    return S / (d[:, :, None] * d[:, None, :])
+
+
+def normalization(x: np.ndarray):
+    """Column mean and deviation (population), deviation < 1e-6 -> 1."""
+    mu = x.mean(axis=0)
+    sd = np.sqrt(np.mean((x - mu) ** 2, axis=0))
+    return mu, np.where(sd < 1e-6, 1.0, sd)
+
+
+# ---------------------------------------------------------------------------
+# Network
+def forward(params, x, quantize=True):
+    """x: standardised inputs (B, 64).  Returns (y (B, 45), activations a0..a3)."""
+    q = bf16 if quantize else (lambda v: np.asarray(v, dtype=np.float64))
+    W = params[0::2]
+    b = params[1::2]
+    acts = [q(x)]
+    for layer in range(3):
+        z = acts[-1] @ q(W[layer]).T + b[layer]
+        acts.append(q(np.maximum(z, 0.0)))
+    y = acts[-1] @ q(W[3]).T + b[3]
+    return y, acts
+
+
+def loss_and_grads(params, x, t, quantize=True):
+    """Mean squared error over the batch and the 45 outputs, and its gradients
+    with respect to [W1, b1, ..., W4, b4] (straight-through at the bf16
+    roundings when `quantize` is set)."""
+    q = bf16 if quantize else (lambda v: np.asarray(v, dtype=np.float64))
+    y, acts = forward(params, x, quantize)
+    B = x.shape[0]
+    r = y - t
+    loss = float(np.sum(r * r) / (B * F_OUT))
+    g = 2.0 * r / (B * F_OUT)                     # dL/dz of the output layer
+    W = params[0::2]
+    grads = [None] * 8
+    for layer in range(3, -1, -1):
+        grads[2 * layer] = q(g).T @ acts[layer]
+        grads[2 * layer + 1] = g.sum(axis=0)
+        if layer > 0:
+            dx = q(g) @ q(W[layer])
+            g = dx * (acts[layer] > 0)
+    return loss, grads
+
+
+def adam(params, grads, m, v, step, lr):
+    """One Adam step (step counts from 1); returns new params, m, v."""
+    out_p, out_m, out_v = [], [], []
+    c1 = 1.0 - BETA1 ** step
+    c2 = 1.0 - BETA2 ** step
+    for p, g, mm, vv in zip(params, grads, m, v):
+        mm = BETA1 * mm + (1.0 - BETA1) * g
+        vv = BETA2 * vv + (1.0 - BETA2) * g * g
+        p = p - lr * (mm / c1) / (np.sqrt(vv / c2) + EPS)
+        out_p.append(p)
+        out_m.append(mm)
+        out_v.append(vv)
+    return out_p, out_m, out_v
+
+
+def predict(params, f, d, norm, quantize=True):
+    """Sigma_hat for raw features f (n, 64) with normalisation (mu_f, sd_f, mu_t, sd_t)."""
+    mu_f, sd_f, mu_t, sd_t = norm
+    y, _ = forward(params, (f - mu_f) / sd_f, quantize)
+    return covariance_from_output(y * sd_t + mu_t, d)

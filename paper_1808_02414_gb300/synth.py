@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
-           "subscene", "WORKLOADS", "workload"]
+           "subscene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices"]
 
 
 @dataclass
@@ -266,3 +266,29 @@ def workload(name: str, **over) -> Scene:
     spec.update(over)
     fn = spec.pop("fn")
     return ring_scene(**spec) if fn == "ring" else shell_scene(**spec)
+
+
+# ---------------------------------------------------------------------------
+# Random draws of the learned surrogate (initial weights, mini-batch order).
+# Layer widths 64 -> 256 -> 256 -> 256 -> 45; weights packed W1, b1, ..., W4, b4
+# with W of shape (out, in), row-major.
+SURROGATE_DIMS = (64, 256, 256, 256, 45)
+
+
+def surrogate_init(seed=0) -> np.ndarray:
+    """He-uniform weights (bound sqrt(6 / fan_in)), zero biases, float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for a, b in zip(SURROGATE_DIMS[:-1], SURROGATE_DIMS[1:]):
+        bound = np.sqrt(6.0 / a)
+        parts.append(rng.uniform(-bound, bound, size=(b, a)).ravel())
+        parts.append(np.zeros(b))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def minibatch_indices(n: int, batch: int, steps: int, seed=0) -> np.ndarray:
+    """steps x batch sample indices: consecutive shuffled epochs over range(n)."""
+    rng = np.random.default_rng(seed)
+    need = steps * batch
+    out = np.concatenate([rng.permutation(n) for _ in range(-(-need // n))])[:need]
+    return out.astype(np.int32).reshape(steps, batch)

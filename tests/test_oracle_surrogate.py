@@ -1,0 +1,179 @@
+"""Pins of the surrogate oracle against things other than itself: torch's
+bf16 conversion, torch autograd and torch.optim.Adam in float64, central
+finite differences, the dense Schur complement of the covariance oracle,
+brute-force counting, closed forms and round trips."""
+import numpy as np
+import pytest
+
+from oracle import covariance, surrogate as S
+from paper_1808_02414_gb300 import synth
+
+
+def _params(seed=0, scale=1.0):
+    p = S.unpack(synth.surrogate_init(seed).astype(np.float64))
+    rng = np.random.default_rng(seed + 100)
+    # non-zero biases so that their gradients are exercised
+    return [a if a.ndim == 2 else scale * rng.normal(0, 0.1, a.shape) for a in p]
+
+
+def _batch(B=7, seed=1):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(B, S.F_IN)), rng.normal(size=(B, S.F_OUT))
+
+
+def test_shapes_and_packing():
+    assert S.n_params() == 64 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 45 + 45
+    flat = synth.surrogate_init(3)
+    assert flat.shape == (S.n_params(),)
+    np.testing.assert_array_equal(S.pack(S.unpack(flat)), flat.astype(np.float64))
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(size=5000) * 10.0 ** rng.integers(-30, 30, 5000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.005859375, 3e38, -7e-39]])
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(S.bf16(x), want)
+
+
+def test_exact_gradients_match_torch_autograd():
+    torch = pytest.importorskip("torch")
+    p = _params()
+    x, t = _batch()
+    loss, g = S.loss_and_grads(p, x, t, quantize=False)
+    tp = [torch.tensor(a, requires_grad=True) for a in p]
+    h = torch.tensor(x)
+    for layer in range(4):
+        h = h @ tp[2 * layer].T + tp[2 * layer + 1]
+        if layer < 3:
+            h = torch.relu(h)
+    tl = ((h - torch.tensor(t)) ** 2).mean()
+    tl.backward()
+    assert abs(loss - tl.item()) < 1e-12 * abs(loss)
+    for a, b in zip(g, tp):
+        np.testing.assert_allclose(a, b.grad.numpy(), rtol=1e-10, atol=1e-14)
+
+
+def test_exact_gradients_match_finite_differences():
+    p = _params(seed=2)
+    x, t = _batch(B=5, seed=3)
+    _, g = S.loss_and_grads(p, x, t, quantize=False)
+    rng = np.random.default_rng(4)
+    h = 1e-6
+    for k in range(8):
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s) for s in p[k].shape)
+            pp = [a.copy() for a in p]
+            pp[k][idx] += h
+            lp, _ = S.loss_and_grads(pp, x, t, quantize=False)
+            pp[k][idx] -= 2 * h
+            lm, _ = S.loss_and_grads(pp, x, t, quantize=False)
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k][idx]) <= 1e-6 * max(1e-3, abs(fd)), (k, idx, fd, g[k][idx])
+
+
+def test_planted_mistake_in_backward_is_caught():
+    """A backward that forgets the ReLU mask disagrees with finite differences."""
+    p = _params(seed=5)
+    x, t = _batch(B=4, seed=6)
+    _, g = S.loss_and_grads(p, x, t, quantize=False)
+    y, acts = S.forward(p, x, quantize=False)
+    gout = 2.0 * (y - t) / (4 * S.F_OUT)
+    wrong = (gout @ p[6]).T @ acts[2]              # no mask on layer 3
+    assert np.abs(wrong - g[4]).max() > 1e-6 * np.abs(g[4]).max()
+
+
+def test_quantized_forward_is_within_bf16_error_of_exact():
+    p = _params(seed=7)
+    x, _ = _batch(B=64, seed=8)
+    yq, acts = S.forward(p, x, quantize=True)
+    ye, _ = S.forward(p, x, quantize=False)
+    rel = np.abs(yq - ye).max() / np.abs(ye).max()
+    assert 1e-4 < rel < 5e-2          # rounded, but only at bf16 precision
+    for a in acts:
+        np.testing.assert_array_equal(S.bf16(a), a)   # activations are bf16 values
+
+
+def test_adam_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    p = [rng.normal(size=(3, 4)), rng.normal(size=5)]
+    m = [np.zeros_like(a) for a in p]
+    v = [np.zeros_like(a) for a in p]
+    tp = [torch.tensor(a, requires_grad=True) for a in p]
+    opt = torch.optim.Adam(tp, lr=1e-2, betas=(S.BETA1, S.BETA2), eps=S.EPS)
+    for step in range(1, 4):
+        g = [rng.normal(size=a.shape) for a in p]
+        p, m, v = S.adam(p, g, m, v, step, 1e-2)
+        for a, b in zip(tp, g):
+            a.grad = torch.tensor(b)
+        opt.step()
+        for a, b in zip(p, tp):
+            np.testing.assert_allclose(a, b.detach().numpy(), rtol=1e-12, atol=1e-15)
+
+
+def test_diagonal_blocks_match_dense_schur_complement():
+    sc = synth.shell_scene(n=12, m=300, seed=3)
+    Zd = S.diagonal_blocks(sc)
+    Z, _, _ = covariance.schur_blocks_unscaled(sc)
+    for i in range(sc.n):
+        blk = Z[9 * i:9 * i + 9, 9 * i:9 * i + 9]
+        np.testing.assert_allclose(Zd[i], blk, rtol=0, atol=1e-10 * np.abs(blk).max())
+
+
+def test_degree_stats_by_counting():
+    sc = synth.shell_scene(n=10, m=200, seed=4)
+    track = {}
+    for j in sc.obs_pt:
+        track[int(j)] = track.get(int(j), 0) + 1
+    got = S.degree_stats(sc)
+    for i in range(sc.n):
+        lens = [track[int(j)] for c, j in zip(sc.obs_cam, sc.obs_pt) if c == i]
+        assert got[i, 0] == pytest.approx(np.log(len(lens)), rel=1e-14)
+        assert got[i, 1] == pytest.approx(sum(np.log(v) for v in lens) / len(lens), rel=1e-14)
+        assert got[i, 2] == pytest.approx(sum(v == 2 for v in lens) / len(lens), rel=1e-14)
+
+
+def test_centre_distance_on_a_ring_is_one():
+    sc = synth.workload("ring20")   # centres on a circle about the origin
+    np.testing.assert_allclose(S.centre_distance(sc), 1.0, rtol=1e-12)
+
+
+def test_features_layout():
+    sc = synth.shell_scene(n=8, m=150, seed=5)
+    f, d = S.features(sc)
+    Z = S.diagonal_blocks(sc)
+    assert f.shape == (8, 64) and d.shape == (8, 9)
+    np.testing.assert_allclose(d ** 2, np.einsum("ikk->ik", Z), rtol=1e-14)
+    assert f[3, 0] == pytest.approx(Z[3, 0, 1] / (d[3, 0] * d[3, 1]), rel=1e-14)   # C_01
+    assert f[3, 35] == pytest.approx(Z[3, 7, 8] / (d[3, 7] * d[3, 8]), rel=1e-14)  # C_78
+    np.testing.assert_allclose(f[:, 36:45], np.log(d), rtol=1e-14)
+    assert np.all(f[:, 50:] == 0)
+    assert np.all(np.abs(f[:, :36]) < 1)   # off-diagonal correlations of an SPD block
+
+
+def test_targets_round_trip_and_diagonal_closed_form():
+    sc = synth.shell_scene(n=10, m=300, seed=6)
+    sig = covariance.camera_covariance(sc)
+    _, d = S.features(sc)
+    t = S.targets(sig, d)
+    np.testing.assert_allclose(S.covariance_from_output(t, d), sig, rtol=1e-10,
+                               atol=1e-12 * np.abs(sig).max())
+    diag = np.zeros((2, 9, 9))
+    diag[:, range(9), range(9)] = [np.arange(1, 10), np.arange(2, 11)]
+    dd = np.full((2, 9), 3.0)
+    tt = S.targets(diag, dd)
+    np.testing.assert_allclose(tt[:, :9], 0.5 * np.log(9.0 * np.array([np.arange(1, 10), np.arange(2, 11)])))
+    assert np.all(tt[:, 9:] == 0)
+
+
+def test_normalization():
+    rng = np.random.default_rng(0)
+    x = rng.normal(3.0, 2.0, size=(500, 4))
+    x[:, 2] = 5.0
+    mu, sd = S.normalization(x)
+    z = (x - mu) / sd
+    np.testing.assert_allclose(z.mean(axis=0), 0, atol=1e-12)
+    np.testing.assert_allclose(z[:, [0, 1, 3]].std(axis=0), 1, rtol=1e-12)
+    assert sd[2] == 1.0 and np.all(z[:, 2] == 0)
