@@ -10,7 +10,9 @@ Model, per camera i of a scene:
   Z_ii    the 9x9 diagonal block of the reduced camera matrix of Sec. 4.2,
           Z = U - W A^-1 W^T, i.e. U_i - sum over the camera's observations
           of W_ij A_j^-1 W_ij^T;
-  d       sqrt(diag Z_ii) (9 values), the Jacobi scale of the block;
+  d       sqrt(diag Z_ii) (9 values), the block's Jacobi scale;
+  L_z     the Cholesky factor of Z_ii (Z_ii = L_z L_z^T): Z_ii^-1 is the
+          covariance the camera would have with every other camera fixed;
   features (64 values):
           [0, 36)   C_kl = Z_kl / (d_k d_l) for k < l, row by row
           [36, 45)  log d_k
@@ -20,11 +22,12 @@ Model, per camera i of a scene:
           48        log n (cameras in the scene)
           49        |c_i - c_mean| / rms radius of the camera centres c = -R^T t
           [50, 64)  zero
-  target  (45 values): the Cholesky factor L of S = diag(d) Sigma_i diag(d),
-          Sigma_i the exact camera covariance block: [0, 9) log L_kk,
-          [9, 45) L_kl for k > l, row by row;
-  output  Sigma_hat_i = diag(1/d) L_hat L_hat^T diag(1/d), L_hat from a
-          network output in the target's form.
+  target  (45 values): the Cholesky factor L of the whitened exact block
+          S = L_z^T Sigma_i L_z (S = I when Sigma_i = Z_ii^-1):
+          [0, 9) log L_kk, [9, 45) L_kl for k > l, row by row;
+  output  Sigma_hat_i = L_z^-T L_hat L_hat^T L_z^-1, L_hat from a network
+          output in the target's form, so that the network learns how far the
+          whole scene moves the camera's covariance away from Z_ii^-1.
 
 Network: 64 -> 256 -> 256 -> 256 -> 45, ReLU after the three hidden layers,
 inputs and targets standardised with per-column mean and standard deviation
@@ -43,7 +46,9 @@ output, the loss and every sum stay in float64 here (fp32 on the GPU).  With
 Parity: forward/backward pinned by finite differences and by torch autograd
 in float64; Adam by torch.optim.Adam; bf16 rounding by torch's conversion;
 features by the dense Schur complement of `covariance` and by brute-force
-counting; targets by the round trip back to Sigma.
+counting; targets by the round trip back to Sigma and by the closed form
+Sigma = Z_ii^-1 -> S = I; the KL measure by its closed form for scaled
+identities.
 """
 from __future__ import annotations
 
@@ -126,7 +131,7 @@ def centre_distance(scene) -> np.ndarray:
 
 
 def features(scene):
-    """(features (n, 64), scale d (n, 9))."""
+    """(features (n, 64), L_z (n, 9, 9) lower triangular)."""
     Z = diagonal_blocks(scene)
     d = np.sqrt(np.einsum("ikk->ik", Z))
     C = Z / (d[:, :, None] * d[:, None, :])
@@ -136,25 +141,33 @@ def features(scene):
     f[:, 45:48] = degree_stats(scene)
     f[:, 48] = np.log(scene.n)
     f[:, 49] = centre_distance(scene)
-    return f, d
+    return f, np.linalg.cholesky(Z)
 
 
-def targets(sigma: np.ndarray, d: np.ndarray) -> np.ndarray:
-    """Cholesky form of S = diag(d) Sigma diag(d), (n, 45)."""
-    S = sigma * d[:, :, None] * d[:, None, :]
+def targets(sigma: np.ndarray, Lz: np.ndarray) -> np.ndarray:
+    """Cholesky form of S = L_z^T Sigma L_z, (n, 45)."""
+    S = Lz.transpose(0, 2, 1) @ sigma @ Lz
     L = np.linalg.cholesky(S)
     return np.concatenate([np.log(np.einsum("ikk->ik", L)), L[:, _IL[0], _IL[1]]], axis=1)
 
 
-def covariance_from_output(t: np.ndarray, d: np.ndarray) -> np.ndarray:
-    """Sigma_hat = diag(1/d) L L^T diag(1/d) from outputs in the target form."""
+def covariance_from_output(t: np.ndarray, Lz: np.ndarray) -> np.ndarray:
+    """Sigma_hat = L_z^-T L L^T L_z^-1 from outputs in the target form."""
     n = t.shape[0]
     L = np.zeros((n, 9, 9))
     k = np.arange(9)
     L[:, k, k] = np.exp(t[:, :9])
     L[:, _IL[0], _IL[1]] = t[:, 9:]
-    S = L @ L.transpose(0, 2, 1)
-    return S / (d[:, :, None] * d[:, None, :])
+    Li = np.linalg.inv(Lz)
+    return Li.transpose(0, 2, 1) @ (L @ L.transpose(0, 2, 1)) @ Li
+
+
+def gaussian_kl(pred: np.ndarray, true: np.ndarray) -> np.ndarray:
+    """KL(N(0, true) || N(0, pred)) per block: an error measure of a
+    covariance that does not depend on the units of the parameters."""
+    Pi = np.linalg.inv(pred)
+    return 0.5 * (np.einsum("iab,iba->i", Pi, true) - true.shape[1] + np.linalg.slogdet(pred)[1]
+                  - np.linalg.slogdet(true)[1])
 
 
 def normalization(x: np.ndarray):
@@ -215,8 +228,8 @@ def adam(params, grads, m, v, step, lr):
     return out_p, out_m, out_v
 
 
-def predict(params, f, d, norm, quantize=True):
+def predict(params, f, Lz, norm, quantize=True):
     """Sigma_hat for raw features f (n, 64) with normalisation (mu_f, sd_f, mu_t, sd_t)."""
     mu_f, sd_f, mu_t, sd_t = norm
     y, _ = forward(params, (f - mu_f) / sd_f, quantize)
-    return covariance_from_output(y * sd_t + mu_t, d)
+    return covariance_from_output(y * sd_t + mu_t, Lz)

@@ -142,10 +142,12 @@ def test_centre_distance_on_a_ring_is_one():
 
 def test_features_layout():
     sc = synth.shell_scene(n=8, m=150, seed=5)
-    f, d = S.features(sc)
+    f, Lz = S.features(sc)
     Z = S.diagonal_blocks(sc)
-    assert f.shape == (8, 64) and d.shape == (8, 9)
-    np.testing.assert_allclose(d ** 2, np.einsum("ikk->ik", Z), rtol=1e-14)
+    d = np.sqrt(np.einsum("ikk->ik", Z))
+    assert f.shape == (8, 64) and Lz.shape == (8, 9, 9)
+    np.testing.assert_allclose(Lz @ Lz.transpose(0, 2, 1), Z, rtol=1e-12, atol=1e-12 * np.abs(Z).max())
+    assert np.all(np.triu(Lz[2], 1) == 0) and np.all(np.einsum("ikk->ik", Lz) > 0)
     assert f[3, 0] == pytest.approx(Z[3, 0, 1] / (d[3, 0] * d[3, 1]), rel=1e-14)   # C_01
     assert f[3, 35] == pytest.approx(Z[3, 7, 8] / (d[3, 7] * d[3, 8]), rel=1e-14)  # C_78
     np.testing.assert_allclose(f[:, 36:45], np.log(d), rtol=1e-14)
@@ -153,19 +155,32 @@ def test_features_layout():
     assert np.all(np.abs(f[:, :36]) < 1)   # off-diagonal correlations of an SPD block
 
 
-def test_targets_round_trip_and_diagonal_closed_form():
+def test_targets_round_trip_and_closed_form():
     sc = synth.shell_scene(n=10, m=300, seed=6)
     sig = covariance.camera_covariance(sc)
-    _, d = S.features(sc)
-    t = S.targets(sig, d)
-    np.testing.assert_allclose(S.covariance_from_output(t, d), sig, rtol=1e-10,
+    _, Lz = S.features(sc)
+    t = S.targets(sig, Lz)
+    np.testing.assert_allclose(S.covariance_from_output(t, Lz), sig, rtol=1e-10,
                                atol=1e-12 * np.abs(sig).max())
-    diag = np.zeros((2, 9, 9))
-    diag[:, range(9), range(9)] = [np.arange(1, 10), np.arange(2, 11)]
-    dd = np.full((2, 9), 3.0)
-    tt = S.targets(diag, dd)
-    np.testing.assert_allclose(tt[:, :9], 0.5 * np.log(9.0 * np.array([np.arange(1, 10), np.arange(2, 11)])))
-    assert np.all(tt[:, 9:] == 0)
+    # the covariance with every other camera fixed, Z_ii^-1, whitens to I
+    local = np.linalg.inv(S.diagonal_blocks(sc))
+    np.testing.assert_allclose(S.targets(local, Lz), 0.0, atol=1e-9)
+    # a whitened block 4 I: log L_kk = log 2, no off-diagonal part
+    Li = np.linalg.inv(Lz)
+    four = 4.0 * Li.transpose(0, 2, 1) @ Li
+    tt = S.targets(four, Lz)
+    np.testing.assert_allclose(tt[:, :9], np.log(2.0), atol=1e-9)
+    np.testing.assert_allclose(tt[:, 9:], 0.0, atol=1e-9)
+
+
+def test_gaussian_kl_closed_form():
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(4, 9, 9))
+    Q = A @ A.transpose(0, 2, 1) + 9 * np.eye(9)
+    np.testing.assert_allclose(S.gaussian_kl(Q, Q), 0.0, atol=1e-12)
+    # pred = c true: KL = 9/2 (1/c - 1 + log c)
+    c = 2.5
+    np.testing.assert_allclose(S.gaussian_kl(c * Q, Q), 4.5 * (1 / c - 1 + np.log(c)), rtol=1e-12)
 
 
 def test_normalization():
