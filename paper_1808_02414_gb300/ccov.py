@@ -86,6 +86,21 @@ def load() -> C.CDLL:
         "ccov_batch_create": ([P, I, P, C.POINTER(C.c_void_p)], I),
         "ccov_batch_run": ([P, P], I),
         "ccov_batch_destroy": ([P], None),
+        "ccov_surrogate_features": ([P, P, P], I),
+        "ccov_surrogate_targets": ([I64, P, P, P, P], I),
+        "ccov_surrogate_create": ([P, I64, P, C.POINTER(C.c_void_p)], I),
+        "ccov_surrogate_fit_normalization": ([P, P, P, I64], I),
+        "ccov_surrogate_set_normalization": ([P, P], I),
+        "ccov_surrogate_get_normalization": ([P, P], I),
+        "ccov_surrogate_set_params": ([P, P], I),
+        "ccov_surrogate_get_params": ([P, P], I),
+        "ccov_surrogate_backward": ([P, P, P, I64, P, I64, P], I),
+        "ccov_surrogate_get_grads": ([P, P], I),
+        "ccov_surrogate_adam": ([P, C.c_float], I),
+        "ccov_surrogate_train": ([P, P, P, I64, P, I64, I, C.c_float, P], I),
+        "ccov_surrogate_predict": ([P, P, P, I64, P], I),
+        "ccov_surrogate_destroy": ([P], None),
+        "ccov_surrogate_last_error": ([P], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

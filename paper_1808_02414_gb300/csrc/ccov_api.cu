@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "ccov_internal.cuh"
+#include "../../include/ccov_surrogate.h"
 
 using ccov::Ctx;
 
@@ -531,6 +532,15 @@ static ccov_status batch_enqueue(Ctx& c, double* out, int out_memory) {
     if (s == CCOV_OK) s = enq_covariance(c, out, out_memory);
     rec(c, 1);
     return s;
+}
+
+ccov_status ccov_surrogate_features(ccov_ctx* h, float* features, double* scale) {
+    if (!h || !features || !scale) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage != 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_features: needs Z (after ccov_schur)");
+    ccov::surr_launch_features(c, features, scale);
+    CK(cudaGetLastError(), "ccov_surrogate_features launch");
+    return check_device(c, "ccov_surrogate_features");
 }
 
 ccov_status ccov_batch_covariance(ccov_ctx* const* ctxs, int k, double* const* outs, int out_memory) {

@@ -22,6 +22,7 @@ enum DevErr : int {
     DEV_SINGULAR_W7 = 4,
     DEV_SINGULAR_JR = 5,  // J_r^T J_r of a camera singular (nullspace solve)
     DEV_TIMEOUT = 6,      // a bounded spin-wait gave up
+    DEV_BAD_INDEX = 7,    // a sample index outside the training set (surrogate)
 };
 
 struct MixedState;  // emulated-FP64 tensor-core path, k_mixed.cu
@@ -101,6 +102,9 @@ void launch_copy_panel(Ctx& c, int64_t k0);
 void launch_init_identity(Ctx& c, double* X, int64_t ld);
 void launch_trtri_row(Ctx& c, int64_t k0);
 void launch_extract(Ctx& c);
+
+// ---- surrogate features (k_surrogate.cu) ----
+void surr_launch_features(Ctx& c, float* feat, double* scale);
 
 // ---- mixed path (k_mixed.cu) ----
 cudaError_t mixed_alloc(Ctx& c);

@@ -4,7 +4,7 @@ import ctypes
 import os
 import re
 
-from paper_1808_02414_gb300 import build, ccov
+from paper_1808_02414_gb300 import build, ccov, surrogate
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -33,6 +33,7 @@ def test_library_builds_loads_and_exports_every_declared_symbol():
     for name in declared_symbols():
         assert hasattr(lib, name), name
     assert sorted(ccov.EXPORTED) == declared_symbols("ccov.h")
+    assert sorted(surrogate.EXPORTED) == declared_symbols("ccov_surrogate.h")
 
 
 def test_status_strings_without_gpu():
