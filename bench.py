@@ -9,6 +9,10 @@ workload is the synthetic 4000-camera shell scene (400k points, track length
 `e2e` = the same through the C ABI with host buffers (host-to-device upload and
 the device-to-host copy of the 9x9 blocks inside every timed step).
 
+`--workload surrogate` trains the learned surrogate on exact blocks of
+2000 scenes (n ~ U{50..500}) and times its prediction on the 4000-camera
+scene (value = cameras / s of ccov_information + features + prediction).
+
 `--workload batch256` times the batched form instead: 256 independent
 sub-reconstructions (n ~ U{10..300} cameras, 100 points per camera, track
 length 1 + Geometric(0.2)), all four steps of every scene recorded once as a
@@ -50,6 +54,9 @@ def parse():
     ap.add_argument("--cpu-sample-cams", type=int, default=800)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--surr-scenes", type=int, default=2000)
+    ap.add_argument("--surr-epochs", type=int, default=30)
+    ap.add_argument("--surr-batch", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -490,12 +497,209 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+# kernels of one surrogate step: cam_prep, point_info, cam_info (ccov_information);
+# features, centre spread, centre feature; pack, 4 GEMMs, output (prediction)
+SURR_STEP_LAUNCHES = 12
+
+
+def _training_scene(spec):
+    from paper_1808_02414_gb300 import synth
+    return synth.training_scene(spec)
+
+
+def surrogate_training_set(n_scenes: int, n_heldout: int = 30, group: int = 32):
+    """Features and targets of every camera of the training scenes, on the
+    device, plus (features, L_z, exact blocks) of `n_heldout` further scenes
+    of the same distribution.  Scenes are drawn in worker processes (spawned,
+    so that no worker inherits a CUDA context) and solved exactly with the
+    FP64 path in batches of `group` contexts."""
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_1808_02414_gb300 import ccov, surrogate, synth
+
+    specs = synth.training_scene_specs(n_scenes + n_heldout)
+    F, TG, HF, HL, HS = [], [], [], [], []
+    procs = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pending, seen = [], 0
+        for sc in pool.imap(_training_scene, specs, chunksize=4):
+            pending.append(sc)
+            seen += 1
+            if len(pending) < group and seen not in (n_scenes, len(specs)):
+                continue
+            if seen <= n_scenes:
+                _solve_group(pending, F, TG, ccov, surrogate, torch)
+            else:
+                _solve_group(pending, HF, None, ccov, surrogate, torch, HL, HS)
+            pending = []
+    held = (torch.cat(HF), torch.cat(HL).cpu().numpy(), torch.cat(HS).cpu().numpy()) if HF else None
+    return torch.cat(F), torch.cat(TG), held
+
+
+def _solve_group(scenes, F, TG, ccov, surrogate, torch, LZ=None, SG=None):
+    ctxs = [ccov.from_scene(sc) for sc in scenes]
+    outs = [torch.empty((sc.n, 9, 9), dtype=torch.float64, device="cuda") for sc in scenes]
+    try:
+        ccov.ccov_batch_covariance(ctxs, outs)
+        for c, o in zip(ctxs, outs):
+            f, lz = surrogate.features(c)
+            F.append(f)
+            if TG is not None:
+                TG.append(surrogate.targets(lz, o))
+            if LZ is not None:
+                LZ.append(lz)
+                SG.append(o)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def _surrogate_accuracy(sm, f, L, truth, S):
+    import numpy as np
+    pred = sm.predict(f, __import__("torch").from_numpy(L).cuda()).cpu().numpy()
+    mu_t = sm.normalization()[128:173].astype(np.float64)
+    n = L.shape[0]
+    kl = {"surrogate": S.gaussian_kl(pred, truth),
+          "local_block_inverse": S.gaussian_kl(S.covariance_from_output(np.zeros((n, 45)), L), truth),
+          "constant_correction": S.gaussian_kl(S.covariance_from_output(np.tile(mu_t, (n, 1)), L), truth)}
+    out = {k: {"median_kl": float(np.median(v)), "p90_kl": float(np.percentile(v, 90))} for k, v in kl.items()}
+    out["surrogate"]["median_rel_fro"] = float(np.median(
+        np.linalg.norm(pred - truth, axis=(1, 2)) / np.linalg.norm(truth, axis=(1, 2))))
+    out["cameras"] = int(n)
+    return out
+
+
+def run_surrogate(args):
+    import numpy as np
+    import torch
+
+    from oracle import surrogate as S
+    from paper_1808_02414_gb300 import ccov, surrogate, synth
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    t0 = time.perf_counter()
+    F, TG, held = surrogate_training_set(args.surr_scenes)
+    data_s = time.perf_counter() - t0
+    N, B = int(F.shape[0]), args.surr_batch
+    steps = max(1, args.surr_epochs * N // B)
+    idx = torch.from_numpy(synth.minibatch_indices(N, B, steps, seed=11)).to(dev)
+    sm = surrogate.Surrogate(synth.surrogate_init(0), max_batch=B, stream=stream.cuda_stream)
+    sm.fit_normalization(F, TG)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = sm.train(F, TG, idx, 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    ms_train_step = train_ms / steps
+    accuracy = {"heldout_scenes_50_500_cams": _surrogate_accuracy(sm, *held, S)}
+
+    # evaluation on the 4000-camera scene: exact blocks from the mixed path
+    scene = synth.workload("shell4k")
+    cams = torch.from_numpy(scene.cams).to(dev)
+    pts = torch.from_numpy(scene.pts).to(dev)
+    rec = scene.obs_records()
+    obs = torch.from_numpy(rec.view(np.uint8)).to(dev)
+    exact = torch.empty((scene.n, 9, 9), dtype=torch.float64, device=dev)
+    with ccov.Context(cams, pts, obs, scene.sigma, precision=ccov.CCOV_PREC_MIXED, stream=stream.cuda_stream) as cx:
+        cx.run(out=exact)
+    ctx = ccov.Context(cams, pts, obs, scene.sigma, stream=stream.cuda_stream)
+
+    def step():
+        ctx.ccov_information()
+        f, lz = surrogate.features(ctx)
+        return sm.predict(f, lz), lz
+
+    for _ in range(args.warmup):
+        pred, lz = step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        pred, lz = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = barrier_max(e0.elapsed_time(e1), world) / args.steps
+    value = scene.n * world / (ms_step / 1e3)
+
+    # end to end with host buffers: upload, the three calls, the blocks back
+    hc = torch.from_numpy(scene.cams).pin_memory().numpy()
+    hp = torch.from_numpy(scene.pts).pin_memory().numpy()
+    ho = torch.from_numpy(rec.view(np.uint8)).pin_memory().numpy().view(rec.dtype)
+    hout = torch.empty((scene.n, 9, 9), dtype=torch.float64).pin_memory()
+    ctx_h = ccov.Context(scene.cams, scene.pts, rec, scene.sigma, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx_h.ccov_load(hc, hp, ho)
+    ctx_h.ccov_information()
+    f, l2 = surrogate.features(ctx_h)
+    hout.copy_(sm.predict(f, l2))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    ctx_h.close()
+
+    accuracy["shell4k_4000_cams"] = _surrogate_accuracy(sm, f, lz.cpu().numpy(), exact.cpu().numpy(), S)
+    ctx.close()
+
+    # executed tensor flops of one training step (padded widths 128/256/256/256/128)
+    Bp = (B + 127) // 128 * 128
+    fwd = 2.0 * Bp * (128 * 256 + 2 * 256 * 256 + 256 * 128)
+    flops_step = fwd + (2.0 * Bp * (128 * 256 + 2 * 256 * 256)) + fwd
+    pk, src = peaks()
+    achieved = flops_step / (ms_train_step / 1e3) / 1e12
+    line = {"metric": "camera covariances/s (surrogate, 4k-cam scene)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "surrogate", "train_scenes": args.surr_scenes, "train_samples": N,
+                       "batch": B, "train_steps": steps, "eval": "shell4k (4000 cameras)",
+                       "step": "ccov_information + surrogate features + prediction",
+                       "l2": "eval inputs 90 MB + blocks, working set > L2 in the information step"},
+            "clocks": clk,
+            "e2e": {"value": scene.n / (ms_e2e / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": scene.cams.nbytes + scene.pts.nbytes + rec.nbytes,
+                    "d2h_bytes_per_step": scene.n * 81 * 8, "ms_per_step": ms_e2e},
+            "gpu_launches": SURR_STEP_LAUNCHES * args.steps,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                         "kernel": "mlp_gemm (training step, 11 GEMMs + pack/loss/Adam, one graph node each)",
+                         "peak_source": f"bf16 burst ({src})",
+                         "note": "executed GEMM flops per training step / whole step time: launch-bound"},
+            "training": {"data_seconds": data_s, "ms_per_step": ms_train_step,
+                         "samples_per_s": B / (ms_train_step / 1e3), "loss_first": float(losses[:10].mean()),
+                         "loss_last": float(losses[-50:].mean())},
+            "accuracy_vs_exact": accuracy}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sub = synth.subscene(scene, np.arange(300))
+        t0 = time.perf_counter()
+        f_o, lz_o = S.features(sub)
+        norm = sm.normalization().astype(np.float64)
+        S.predict(S.unpack(sm.params().astype(np.float64)), f_o, lz_o,
+                  (norm[:64], norm[64:128], norm[128:173], norm[173:]))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sub.n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"features + prediction of a {sub.n}-camera sub-scene, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -7,7 +7,7 @@
  * filtering unconstrained cameras) only need a fast, approximate screen,
  * with the exact method kept as the fallback and as the judge of the error.
  *
- * Per camera i (after ccov_schur):
+ * Per camera i (after ccov_information):
  *   Z_ii     the 9x9 diagonal block of the reduced camera matrix of Sec. 4.2
  *   d        sqrt(diag Z_ii): the block's Jacobi scale
  *   L_z      the Cholesky factor of Z_ii (the `scale` arrays, 9 x 9 row-major,
@@ -54,10 +54,11 @@ extern "C" {
 
 typedef struct ccov_surrogate ccov_surrogate;
 
-/* Features and scales of every camera of a context that has run ccov_schur
- * (and not yet ccov_covariance, which consumes Z).  features: device n x 64
- * float32; scale: device n x 81 float64 (L_z).  DEGENERATE if a block Z_ii
- * is not positive definite. */
+/* Features and scales of every camera of a context that has run
+ * ccov_information.  Z_ii is accumulated from the information blocks
+ * (U_i - sum_j W_ij A_j^-1 W_ij^T), so neither the dense Z of ccov_schur nor
+ * step (d) is needed.  features: device n x 64 float32; scale: device n x 81
+ * float64 (L_z).  DEGENERATE if a block Z_ii is not positive definite. */
 CCOV_API ccov_status ccov_surrogate_features(ccov_ctx* ctx, float* features, double* scale);
 
 /* Training targets from exact covariance blocks: sigma device n x 81

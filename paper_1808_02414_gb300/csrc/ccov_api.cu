@@ -537,7 +537,7 @@ static ccov_status batch_enqueue(Ctx& c, double* out, int out_memory) {
 ccov_status ccov_surrogate_features(ccov_ctx* h, float* features, double* scale) {
     if (!h || !features || !scale) return CCOV_ERR_INVALID_ARG;
     Ctx& c = h->c;
-    if (c.stage != 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_features: needs Z (after ccov_schur)");
+    if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_features: call ccov_information first");
     ccov::surr_launch_features(c, features, scale);
     CK(cudaGetLastError(), "ccov_surrogate_features launch");
     return check_device(c, "ccov_surrogate_features");

@@ -395,18 +395,57 @@ __device__ __forceinline__ void camera_centre(const double* cp, double* c) {
     for (int a = 0; a < 3; ++a) c[a] = -(cp[a] * cp[9] + cp[3 + a] * cp[10] + cp[6 + a] * cp[11]);
 }
 
-__global__ void features_kernel(int64_t n, int64_t Np, const double* __restrict__ Z, const int* __restrict__ cam_ptr,
-                                const int* __restrict__ cam_perm, const ccov_obs* __restrict__ obs,
-                                const int* __restrict__ pt_ptr, const double* __restrict__ camprep,
-                                double* __restrict__ csum, float* __restrict__ feat, double* __restrict__ scale,
-                                int* flag) {
+// Z_ii = U_i - sum over the camera's observations of W_ij A_j^-1 W_ij^T,
+// accumulated from the information blocks (no dense Z needed): lanes take
+// the observations, the 45 lower-triangle entries are reduced over the warp.
+constexpr int kFeatWarps = 8;
+
+__global__ void __launch_bounds__(32 * kFeatWarps)
+features_kernel(int64_t n, const double* __restrict__ U, const double* __restrict__ W,
+                const double* __restrict__ Ainv, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
+                const ccov_obs* __restrict__ obs, const int* __restrict__ pt_ptr,
+                const double* __restrict__ camprep, double* __restrict__ csum, float* __restrict__ feat,
+                double* __restrict__ scale, int* flag) {
+    __shared__ double zsh[kFeatWarps][45];
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    const double* Zi = Z + 9 * i * Np + 9 * i;
+    double* zs = zsh[threadIdx.x >> 5];  // Z_ii, lower triangle row by row
+    const int o0 = cam_ptr[i], o1 = cam_ptr[i + 1];
+    {
+        double acc[45];
+#pragma unroll
+        for (int e = 0; e < 45; ++e) acc[e] = 0.0;
+        for (int q = o0 + lane; q < o1; q += 32) {
+            const int o = cam_perm[q];
+            const int j = obs[o].pt;
+            const double* w = W + 27 * (int64_t)o;
+            const double* a = Ainv + 6 * (int64_t)j;
+            const double Am[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+            double V[27];  // W A^-1
+#pragma unroll
+            for (int r = 0; r < 9; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    V[3 * r + k] = w[3 * r] * Am[k] + w[3 * r + 1] * Am[3 + k] + w[3 * r + 2] * Am[6 + k];
+            int e = 0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r)
+#pragma unroll
+                for (int c = 0; c <= r; ++c, ++e)
+                    acc[e] += V[3 * r] * w[3 * c] + V[3 * r + 1] * w[3 * c + 1] + V[3 * r + 2] * w[3 * c + 2];
+        }
+#pragma unroll
+        for (int e = 0; e < 45; ++e) {
+            double v = acc[e];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) zs[e] = U[45 * i + e] - v;
+        }
+    }
+    __syncwarp();
     double d = 1.0;
     if (lane < 9) {
-        const double zz = Zi[lane * Np + lane];
+        const double zz = zs[lane * (lane + 1) / 2 + lane];
         if (!(zz > 0.0)) set_flag(flag, DEV_NOT_SPD, (int)(9 * i + lane));
         d = zz > 0.0 ? sqrt(zz) : 1.0;
         feat[i * kIn + 36 + lane] = (float)log(d);
@@ -417,7 +456,7 @@ __global__ void features_kernel(int64_t n, int64_t Np, const double* __restrict_
         bool spd = true;
         for (int r = 0; r < 9; ++r)
             for (int c = 0; c <= r; ++c) {
-                double v = Zi[r * Np + c];
+                double v = zs[r * (r + 1) / 2 + c];
                 for (int k = 0; k < c; ++k) v -= L[r * (r + 1) / 2 + k] * L[c * (c + 1) / 2 + k];
                 if (r == c) {
                     if (!(v > 0.0)) { spd = false; v = 1.0; }
@@ -434,15 +473,14 @@ __global__ void features_kernel(int64_t n, int64_t Np, const double* __restrict_
     double dall[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) dall[k] = __shfl_sync(0xffffffffu, d, k);
-    // C_kl, k < l, row by row: pair p -> (k, l)
+    // C_kl, k < l, row by row: pair p -> (k, l); Z_kl = Z_lk from the lower triangle
     for (int p = lane; p < 36; p += 32) {
         int k = 0, rem = p;
         while (rem >= 8 - k) { rem -= 8 - k; ++k; }
         const int l = k + 1 + rem;
-        feat[i * kIn + p] = (float)(Zi[l * Np + k] / (dall[k] * dall[l]));
+        feat[i * kIn + p] = (float)(zs[l * (l + 1) / 2 + k] / (dall[k] * dall[l]));
     }
     double slog = 0.0, two = 0.0;
-    const int o0 = cam_ptr[i], o1 = cam_ptr[i + 1];
     for (int q = o0 + lane; q < o1; q += 32) {
         const int j = obs[cam_perm[q]].pt;
         const int L = pt_ptr[j + 1] - pt_ptr[j];
@@ -569,9 +607,9 @@ void surr_launch_features(Ctx& c, float* feat, double* scale) {
     using namespace surr;
     double* csum = c.d_small + 100;  // 4 slots that nothing else uses
     cudaMemsetAsync(csum, 0, 4 * sizeof(double), c.stream);
-    const int wpb = 8;
-    features_kernel<<<(unsigned)((c.n + wpb - 1) / wpb), 32 * wpb, 0, c.stream>>>(
-        c.n, c.Np, c.d_Z, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pt_ptr, c.d_camprep, csum, feat, scale, c.d_flag);
+    features_kernel<<<(unsigned)((c.n + kFeatWarps - 1) / kFeatWarps), 32 * kFeatWarps, 0, c.stream>>>(
+        c.n, c.d_U, c.d_W, c.d_Ainv, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pt_ptr, c.d_camprep, csum, feat, scale,
+        c.d_flag);
     centre_spread_kernel<<<(unsigned)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_camprep, csum);
     centre_feature_kernel<<<(unsigned)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_camprep, csum, feat);
     c.launches += 3;

@@ -33,7 +33,7 @@ def _dev(t, dtype_name: str):
 
 def features(ctx: ccov.Context):
     """(features (n, 64) float32, L_z (n, 9, 9) float64) on the device, from
-    a context that has run ccov_schur (and not yet ccov_covariance)."""
+    a context that has run ccov_information."""
     import torch
     f = torch.empty((ctx.n, N_FEATURES), dtype=torch.float32, device="cuda")
     d = torch.empty((ctx.n, 9, 9), dtype=torch.float64, device="cuda")

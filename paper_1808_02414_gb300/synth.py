@@ -19,7 +19,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
-           "subscene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices"]
+           "subscene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
+           "training_scene_specs", "training_scene"]
 
 
 @dataclass
@@ -292,3 +293,16 @@ def minibatch_indices(n: int, batch: int, steps: int, seed=0) -> np.ndarray:
     need = steps * batch
     out = np.concatenate([rng.permutation(n) for _ in range(-(-need // n))])[:need]
     return out.astype(np.int32).reshape(steps, batch)
+
+
+def training_scene_specs(k=2000, n_lo=50, n_hi=500, seed=5):
+    """(n, seed) of k training scenes for the surrogate: n ~ U{n_lo..n_hi}."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=k)
+    return [(int(nb), int(seed * 100003 + b)) for b, nb in enumerate(ns)]
+
+
+def training_scene(spec) -> Scene:
+    """Shell scene with 100 points per camera and track length 1 + Geometric(1/7) (mean 8)."""
+    n, s = spec
+    return shell_scene(n=n, m=100 * n, p_geom=1.0 / 7.0, seed=s)
