@@ -436,8 +436,8 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
 
 // Rows of a 128 x 128 FP64 matrix (the inverse of a diagonal block), per-row
 // exponent; w = round(v 2^(T - e)) is exact in double (|w| <= 2^T <= 2^47).
-__global__ void slice_f64_kernel(const double* __restrict__ src, int s, int plane_rows,
-                                 __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
+__global__ void slice_ds_kernel(const float2* __restrict__ src, int s, int plane_rows,
+                                __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= kNB) return;
@@ -445,7 +445,8 @@ __global__ void slice_f64_kernel(const double* __restrict__ src, int s, int plan
     double mx = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        v[q] = src[r * kNB + lane + 32 * q];
+        const float2 x = src[r * kNB + lane + 32 * q];
+        v[q] = (double)x.x + (double)x.y;
         mx = fmax(mx, fabs(v[q]));
     }
 #pragma unroll
@@ -482,64 +483,196 @@ __global__ void zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, c
     *q = llrint(ldexp(D[i] * v * D[j], kFL));
 }
 
-// Cholesky of the 128 x 128 diagonal block from Q60 in FP64 shared memory
-// (L in the lower triangle, its inverse transposed in the upper one), L
-// written back as Q60, the inverse as FP64 (full, zero above the diagonal).
+// Double-single arithmetic: a value is an unevaluated sum hi + lo of two
+// floats (about 44 significant bits; Dekker 1971, with the products split
+// by FMA).  GB300 issues FP32 about eighty times faster than FP64 per SM,
+// and the digits that the tensor-core products keep of L and L^-1 hold 39
+// bits, so the one-CTA factorisation of a diagonal block runs in this form.
+// Explicit _rn intrinsics keep the compiler from contracting the
+// error-free transformations.
+struct dsf {
+    float h, l;
+};
+
+// acc + a * b
+__device__ __forceinline__ dsf ds_fma(dsf acc, dsf a, dsf b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const float s = __fadd_rn(acc.h, p);
+    const float v = __fsub_rn(s, acc.h);
+    float t = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, v)), __fsub_rn(p, v));
+    t = __fadd_rn(t, __fadd_rn(acc.l, e));
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.h, -a.l}; }
+
+// Q60 fixed point <-> double-single, with integer conversions only: v =
+// f + r exactly with f = v rounded to a float (an integer value) and r the
+// remainder (|r| <= 2^39); the power-of-two scalings are exact in float.
+__device__ __forceinline__ dsf ds_from_q60(long long v) {
+    const float f = __ll2float_rn(v);
+    const long long r = v - __float2ll_rz(f);
+    constexpr float kS = 8.673617379884035e-19f;  // 2^-60
+    return {__fmul_rn(f, kS), __fmul_rn(__ll2float_rn(r), kS)};
+}
+
+__device__ __forceinline__ long long ds_to_q60(dsf a) {
+    constexpr float kU = 1.152921504606847e18f;  // 2^60
+    return __float2ll_rn(__fmul_rn(a.h, kU)) + __float2ll_rn(__fmul_rn(a.l, kU));
+}
+
+__device__ __forceinline__ dsf ds_mul(dsf a, dsf b) { return ds_fma({0.f, 0.f}, a, b); }
+
+// sqrt(d), 1 / sqrt(d) and 1 / d: one Newton step on the float estimate of
+// 1 / sqrt(d) doubles its 22 correct bits.
+__device__ __forceinline__ void ds_sqrt_inv(dsf d, dsf& l, dsf& inv, dsf& inv2) {
+    const float y0 = rsqrtf(d.h);
+    const dsf y = {y0, 0.f};
+    const dsf e = ds_fma({1.f, 0.f}, ds_neg(d), ds_mul(y, y));  // 1 - d y0^2
+    inv = ds_fma(y, {0.5f * y0, 0.f}, e);                      // y0 + y0 (1 - d y0^2) / 2
+    l = ds_mul(d, inv);
+    inv2 = ds_mul(inv, inv);
+}
+
+
+// Cholesky of the 128 x 128 diagonal block from Q60 (L in the lower
+// triangle, its inverse X = L^-1 transposed in the upper one, both in
+// double-single shared memory), L written back as Q60, X as double-single
+// pairs (full, zero above the diagonal).  Blocked by 32-column panels: all
+// threads factor the panel's diagonal block column by column, invert it
+// column sweep by column sweep, solve the rows below with that inverse and
+// update the trailing block; the off-diagonal blocks of X then follow by
+// block rows, X_ij = -X_ii sum_k L_ik X_kj.
 constexpr int kLD = kNB + 1;
+constexpr int kPW = 32;                                   // panel width
+constexpr size_t kDiagSmem = sizeof(dsf) * (kNB * kLD + kNB + 3 * kPW * kPW);
 __global__ void __launch_bounds__(512)
 potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, double* __restrict__ Linv, int* flag) {
-    extern __shared__ __align__(16) double S[];   // 128 x 129, then 128 inverse diagonal
-    double* invd = S + kNB * kLD;
-    const int tid = threadIdx.x;
-    const int tx = tid & 31, ty = tid >> 5;  // 32 x 16
-    const double sc = ldexp(1.0, -kFL);
+    extern __shared__ __align__(16) dsf S[];      // 128 x 129
+    dsf* invd = S + kNB * kLD;                    // 1 / L_jj
+    dsf* T = invd + kNB;                          // 3 x 32 x 32: one block row of sum_k L_ik X_kj
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < kNB * kNB; e += 512) {
         int i = e >> 7, j = e & 127;
-        if (j <= i) S[i * kLD + j] = (double)Z[(k0 + i) * ld + k0 + j] * sc;
+        if (j <= i) S[i * kLD + j] = ds_from_q60(Z[(k0 + i) * ld + k0 + j]);
     }
+    // update pair of this thread inside a 32 x 32 diagonal block: the
+    // tid-th (row, column) of a lower triangle, row by row
+    int tr = (int)((sqrtf(8.f * (float)tid + 1.f) - 1.f) * 0.5f);
+    while ((tr + 1) * (tr + 2) / 2 <= tid) ++tr;
+    while (tr * (tr + 1) / 2 > tid) --tr;
+    const int tk = tid - tr * (tr + 1) / 2;
     __syncthreads();
-    for (int j = 0; j < kNB; ++j) {
-        if (tid == 0) {
-            double d = S[j * kLD + j];
-            if (!(d > 0.0)) { set_flag(flag, DEV_NOT_SPD, (int)(k0 + j)); d = 1.0; }
-            double l = sqrt(d);
-            S[j * kLD + j] = l;
-            invd[j] = 1.0 / l;
+    for (int p = 0; p < kNB / kPW; ++p) {
+        const int b0 = kPW * p;
+        // diagonal block, right-looking over its 32 columns with all threads:
+        // column jj is used unscaled (with 1 / L_jj^2) and scaled one step later
+        for (int jj = 0; jj < kPW; ++jj) {
+            const int j = b0 + jj;
+            if (tid == 0) {
+                dsf d = S[j * kLD + j];
+                if (!(d.h > 0.f)) { set_flag(flag, DEV_NOT_SPD, (int)(k0 + j)); d = {1.f, 0.f}; }
+                dsf l, inv, inv2;
+                ds_sqrt_inv(d, l, inv, inv2);
+                S[j * kLD + j] = l;
+                invd[j] = inv;
+                T[jj] = inv2;
+            } else if (jj > 0 && warp == 1 && lane > jj - 1) {
+                S[(b0 + lane) * kLD + j - 1] = ds_mul(S[(b0 + lane) * kLD + j - 1], invd[j - 1]);
+            }
+            __syncthreads();
+            const int m = kPW - 1 - jj;  // rows (and columns) below jj
+            if (tid < m * (m + 1) / 2) {
+                const int r = b0 + jj + 1 + tr, k = b0 + jj + 1 + tk;
+                const dsf t = ds_mul(S[k * kLD + j], T[jj]);
+                S[r * kLD + k] = ds_fma(S[r * kLD + k], ds_neg(S[r * kLD + j]), t);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const double iv = invd[j];
-        for (int i = j + 1 + tid; i < kNB; i += 512) S[i * kLD + j] *= iv;
-        __syncthreads();
-        for (int i = j + 1 + ty; i < kNB; i += 16) {
-            const double lij = S[i * kLD + j];
-            for (int l = j + 1 + tx; l <= i; l += 32) S[i * kLD + l] -= lij * S[l * kLD + j];
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < kNB * kNB; e += 512) {
-        int i = e >> 7, j = e & 127;
-        if (j <= i) Z[(k0 + i) * ld + k0 + j] = llrint(ldexp(S[i * kLD + j], kFL));
-    }
-    // X = L^-1 row by row: X[i][c] = -(sum_{k=c}^{i-1} L[i][k] X[k][c]) / L[i][i],
-    // X[k][c] kept at S[c][k] (upper triangle); 4 threads per column c
-    const int c = tid >> 2, part = tid & 3;
-    for (int i = 1; i < kNB; ++i) {
-        double sum = 0.0;
-        if (c < i) {
-            for (int k = c + part; k < i; k += 4) {
-                const double xkc = (k == c) ? invd[c] : S[c * kLD + k];
-                sum += S[i * kLD + k] * xkc;
+        // X_pp = L_pp^-1 by column sweeps: row j of X is scaled by 1/L_jj, then
+        // removed from the rows below; X[r][c] (r > c) lives at S[c][r]
+        {
+            const int r = tid >> 4, c2 = (tid & 15) * 2;   // 32 rows x 16 threads, 2 columns each
+            for (int jj = 0; jj < kPW; ++jj) {
+                // X[jj][c] = (delta_jc - sum_{k<jj} L[jj][k] X[k][c]) / L[jj][jj] was formed
+                // by the earlier sweeps; finish row jj, then eliminate it below
+                if (r == jj) {
+                    for (int q = 0; q < 2; ++q) {
+                        const int c = c2 + q;
+                        if (c < jj) {
+                            S[(b0 + c) * kLD + b0 + jj] = ds_mul(S[(b0 + c) * kLD + b0 + jj], invd[b0 + jj]);
+                        }
+                    }
+                }
+                __syncthreads();
+                if (r > jj) {
+                    const dsf l = ds_neg(S[(b0 + r) * kLD + b0 + jj]);
+                    for (int q = 0; q < 2; ++q) {
+                        const int c = c2 + q;
+                        if (c > jj || c >= r) continue;
+                        // X[r][c] += -L[r][jj] X[jj][c]; X[jj][jj] = invd, X[r][c] starts at 0
+                        const dsf xjc = c == jj ? invd[b0 + jj] : S[(b0 + c) * kLD + b0 + jj];
+                        dsf* xr = &S[(b0 + c) * kLD + b0 + r];
+                        *xr = ds_fma(c == jj ? dsf{0.f, 0.f} : *xr, l, xjc);
+                    }
+                }
+                __syncthreads();
             }
         }
-        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (b0 + kPW == kNB) break;
+        // rows below: L[i][b0 + c] = sum_{k <= c} A[i][b0 + k] X_pp[c][k], one thread per entry
+        const int rows = kNB - b0 - kPW;
+        for (int e = tid; e < rows * kPW; e += 512) {
+            const int i = b0 + kPW + e / kPW, c = e % kPW;
+            dsf v = ds_mul(S[i * kLD + b0 + c], invd[b0 + c]);
+            for (int k = 0; k < c; ++k) v = ds_fma(v, S[i * kLD + b0 + k], S[(b0 + k) * kLD + b0 + c]);
+            T[e] = v;
+        }
         __syncthreads();
-        if (c < i && part == 0) S[c * kLD + i] = -sum * invd[i];
+        for (int e = tid; e < rows * kPW; e += 512) S[(b0 + kPW + e / kPW) * kLD + b0 + e % kPW] = T[e];
+        __syncthreads();
+        // trailing update of the lower triangle below and right of the panel
+        const int t0 = b0 + kPW, w = kNB - t0;
+        for (int e = tid; e < w * w; e += 512) {
+            const int i = t0 + e / w, l = t0 + e % w;
+            if (l > i) continue;
+            dsf v = S[i * kLD + l];
+            for (int k = 0; k < kPW; ++k) v = ds_fma(v, ds_neg(S[i * kLD + b0 + k]), S[l * kLD + b0 + k]);
+            S[i * kLD + l] = v;
+        }
         __syncthreads();
     }
+    // off-diagonal blocks of X by block rows; X[r][c] (r > c) lives at S[c][r]
+    for (int bi = 1; bi < kNB / kPW; ++bi) {
+        const int r0 = kPW * bi;
+        for (int e = tid; e < bi * kPW * kPW; e += 512) {
+            const int bj = e / (kPW * kPW), r = (e / kPW) % kPW, cc = e % kPW;
+            const int col = kPW * bj + cc;
+            dsf v = ds_mul(S[(r0 + r) * kLD + col], invd[col]);
+            for (int k = col + 1; k < r0; ++k) v = ds_fma(v, S[(r0 + r) * kLD + k], S[col * kLD + k]);
+            T[e] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < bi * kPW * kPW; e += 512) {
+            const int bj = e / (kPW * kPW), r = (e / kPW) % kPW, cc = e % kPW;
+            const int col = kPW * bj + cc;
+            const dsf* Tb = T + bj * kPW * kPW;
+            dsf v = ds_mul(invd[r0 + r], Tb[r * kPW + cc]);
+            for (int k = 0; k < r; ++k) v = ds_fma(v, S[(r0 + k) * kLD + r0 + r], Tb[k * kPW + cc]);
+            S[col * kLD + r0 + r] = ds_neg(v);
+        }
+        __syncthreads();
+    }
+    float2* Xo = reinterpret_cast<float2*>(Linv);
     for (int e = tid; e < kNB * kNB; e += 512) {
         int i = e >> 7, j = e & 127;
-        Linv[e] = (j < i) ? S[j * kLD + i] : (j == i ? invd[i] : 0.0);
+        if (j <= i) Z[(k0 + i) * ld + k0 + j] = ds_to_q60(S[i * kLD + j]);
+        const dsf x = (j < i) ? S[j * kLD + i] : (j == i ? invd[i] : dsf{0.f, 0.f});
+        Xo[e] = make_float2(x.h, x.l);
     }
 }
 
@@ -703,14 +836,14 @@ void slice_cols(Ctx& c, int K, int ncols, const long long* src, Buf b) {
 
 void slice_linv(Ctx& c, const double* Linv, Buf b) {
     MixedState& st = *c.mixed;
-    slice_f64_kernel<<<kNB / 8, 256, 0, c.stream>>>(Linv, st.s, (int)c.Np, b == BUF_P ? st.digP : st.digQ,
+    slice_ds_kernel<<<kNB / 8, 256, 0, c.stream>>>(reinterpret_cast<const float2*>(Linv), st.s, (int)c.Np, b == BUF_P ? st.digP : st.digQ,
                                                      b == BUF_P ? st.expP : st.expQ);
     c.launches++;
 }
 
 void potrf_block(Ctx& c, int64_t blk) {
     long long* Zq = reinterpret_cast<long long*>(c.d_Z);
-    potrf_diag_q_kernel<<<1, 512, sizeof(double) * (kNB * kLD + kNB), c.stream>>>(
+    potrf_diag_q_kernel<<<1, 512, kDiagSmem, c.stream>>>(
         Zq, c.Np, blk * kNB, c.d_Linv + blk * kNB * kNB, c.d_flag);
     c.launches++;
 }
@@ -742,7 +875,7 @@ cudaError_t mixed_alloc(Ctx& c) {
     for (cudaError_t x : a)
         if (x != cudaSuccess) return x;
     if ((e = cudaFuncSetAttribute(potrf_diag_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(double) * (kNB * kLD + kNB)))) != cudaSuccess)
+                                  (int)kDiagSmem)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(slice_cols_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   256 * 33 * 8)) != cudaSuccess)
