@@ -370,33 +370,61 @@ __device__ __forceinline__ long long round_shift(long long v, int sh) {
     return (v + (1ll << (-sh - 1))) >> (-sh);
 }
 
-// Rows of an int64 Q(F) matrix, K = 128 or 256 values per row, exponent 0
-// (entries of the scaled factor are bounded by 1).  One warp per row.
-template <int K>
-__global__ void slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s,
-                                  int plane_rows, __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= rows) return;
-    if (lane == 0) expo[r] = 0;
-    const int T = 7 + 8 * (s - 1);
+// Digits of eight values consecutive along K (w already in units of the
+// last digit), plane by plane from the least significant one; each plane's
+// eight digits (a core-matrix row) go out as one 16-byte store.
+__device__ __forceinline__ void split_store8(long long* w, int s, __nv_bfloat16* dst0, int64_t plane_stride) {
+    for (int a = s - 1; a >= 0; --a) {
+        float dv[8];
 #pragma unroll
-    for (int q = 0; q < K / 32; ++q) {
-        float d[7];
-        split_digits(round_shift(src[(int64_t)r * ld + lane + 32 * q], T - F), s, d);
-        for (int a = 0; a < s; ++a)
-            dst[blk_off(a, r, lane + 32 * q, K, plane_rows)] = __float2bfloat16_rn(d[a]);
+        for (int j = 0; j < 8; ++j) {
+            if (a > 0) {
+                const long long lo = ((w[j] + 128) & 255) - 128;
+                dv[j] = (float)lo;
+                w[j] = (w[j] - lo) >> 8;
+            } else {
+                dv[j] = (float)w[j];
+            }
+        }
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(dv[2 * j], dv[2 * j + 1]);
+        *reinterpret_cast<uint4*>(dst0 + a * plane_stride) = *reinterpret_cast<const uint4*>(h);
     }
+}
+
+// Rows of an int64 Q(F) matrix, K = 128 or 256 values per row, exponent 0
+// (entries of the scaled factor are bounded by 1).  A thread takes eight
+// consecutive values of a row and writes each digit plane with one store.
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
+                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
+    constexpr int G = K / 8;  // groups of eight per row
+    const int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = (int)(item / G), g = (int)(item % G);
+    if (r >= rows) return;
+    if (g == 0) expo[r] = 0;
+    const int T = 7 + 8 * (s - 1);
+    const long long* p = src + (int64_t)r * ld + 8 * g;
+    long long w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = round_shift(p[j], T - F);
+    split_store8(w, s, dst + blk_off(0, r, 8 * g, K, plane_rows), blk_off(1, 0, 0, K, plane_rows));
 }
 
 // Column split: a K-row block (K = 128 or 256) of an int64 Q(F) matrix,
 // columns [0, ncols), transposed into digit rows (row = source column,
-// K = source rows), per-column exponent from the column maximum.
+// K = source rows), per-column exponent from the column maximum.  The block
+// stages 32 columns in shared memory; a warp finds each column's exponent,
+// then a thread splits eight consecutive source rows of a column and writes
+// each digit plane with one 16-byte store.
 template <int K>
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
                   __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
     extern __shared__ __align__(16) long long tile[];   // [K][33]
+    __shared__ int cexp[32];
     const int c0 = blockIdx.x * 32;
     const int tid = threadIdx.x;
     for (int e = tid; e < K * 32; e += 256) {
@@ -405,16 +433,12 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
     }
     __syncthreads();
     const int lane = tid & 31, w = tid >> 5;
-    const int T = 7 + 8 * (s - 1);
     for (int c = w; c < 32; c += 8) {
-        const int col = c0 + c;
-        if (col >= ncols) break;
-        long long v[K / 32];
         unsigned long long mx = 0;
 #pragma unroll
         for (int q = 0; q < K / 32; ++q) {
-            v[q] = tile[(lane + 32 * q) * 33 + c];
-            unsigned long long a = (unsigned long long)(v[q] < 0 ? -v[q] : v[q]);
+            const long long v = tile[(lane + 32 * q) * 33 + c];
+            const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
             mx = a > mx ? a : mx;
         }
 #pragma unroll
@@ -422,15 +446,24 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
             unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
             mx = t > mx ? t : mx;
         }
-        const int e = mx == 0 ? 0 : (64 - __clzll((long long)mx)) - F;
-        if (lane == 0) expo[col] = e;
-#pragma unroll
-        for (int q = 0; q < K / 32; ++q) {
-            float d[7];
-            split_digits(round_shift(v[q], T - e - F), s, d);
-            for (int a = 0; a < s; ++a)
-                dst[blk_off(a, col, lane + 32 * q, K, plane_rows)] = __float2bfloat16_rn(d[a]);
+        if (lane == 0) {
+            const int e = mx == 0 ? 0 : (64 - __clzll((long long)mx)) - F;
+            cexp[c] = e;
+            if (c0 + c < ncols) expo[c0 + c] = e;
         }
+    }
+    __syncthreads();
+    const int T = 7 + 8 * (s - 1);
+    constexpr int G = K / 8;
+    for (int item = tid; item < 32 * G; item += 256) {
+        const int c = item / G, g = item % G;
+        const int col = c0 + c;
+        if (col >= ncols) continue;
+        const int e = cexp[c];
+        long long w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = round_shift(tile[(8 * g + j) * 33 + c], T - e - F);
+        split_store8(w, s, dst + blk_off(0, col, 8 * g, K, plane_rows), blk_off(1, 0, 0, K, plane_rows));
     }
 }
 
@@ -513,11 +546,14 @@ __device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.h, -a.l}; }
 // Q60 fixed point <-> double-single, with integer conversions only: v =
 // f + r exactly with f = v rounded to a float (an integer value) and r the
 // remainder (|r| <= 2^39); the power-of-two scalings are exact in float.
-__device__ __forceinline__ dsf ds_from_q60(long long v) {
+__device__ __forceinline__ dsf ds_from_fixed(long long v, float scale) {
     const float f = __ll2float_rn(v);
     const long long r = v - __float2ll_rz(f);
-    constexpr float kS = 8.673617379884035e-19f;  // 2^-60
-    return {__fmul_rn(f, kS), __fmul_rn(__ll2float_rn(r), kS)};
+    return {__fmul_rn(f, scale), __fmul_rn(__ll2float_rn(r), scale)};
+}
+
+__device__ __forceinline__ dsf ds_from_q60(long long v) {
+    return ds_from_fixed(v, 8.673617379884035e-19f);  // 2^-60
 }
 
 __device__ __forceinline__ long long ds_to_q60(dsf a) {
@@ -677,28 +713,29 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, double* _
 }
 
 // Camera Gram blocks Sig_c += X[k, c]^T X[k, c] from the finished Q42 row
-// block k of X (128 rows), 4 cameras (36 columns) per CTA.
+// block k of X (128 rows), 4 cameras (36 columns) per CTA, summed in
+// double-single arithmetic and added to the FP64 blocks once.
 constexpr int kGW = 36;
 __global__ void __launch_bounds__(128)
 gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long* __restrict__ R,
               double* __restrict__ Sig) {
-    __shared__ double T[kNB][kGW + 1];
+    __shared__ dsf T[kNB][kGW + 1];
     const int tid = threadIdx.x;
     const int64_t c0 = blockIdx.x * (int64_t)kGW;
-    const double sc = ldexp(1.0, -kFX);
+    constexpr float kS = 2.2737367544323206e-13f;  // 2^-42
     for (int e = tid; e < kNB * kGW; e += 128) {
         int r = e / kGW, c = e % kGW;
         int64_t gc = c0 + c;
-        T[r][c] = (gc < ncols) ? (double)R[(k0 + r) * Np + gc] * sc : 0.0;
+        T[r][c] = (gc < ncols) ? ds_from_fixed(R[(k0 + r) * Np + gc], kS) : dsf{0.f, 0.f};
     }
     __syncthreads();
     for (int e = tid; e < 4 * 81; e += 128) {
         int g = e / 81, ab = e % 81, a = ab / 9, b = ab % 9;
         int64_t cam = (c0 / 9) + g;
         if (cam >= n || c0 + 9 * g >= ncols) continue;
-        double v = 0.0;
-        for (int r = 0; r < kNB; ++r) v += T[r][9 * g + a] * T[r][9 * g + b];
-        Sig[81 * cam + ab] += v;
+        dsf v = {0.f, 0.f};
+        for (int r = 0; r < kNB; ++r) v = ds_fma(v, T[r][9 * g + a], T[r][9 * g + b]);
+        Sig[81 * cam + ab] += (double)v.h + (double)v.l;
     }
 }
 
@@ -813,7 +850,7 @@ void slice_rows(Ctx& c, int K, int rows, const long long* src, Buf b) {
     MixedState& st = *c.mixed;
     __nv_bfloat16* dst = b == BUF_P ? st.digP : st.digQ;
     int* ex = b == BUF_P ? st.expP : st.expQ;
-    const int grid = (rows + 7) / 8;
+    const int grid = (int)(((int64_t)rows * (K / 8) + 255) / 256);
     if (K == 256)
         slice_rows_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex);
     else
