@@ -45,12 +45,13 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;              // producer, MMA, epi
 
 struct MixedState {
     int s = 5;
-    __nv_bfloat16* digP = nullptr;   // [s][Np][K] digit planes, row stride K (128 or 256)
+    __nv_bfloat16* digP = nullptr;   // s digit planes of Np rows x 256, layout of blk_off
     __nv_bfloat16* digQ = nullptr;
     int* expP = nullptr;             // Np
     int* expQ = nullptr;             // Np
     long long* R = nullptr;          // Np x Np, Q42
     CUtensorMap mapZ, mapR;          // int64 result maps
+    CUtensorMap mapBP, mapBQ;        // B-operand views of digP and digQ
     int64_t tiles_done = 0;
 };
 
@@ -61,14 +62,16 @@ using namespace ptx;
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
 // Digit planes are stored in the order the tensor cores read K-major
-// operands without swizzle: per plane, per 16-wide slice of K and per block of
-// 128 rows, one contiguous 4 KB block of 16 groups of 8 rows, each group two
-// 8 x 8 core matrices (8 rows x 16 bytes) along K.  A stage of the pipeline
-// is then a handful of contiguous bulk copies.
-__host__ __device__ __forceinline__ int64_t blk_off(int plane, int r, int k, int K, int plane_rows) {
+// operands without swizzle: per 16-wide slice of K, per block of 128 rows
+// and per plane, one contiguous 4 KB block of 16 groups of 8 rows, each
+// group two 8 x 8 core matrices (8 rows x 16 bytes) along K.  The S planes
+// of one row block and K slice are adjacent, so a pipeline stage takes the
+// A tile of all planes as one bulk copy and the 64-row B tile of all planes
+// (every other 2 KB half block) as one tensor copy.
+__host__ __device__ __forceinline__ int64_t blk_off(int plane, int r, int k, int plane_rows, int S) {
     const int64_t rb = plane_rows / 128;
-    return ((((int64_t)plane * (K / 16) + (k >> 4)) * rb + (r >> 7)) << 11) + (((r & 127) >> 3) << 7) +
-           (((k & 15) >> 3) << 6) + ((r & 7) << 3) + (k & 7);
+    return (((((int64_t)(k >> 4) * rb + (r >> 7)) * S + plane) << 11) + (((r & 127) >> 3) << 7) +
+           (((k & 15) >> 3) << 6) + ((r & 7) << 3) + (k & 7));
 }
 
 // Accumulators of the digit orders.  Order g = a + b collects the products
@@ -149,7 +152,7 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
 // (load of C overlapped with the MMAs of the same tile, store asynchronous).
 template <int S, int K>
 __global__ void __launch_bounds__(kThreads, 1)
-ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB, GemmArgs g) {
     using SL = Slots<S, K>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -210,16 +213,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, GemmArgs g) {
                     if (!mbar_wait(empty + stage, phase ^ 1, g.flag, 1)) { ok = false; break; }
                     unsigned char* st = tiles + stage * stage_bytes;
                     mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
-#pragma unroll
-                    for (int p = 0; p < S; ++p) {
-                        if ((p & 1) == (int)rank)  // A: half of the planes each, to both CTAs
-                            bulk_load_mc(st + p * kAPl,
-                                         g.digA + blk_off(p, g.a_row0 + ti * kBM, ks * kKS, K, g.plane_rows), kAPl,
-                                         full + stage, kBoth);
-                        bulk_load(st + S * kAPl + p * kBPl,
-                                  g.digB + blk_off(p, g.b_row0 + tj * kBN, ks * kKS, K, g.plane_rows), kBPl,
-                                  full + stage);
-                    }
+                    // A: planes [pa0, pa1) of the tile, one copy sent to both CTAs
+                    const int pa0 = rank ? (S + 1) / 2 : 0, pa1 = rank ? S : (S + 1) / 2;
+                    bulk_load_mc(st + pa0 * kAPl, g.digA + blk_off(pa0, g.a_row0 + ti * kBM, ks * kKS, g.plane_rows, S),
+                                 (uint32_t)((pa1 - pa0) * kAPl), full + stage, kBoth);
+                    // B: this CTA's 64 rows of every plane, one tensor copy
+                    const int br = g.b_row0 + tj * kBN;
+                    tma_load_5d(st + S * kAPl, &mapB, full + stage, 0, 0, (br >> 6) & 1, 0,
+                                ks * (g.plane_rows >> 7) + (br >> 7));
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
             }
@@ -410,7 +411,7 @@ slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F
     long long w[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) w[j] = round_shift(p[j], T - F);
-    split_store8(w, s, dst + blk_off(0, r, 8 * g, K, plane_rows), blk_off(1, 0, 0, K, plane_rows));
+    split_store8(w, s, dst + blk_off(0, r, 8 * g, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
 }
 
 // Column split: a K-row block (K = 128 or 256) of an int64 Q(F) matrix,
@@ -463,7 +464,7 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
         long long w[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) w[j] = round_shift(tile[(8 * g + j) * 33 + c], T - e - F);
-        split_store8(w, s, dst + blk_off(0, col, 8 * g, K, plane_rows), blk_off(1, 0, 0, K, plane_rows));
+        split_store8(w, s, dst + blk_off(0, col, 8 * g, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
     }
 }
 
@@ -493,7 +494,7 @@ __global__ void slice_ds_kernel(const float2* __restrict__ src, int s, int plane
         float d[7];
         split_digits(llrint(ldexp(v[q], T - e)), s, d);
         for (int a = 0; a < s; ++a)
-            dst[blk_off(a, r, lane + 32 * q, kNB, plane_rows)] = __float2bfloat16_rn(d[a]);
+            dst[blk_off(a, r, lane + 32 * q, plane_rows, s)] = __float2bfloat16_rn(d[a]);
     }
 }
 
@@ -771,6 +772,20 @@ bool make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, in
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The B-operand view of a digit buffer: (128 elements of an 8-row group,
+// 8 groups, 2 halves of a 128-row block, s planes, K slice x row block).
+bool make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[5] = {128, 8, 2, (cuuint64_t)s, (cuuint64_t)(kKMax / 16) * (cuuint64_t)(Np / 128)};
+    cuuint64_t strides[4] = {256, 2048, 4096, (cuuint64_t)s * 4096};
+    cuuint32_t box[5] = {128, 8, 1, (cuuint32_t)s, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 size_t gemm_smem(int s, int stages) {
     return 1024 + (size_t)kCTile + (size_t)stages * s * (kAPl + kBPl) + 8 * (2 * stages + 4) + 16;
 }
@@ -826,7 +841,8 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-#define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_>, mapC, g)
+    const CUtensorMap& mapB = bb == BUF_P ? st.mapBP : st.mapBQ;
+#define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_>, mapC, mapB, g)
     if (K == 256) {
         switch (st.s) {
             case 4: CCOV_OZ(4, 256); break;
@@ -907,6 +923,8 @@ cudaError_t mixed_alloc(Ctx& c) {
     if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
     if (c.d_Z && !make_c_map(&st.mapZ, reinterpret_cast<long long*>(c.d_Z), Np, Np, Np)) return cudaErrorInvalidValue;
     if (!make_c_map(&st.mapR, st.R, Np, Np, Np)) return cudaErrorInvalidValue;
+    if (!make_b_map(&st.mapBP, st.digP, st.s, Np) || !make_b_map(&st.mapBQ, st.digQ, st.s, Np))
+        return cudaErrorInvalidValue;
     cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
                         set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
     for (cudaError_t x : a)
@@ -1047,7 +1065,7 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
             for (int a = 0; a < s; ++a)
                 for (int r = 0; r < c.Np; ++r)
                     for (int k = 0; k < K; ++k) {
-                        const int64_t o = blk_off(a, r, k, K, (int)c.Np);
+                        const int64_t o = blk_off(a, r, k, (int)c.Np, s);
                         if (r < M) ha[o] = digA[((size_t)a * M + r) * K + k];
                         if (r < N) hb[o] = digB[((size_t)a * N + r) * K + k];
                     }
