@@ -40,8 +40,9 @@ constexpr int kCTile = 4 * kCBox;                          // 64 KB result tile 
 constexpr int kFX = 42;                                    // fixed point of X = L^-1
 constexpr int kFL = 60;                                    // fixed point of Z_s and L
 constexpr int kKMax = 256;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;              // producer, MMA, epilogue warps
+constexpr int kEpiCols = kBN / (kEpiWarps / 4);            // tile columns per epilogue thread
 
 struct MixedState {
     int s = 5;
@@ -147,8 +148,8 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
 // work on the two halves (adjacent 64-column tiles) of one 128 x 128 block:
 // they need the same A tile, and each CTA loads half of its digit planes and
 // multicasts them to both.  Warp 0 lane 0: producer of the digit tiles.  Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps
-// 2..9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one half of
-// the 64 columns, and the result tile goes through shared memory with TMA
+// 2..17: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter
+// of the 64 columns, and the result tile goes through shared memory with TMA
 // (load of C overlapped with the MMAs of the same tile, store asynchronous).
 template <int S, int K>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -269,7 +270,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
         }
     } else {
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;   // which kEpiCols columns
         const int r = 32 * quarter + lane;  // row in the tile = TMEM lane
         const bool leader = (warp == 2 && lane == 0);
         uint32_t acc_phase = 0, c_phase = 0;
@@ -292,10 +293,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             // then release TMEM so that the next tile's MMAs start at once
             const int eA = g.expA ? g.expA[g.a_row0 + ti * kBM + r] : 0;
             const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
-            long long res[32];
+            long long res[kEpiCols];
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int col0 = 32 * half + 8 * cc;  // column within the tile
+            for (int cc = 0; cc < kEpiCols / 8; ++cc) {
+                const int col0 = kEpiCols * part + 8 * cc;  // column within the tile
                 float v[SL::total][8];
 #pragma unroll
                 for (int sl = 0; sl < SL::total; ++sl) tmem_ld8(trow + (uint32_t)(sl * kBN + col0), v[sl]);
@@ -324,8 +325,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
                 c_phase ^= 1;
             }
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int col = 32 * half + q;
+            for (int q = 0; q < kEpiCols; ++q) {
+                const int col = kEpiCols * part + q;
                 // 128-byte swizzle: 16-byte chunk index XOR (row % 8)
                 const int box = col >> 4, jj = col & 15;
                 long long* cp = (long long*)(ctile + box * kCBox + r * 128 +
