@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="shell4k")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--cpu-sample-cams", type=int, default=800)
+    ap.add_argument("--cpu-sample-cams", type=int, default=900)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--surr-scenes", type=int, default=2000)
