@@ -5,7 +5,9 @@ A step is one pass of the whole path on one scene: ccov_information ->
 ccov_schur -> ccov_nullspace -> ccov_covariance (steps (a)-(d)).  The
 workload is the synthetic 4000-camera shell scene (400k points, track length
 1 + Geometric(1/7), about 3.2M observations, reduced camera matrix
-36000 x 36000).  `value` = cameras / s with the inputs resident on the device;
+36000 x 36000).  For the mixed form the line also carries one pass of the
+plain FP64 GPU form on the same scene (`vs_fp64_gpu`: its time and the mixed
+blocks' relative Frobenius error against it).  `value` = cameras / s with the inputs resident on the device;
 `e2e` = the same through the C ABI with host buffers (host-to-device upload and
 the device-to-host copy of the 9x9 blocks inside every timed step).
 
@@ -53,6 +55,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--cpu-sample-cams", type=int, default=900)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--surr-scenes", type=int, default=2000)
     ap.add_argument("--surr-epochs", type=int, default=30)
@@ -325,6 +328,26 @@ def run_ours(args):
             "phases_ms": {k: last[k] for k in ("ms_information", "ms_schur", "ms_nullspace",
                                                 "ms_covariance", "ms_factor", "ms_inverse")}}
     ctx.close()
+    if prec == ccov.CCOV_PREC_MIXED and not args.no_fp64_check:
+        # the same scene through the plain FP64 GPU form, once: its time and the
+        # mixed form's per-block error against it
+        mixed = out.cpu().numpy()
+        ref = torch.empty_like(out)
+        with ccov.Context(cams, pts, obs, scene.sigma, precision=ccov.CCOV_PREC_FP64,
+                          stream=stream.cuda_stream) as c64:
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            c64.run(out=ref)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = g0.elapsed_time(g1)
+        ref = ref.cpu().numpy()
+        err = np.linalg.norm(mixed - ref, axis=(1, 2)) / np.linalg.norm(ref, axis=(1, 2))
+        line["vs_fp64_gpu"] = {"ms_per_step": ms64, "value": scene.n / (ms64 / 1e3), "unit": UNIT,
+                               "speedup_of_mixed": ms64 / ms_step,
+                               "max_rel_fro_per_block": float(err.max()),
+                               "median_rel_fro_per_block": float(np.median(err))}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub, dt = cpu_oracle_sample(scene, args.cpu_sample_cams)
         line["cpu_baseline"] = {"value": sub.n / dt, "unit": UNIT, "cores": os.cpu_count(),
