@@ -26,6 +26,9 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <utility>
+#include <vector>
+
 #include "ccov_internal.cuh"
 #include "tc_ptx.cuh"
 #include "../../include/ccov_testing.h"
@@ -53,7 +56,24 @@ struct MixedState {
     long long* R = nullptr;          // Np x Np, Q42
     CUtensorMap mapZ, mapR;          // int64 result maps
     CUtensorMap mapBP, mapBQ;        // B-operand views of digP and digQ
+    // the triangular inverse runs on a second stream with a second set of
+    // digit buffers, behind the Cholesky one pair of sub-panels at a time
+    __nv_bfloat16 *digP2 = nullptr, *digQ2 = nullptr;
+    int *expP2 = nullptr, *expQ2 = nullptr;
+    CUtensorMap mapBP2, mapBQ2;
+    cudaStream_t side = nullptr;     // triangular inverse, lowest priority
+    cudaStream_t hi = nullptr;       // Cholesky (the critical path), highest priority
+    std::vector<cudaEvent_t> ev;     // [0] fork, [1] inverse done, [2] Cholesky done, [3 + k] pair k final
     int64_t tiles_done = 0;
+
+    void swap_sets() {
+        std::swap(digP, digP2);
+        std::swap(digQ, digQ2);
+        std::swap(expP, expP2);
+        std::swap(expQ, expQ2);
+        std::swap(mapBP, mapBP2);
+        std::swap(mapBQ, mapBQ2);
+    }
 };
 
 namespace {
@@ -917,14 +937,28 @@ cudaError_t mixed_alloc(Ctx& c) {
     if ((e = cudaMalloc(&st.expP, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.expQ, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.R, Np * Np * sizeof(long long))) != cudaSuccess) return e;
-    c.bytes += (int64_t)(plane * 4 + Np * 8 + Np * Np * 8);
+    if ((e = cudaMalloc(&st.digP2, plane * 2)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&st.digQ2, plane * 2)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&st.expP2, Np * sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&st.expQ2, Np * sizeof(int))) != cudaSuccess) return e;
+    c.bytes += (int64_t)(plane * 8 + Np * 16 + Np * Np * 8);
     // on the context's stream (it need not synchronise with the legacy stream)
     if ((e = cudaMemsetAsync(st.digP, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(st.digQ, 0, plane * 2, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(st.digP2, 0, plane * 2, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(st.digQ2, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    int prio_lo = 0, prio_hi = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithPriority(&st.side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithPriority(&st.hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess) return e;
+    st.ev.assign(3 + (size_t)(Np / kNB + 1) / 2, nullptr);
+    for (auto& ev : st.ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
     if (c.d_Z && !make_c_map(&st.mapZ, reinterpret_cast<long long*>(c.d_Z), Np, Np, Np)) return cudaErrorInvalidValue;
     if (!make_c_map(&st.mapR, st.R, Np, Np, Np)) return cudaErrorInvalidValue;
-    if (!make_b_map(&st.mapBP, st.digP, st.s, Np) || !make_b_map(&st.mapBQ, st.digQ, st.s, Np))
+    if (!make_b_map(&st.mapBP, st.digP, st.s, Np) || !make_b_map(&st.mapBQ, st.digQ, st.s, Np) ||
+        !make_b_map(&st.mapBP2, st.digP2, st.s, Np) || !make_b_map(&st.mapBQ2, st.digQ2, st.s, Np))
         return cudaErrorInvalidValue;
     cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
                         set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
@@ -945,9 +979,15 @@ cudaError_t mixed_alloc(Ctx& c) {
 void mixed_free(Ctx& c) {
     if (!c.mixed) return;
     MixedState& st = *c.mixed;
-    void* ptrs[] = {st.digP, st.digQ, st.expP, st.expQ, st.R};
+    if (st.side) cudaStreamSynchronize(st.side);
+    if (st.hi) cudaStreamSynchronize(st.hi);
+    void* ptrs[] = {st.digP, st.digQ, st.expP, st.expQ, st.R, st.digP2, st.digQ2, st.expP2, st.expQ2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto ev : st.ev)
+        if (ev) cudaEventDestroy(ev);
+    if (st.side) cudaStreamDestroy(st.side);
+    if (st.hi) cudaStreamDestroy(st.hi);
     delete c.mixed;
     c.mixed = nullptr;
 }
@@ -959,6 +999,12 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     MixedState& st = *c.mixed;
     const int64_t Np = c.Np, nb = Np / kNB;
     long long* Zq = reinterpret_cast<long long*>(c.d_Z);
+    cudaError_t e;
+    // both phases start after what the context stream holds
+    if ((e = cudaEventRecord(st.ev[0], c.stream)) != cudaSuccess) return e;
+    cudaStream_t main_stream = c.stream;
+    if ((e = cudaStreamWaitEvent(st.hi, st.ev[0], 0)) != cudaSuccess) return e;
+    c.stream = st.hi;
     {
         int64_t nt = (Np + 31) / 32;
         zscale_q_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(32, 32), 0, c.stream>>>(c.N, Np, c.d_Z, c.d_F,
@@ -967,12 +1013,13 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     }
     auto Zat = [&](int64_t row, int64_t col) { return Zq + row * Np + col; };
     auto Rat = [&](int64_t row, int64_t col) { return st.R + row * Np + col; };
-    // ---- Cholesky ----
+    // ---- Cholesky (context stream); event 2 + p / 2 once sub-panels p, p + 1 are final ----
+    auto pair_done = [&](int64_t p) { return cudaEventRecord(st.ev[3 + p / 2], c.stream); };
     for (int64_t p = 0; p < nb; p += 2) {
         const int64_t q = p + 1;
         const int64_t kp = p * kNB, remP = Np - kp - kNB;
         potrf_block(c, p);
-        if (remP <= 0) break;
+        if (remP <= 0) { pair_done(p); break; }
         // L[rows > p, p] = A[rows > p, p] L_pp^-T
         slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
         slice_linv(c, c.d_Linv + p * kNB * kNB, BUF_Q);
@@ -984,20 +1031,30 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
                      kFL, nullptr, nullptr);
         potrf_block(c, q);
         const int64_t kq = q * kNB, remQ = Np - kq - kNB;
-        if (remQ <= 0) break;
+        if (remQ <= 0) { pair_done(p); break; }
         slice_rows(c, 128, (int)remQ, Zat(kq + kNB, kq), BUF_P);
         slice_linv(c, c.d_Linv + q * kNB * kNB, BUF_Q);
         launch_ozaki(c, 128, BUF_P, 0, (int)remQ, BUF_Q, 0, kNB, st.mapZ, (int)kq, (int)(kq + kNB), 0, 0, kFL,
                      nullptr, st.expQ);
         // trailing update with both sub-panels: A22 -= L[:, p:q] L[:, p:q]^T (lower tiles)
         slice_rows(c, 256, (int)remQ, Zat(kq + kNB, kp), BUF_P);
+        // columns p, q of L are final once the trailing update is issued: it
+        // only writes columns beyond q
+        pair_done(p);
         launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_P, 0, (int)remQ, st.mapZ, (int)(kq + kNB), (int)(kq + kNB),
                      1, 1, kFL, nullptr, nullptr);
     }
     if (!c.capturing) cudaEventRecord(c.ev[3], c.stream);
-    // ---- triangular inverse X = L^-1 (Q42), row blocks of 128 ----
-    cudaError_t e = cudaMemsetAsync(st.R, 0, sizeof(long long) * Np * Np, c.stream);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(st.ev[2], c.stream)) != cudaSuccess) { c.stream = main_stream; return e; }
+    // ---- triangular inverse X = L^-1 (Q42), row blocks of 128, on a
+    // low-priority stream with the second digit buffers: row block pair k
+    // waits only for Cholesky pair k, so its GEMMs fill the GPU while the
+    // Cholesky (high priority) runs its serial diagonal blocks ----
+    if ((e = cudaStreamWaitEvent(st.side, st.ev[0], 0)) != cudaSuccess) { c.stream = main_stream; return e; }
+    c.stream = st.side;
+    st.swap_sets();
+    e = cudaMemsetAsync(st.R, 0, sizeof(long long) * Np * Np, c.stream);
+    if (e != cudaSuccess) { st.swap_sets(); c.stream = main_stream; return e; }
     identity_q_kernel<<<(int)((Np + 255) / 256), 256, 0, c.stream>>>(Np, st.R);
     c.launches++;
     auto finalize = [&](int64_t blk) {
@@ -1012,6 +1069,7 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     for (int64_t p = 0; p < nb; p += 2) {
         const int64_t q = p + 1;
         const int64_t kp = p * kNB;
+        cudaStreamWaitEvent(c.stream, st.ev[3 + p / 2], 0);
         finalize(p);
         if (q >= nb) break;
         const int64_t kq = q * kNB;
@@ -1029,6 +1087,12 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_Q, 0, (int)nc, st.mapR, 0, (int)(kq + kNB), 0, 1, kFX,
                      nullptr, st.expQ);
     }
+    st.swap_sets();
+    c.stream = main_stream;
+    // join: the rest of the step (extraction of the blocks) follows both streams
+    if ((e = cudaEventRecord(st.ev[1], st.side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream, st.ev[1], 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream, st.ev[2], 0)) != cudaSuccess) return e;
     if (c.mixed_bad_launch) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
