@@ -565,6 +565,14 @@ __device__ __forceinline__ dsf ds_fma(dsf acc, dsf a, dsf b) {
 
 __device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.h, -a.l}; }
 
+// Row and column of entry t of a lower triangle stored row by row.
+__device__ __forceinline__ void tri_index(int t, int& i, int& l) {
+    i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    l = t - i * (i + 1) / 2;
+}
+
 // Q60 fixed point <-> double-single, with integer conversions only: v =
 // f + r exactly with f = v rounded to a float (an integer value) and r the
 // remainder (|r| <= 2^39); the power-of-two scalings are exact in float.
@@ -693,35 +701,58 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, double* _
         __syncthreads();
         for (int e = tid; e < rows * kPW; e += 512) S[(b0 + kPW + e / kPW) * kLD + b0 + e % kPW] = T[e];
         __syncthreads();
-        // trailing update of the lower triangle below and right of the panel
-        const int t0 = b0 + kPW, w = kNB - t0;
-        for (int e = tid; e < w * w; e += 512) {
-            const int i = t0 + e / w, l = t0 + e % w;
-            if (l > i) continue;
-            dsf v = S[i * kLD + l];
-            for (int k = 0; k < kPW; ++k) v = ds_fma(v, ds_neg(S[i * kLD + b0 + k]), S[l * kLD + b0 + k]);
-            S[i * kLD + l] = v;
+        // trailing update of the lower triangle below and right of the panel;
+        // entries t and t + 512 of the triangle (row by row) share a thread,
+        // two independent chains for the FP32 pipes
+        const int t0 = b0 + kPW, w = kNB - t0, nt = w * (w + 1) / 2;
+        for (int t = tid; t < nt; t += 1024) {
+            int i0, l0, i1 = 0, l1 = 0;
+            tri_index(t, i0, l0);
+            const bool two = t + 512 < nt;
+            if (two) tri_index(t + 512, i1, l1);
+            i0 += t0; l0 += t0; i1 += t0; l1 += t0;
+            dsf v0 = S[i0 * kLD + l0], v1 = two ? S[i1 * kLD + l1] : dsf{0.f, 0.f};
+            for (int k = 0; k < kPW; ++k) {
+                v0 = ds_fma(v0, ds_neg(S[i0 * kLD + b0 + k]), S[l0 * kLD + b0 + k]);
+                if (two) v1 = ds_fma(v1, ds_neg(S[i1 * kLD + b0 + k]), S[l1 * kLD + b0 + k]);
+            }
+            S[i0 * kLD + l0] = v0;
+            if (two) S[i1 * kLD + l1] = v1;
         }
         __syncthreads();
     }
     // off-diagonal blocks of X by block rows; X[r][c] (r > c) lives at S[c][r]
     for (int bi = 1; bi < kNB / kPW; ++bi) {
         const int r0 = kPW * bi;
-        for (int e = tid; e < bi * kPW * kPW; e += 512) {
-            const int bj = e / (kPW * kPW), r = (e / kPW) % kPW, cc = e % kPW;
-            const int col = kPW * bj + cc;
-            dsf v = ds_mul(S[(r0 + r) * kLD + col], invd[col]);
-            for (int k = col + 1; k < r0; ++k) v = ds_fma(v, S[(r0 + r) * kLD + k], S[col * kLD + k]);
-            T[e] = v;
+        // a thread takes rows r and r + 16 of the same column: equal sums
+        for (int bj = 0; bj < bi; ++bj) {
+            const int r = tid / kPW, cc = tid % kPW, col = kPW * bj + cc;   // r < 16
+            const dsf* ra = S + (r0 + r) * kLD;
+            const dsf* rb = S + (r0 + r + 16) * kLD;
+            dsf v0 = ds_mul(ra[col], invd[col]), v1 = ds_mul(rb[col], invd[col]);
+            for (int k = col + 1; k < r0; ++k) {
+                const dsf x = S[col * kLD + k];
+                v0 = ds_fma(v0, ra[k], x);
+                v1 = ds_fma(v1, rb[k], x);
+            }
+            T[bj * kPW * kPW + r * kPW + cc] = v0;
+            T[bj * kPW * kPW + (r + 16) * kPW + cc] = v1;
         }
         __syncthreads();
-        for (int e = tid; e < bi * kPW * kPW; e += 512) {
-            const int bj = e / (kPW * kPW), r = (e / kPW) % kPW, cc = e % kPW;
-            const int col = kPW * bj + cc;
+        for (int bj = 0; bj < bi; ++bj) {
+            const int r = tid / kPW, cc = tid % kPW, col = kPW * bj + cc;   // rows r and r + 16
             const dsf* Tb = T + bj * kPW * kPW;
-            dsf v = ds_mul(invd[r0 + r], Tb[r * kPW + cc]);
-            for (int k = 0; k < r; ++k) v = ds_fma(v, S[(r0 + k) * kLD + r0 + r], Tb[k * kPW + cc]);
-            S[col * kLD + r0 + r] = ds_neg(v);
+            const int r1 = r + 16;
+            dsf v0 = ds_mul(invd[r0 + r], Tb[r * kPW + cc]);
+            dsf v1 = ds_mul(invd[r0 + r1], Tb[r1 * kPW + cc]);
+            for (int k = 0; k < r; ++k) {
+                const dsf t = Tb[k * kPW + cc];
+                v0 = ds_fma(v0, S[(r0 + k) * kLD + r0 + r], t);
+                v1 = ds_fma(v1, S[(r0 + k) * kLD + r0 + r1], t);
+            }
+            for (int k = r; k < r1; ++k) v1 = ds_fma(v1, S[(r0 + k) * kLD + r0 + r1], Tb[k * kPW + cc]);
+            S[col * kLD + r0 + r] = ds_neg(v0);
+            S[col * kLD + r0 + r1] = ds_neg(v1);
         }
         __syncthreads();
     }
