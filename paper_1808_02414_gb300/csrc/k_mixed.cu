@@ -64,7 +64,6 @@ struct MixedState {
     cudaStream_t side = nullptr;     // triangular inverse, lowest priority
     cudaStream_t hi = nullptr;       // Cholesky (the critical path), highest priority
     std::vector<cudaEvent_t> ev;     // [0] fork, [1] inverse done, [2] Cholesky done, [3 + k] pair k final
-    int64_t tiles_done = 0;
 
     void swap_sets() {
         std::swap(digP, digP2);
@@ -911,7 +910,6 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
 #undef CCOV_OZ
     prof_end(c, flops);
     c.launches++;
-    st.tiles_done += ntiles;
 }
 
 void slice_rows(Ctx& c, int K, int rows, const long long* src, Buf b) {
