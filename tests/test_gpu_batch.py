@@ -102,3 +102,23 @@ def test_batch_reports_a_degenerate_member():
             c.close()
     assert metrics.rel_fro(ok[0], covariance.camera_covariance(scenes[0])).max() < 1e-9
     assert metrics.rel_fro(ok[1], covariance.camera_covariance(scenes[2])).max() < 1e-9
+
+
+def test_mixed_batch_graph_replays_match_direct_calls():
+    torch = pytest.importorskip("torch")
+    scenes = _scenes(k=3, seed=25)
+    ctxs = [ccov.from_scene(sc, precision=ccov.CCOV_PREC_MIXED) for sc in scenes]
+    outs = [torch.zeros((sc.n, 9, 9), dtype=torch.float64, device="cuda") for sc in scenes]
+    try:
+        direct = ccov.ccov_batch_covariance(ctxs)
+        with ccov.Batch(ctxs, outs) as b:
+            for _ in range(3):
+                for o in outs:
+                    o.zero_()
+                torch.cuda.synchronize()
+                b.run()
+                for o, d in zip(outs, direct):
+                    assert metrics.rel_fro(o.cpu().numpy(), d).max() < 1e-12
+    finally:
+        for c in ctxs:
+            c.close()

@@ -129,3 +129,28 @@ def test_mixed_six_digits_tighter():
     want = ccov.camera_covariances(sc)
     got = ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED, mixed_slices=6)
     assert metrics.rel_fro(got, want).max() < 1e-8
+
+
+def test_mixed_repeatable_on_a_user_stream_and_after_reload():
+    """The mixed form forks its Cholesky and triangular inverse onto internal
+    streams and joins them back onto the context stream: repeated calls, a
+    user-provided stream and new inputs give the same blocks."""
+    torch = pytest.importorskip("torch")
+    sc = synth.shell_scene(n=60, m=3000, seed=12)
+    want = covariance.camera_covariance(sc)
+    user = torch.cuda.Stream()
+    with ccov.from_scene(sc, precision=ccov.CCOV_PREC_MIXED, stream=user.cuda_stream) as ctx:
+        a = ctx.run()
+        b = ctx.run()
+        moved = sc.cams.copy()
+        moved[:, 3:6] *= 1.5            # a scaled scene: covariances of t change by 1.5^2
+        ctx.ccov_load(moved, sc.pts * 1.5, sc.obs_records())
+        c = ctx.run()
+        ctx.ccov_load(sc.cams, sc.pts, sc.obs_records())
+        d = ctx.run()
+    assert metrics.rel_fro(a, want).max() < 1e-6
+    assert metrics.rel_fro(a, b).max() < 1e-12
+    assert metrics.rel_fro(a, d).max() < 1e-12
+    scaled = covariance.camera_covariance(synth.Scene(cams=moved, pts=sc.pts * 1.5, obs_cam=sc.obs_cam,
+                                                      obs_pt=sc.obs_pt, obs_u=sc.obs_u, sigma=sc.sigma))
+    assert metrics.rel_fro(c, scaled).max() < 1e-6
