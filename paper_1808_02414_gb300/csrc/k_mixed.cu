@@ -18,7 +18,11 @@
 // shifts: no FP64 arithmetic in the O(N^3) part.
 //
 // Blocking: 128-column sub-panels factored and inverted one at a time, with
-// the big trailing updates applied for two sub-panels at once (K = 256).
+// the big trailing updates applied for two sub-panels at once (K = 256).  The
+// diagonal blocks are factored and inverted by one CTA in double-single
+// arithmetic.  The triangular inverse runs on a second stream, each pair of
+// row blocks as soon as the Cholesky has finished the same pair of columns,
+// so that its GEMMs fill the GPU while the Cholesky's serial steps run.
 //
 // Paper counterpart: the dense inversion of Z_p (Sec. 4.2); the paper runs it
 // in double precision with LAPACK on a CPU.
