@@ -117,8 +117,11 @@ def test_mixed_batch_graph_replays_match_direct_calls():
                     o.zero_()
                 torch.cuda.synchronize()
                 b.run()
+                # the FP64 Schur scatter adds in varying order; the digit
+                # rounding of the mixed form turns last-bit differences of Z
+                # into about 1e-10 (the form's own accuracy is 5e-9)
                 for o, d in zip(outs, direct):
-                    assert metrics.rel_fro(o.cpu().numpy(), d).max() < 1e-12
+                    assert metrics.rel_fro(o.cpu().numpy(), d).max() < 1e-9
     finally:
         for c in ctxs:
             c.close()
