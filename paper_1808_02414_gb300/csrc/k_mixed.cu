@@ -60,6 +60,9 @@ struct MixedState {
     long long* R = nullptr;          // Np x Np, Q42
     CUtensorMap mapZ, mapR;          // int64 result maps
     CUtensorMap mapBP, mapBQ;        // B-operand views of digP and digQ
+    __nv_bfloat16* digL = nullptr;   // digits of the inverses of the diagonal blocks (row block b: L_bb^-1)
+    int* expL = nullptr;             // their row exponents
+    CUtensorMap mapBL;
     // the triangular inverse runs on a second stream with a second set of
     // digit buffers, behind the Cholesky one pair of sub-panels at a time
     __nv_bfloat16 *digP2 = nullptr, *digQ2 = nullptr;
@@ -377,17 +380,6 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
-// Digit split.  For a value v with row exponent e (|v| < 2^e, or <= 1 for the
-// fixed exponent 0 of the factor) w = round(v 2^(T - e)), T = 7 + 8 (s - 1),
-// is cut into balanced base-256 digits from the least significant one.
-__device__ __forceinline__ void split_digits(long long w, int s, float* d) {
-    for (int a = s - 1; a > 0; --a) {
-        long long lo = ((w + 128) & 255) - 128;
-        d[a] = (float)lo;
-        w = (w - lo) >> 8;
-    }
-    d[0] = (float)w;
-}
 
 __device__ __forceinline__ long long round_shift(long long v, int sh) {
     if (sh >= 0) return (long long)((unsigned long long)v << sh);
@@ -492,36 +484,6 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
     }
 }
 
-// Rows of a 128 x 128 FP64 matrix (the inverse of a diagonal block), per-row
-// exponent; w = round(v 2^(T - e)) is exact in double (|w| <= 2^T <= 2^47).
-__global__ void slice_ds_kernel(const float2* __restrict__ src, int s, int plane_rows,
-                                __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= kNB) return;
-    double v[4];
-    double mx = 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float2 x = src[r * kNB + lane + 32 * q];
-        v[q] = (double)x.x + (double)x.y;
-        mx = fmax(mx, fabs(v[q]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
-    if (lane == 0) expo[r] = e;
-    const int T = 7 + 8 * (s - 1);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float d[7];
-        split_digits(llrint(ldexp(v[q], T - e)), s, d);
-        for (int a = 0; a < s; ++a)
-            dst[blk_off(a, r, lane + 32 * q, plane_rows, s)] = __float2bfloat16_rn(d[a]);
-    }
-}
-
 // Lower triangle of Z_s = D (Z + F G^T) D written as Q60 int64 in place
 // (padded rows/columns: identity).
 __global__ void zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
@@ -620,7 +582,8 @@ constexpr int kLD = kNB + 1;
 constexpr int kPW = 32;                                   // panel width
 constexpr size_t kDiagSmem = sizeof(dsf) * (kNB * kLD + kNB + 3 * kPW * kPW);
 __global__ void __launch_bounds__(512)
-potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, double* __restrict__ Linv, int* flag) {
+potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bfloat16* __restrict__ digL,
+                    int* __restrict__ expL, int s, int* flag) {
     extern __shared__ __align__(16) dsf S[];      // 128 x 129
     dsf* invd = S + kNB * kLD;                    // 1 / L_jj
     dsf* T = invd + kNB;                          // 3 x 32 x 32: one block row of sum_k L_ik X_kj
@@ -759,12 +722,44 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, double* _
         }
         __syncthreads();
     }
-    float2* Xo = reinterpret_cast<float2*>(Linv);
     for (int e = tid; e < kNB * kNB; e += 512) {
         int i = e >> 7, j = e & 127;
         if (j <= i) Z[(k0 + i) * ld + k0 + j] = ds_to_q60(S[i * kLD + j]);
-        const dsf x = (j < i) ? S[j * kLD + i] : (j == i ? invd[i] : dsf{0.f, 0.f});
-        Xo[e] = make_float2(x.h, x.l);
+    }
+    // X = L^-1 as digit planes (row block k0 / 128 of the inverses' buffer):
+    // per row the exponent e of its largest entry (|x| < 2^e), then
+    // w = round(x 2^(T - e)) from both halves of the double-single value
+    int* rexp = reinterpret_cast<int*>(T);          // 128 row exponents (T is free again)
+    auto xval = [&](int r, int k) -> dsf {          // X[r][k]
+        return k < r ? S[k * kLD + r] : (k == r ? invd[r] : dsf{0.f, 0.f});
+    };
+    for (int r = warp; r < kNB; r += 16) {
+        float mx = 0.f;
+        for (int k = lane; k <= r; k += 32) mx = fmaxf(mx, fabsf(xval(r, k).h));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int ex = 0;
+        if (mx > 0.f) frexpf(mx * 1.00001f, &ex);   // margin for the low half: |x| < 2^ex
+        if (lane == 0) {
+            rexp[r] = ex;
+            expL[k0 + r] = ex;
+        }
+    }
+    __syncthreads();
+    const int Tb = 7 + 8 * (s - 1);
+    const int64_t pstride = blk_off(1, 0, 0, (int)ld, s) - blk_off(0, 0, 0, (int)ld, s);
+    for (int item = tid; item < kNB * (kNB / 8); item += 512) {
+        const int r = item >> 4, g8 = item & 15;
+        const int sh = Tb - rexp[r];
+        const float scale = __int_as_float((127 + sh) << 23);   // 2^sh (ex >= 1: the diagonal 1 / L_rr >= 1)
+        long long w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const dsf x = xval(r, 8 * g8 + j);
+            const float hs = __fmul_rn(x.h, scale), ls = __fmul_rn(x.l, scale);
+            const long long wh = __float2ll_rn(hs);
+            w[j] = wh + __float2ll_rn(__fadd_rn(__fsub_rn(hs, __ll2float_rn(wh)), ls));
+        }
+        split_store8(w, s, digL + blk_off(0, (int)k0 + r, 8 * g8, (int)ld, s), pstride);
     }
 }
 
@@ -859,7 +854,11 @@ cudaError_t set_attr() {
                                 (int)gemm_smem(S, pick_stages(S)));
 }
 
-enum Buf { BUF_P = 0, BUF_Q = 1 };
+enum Buf { BUF_P = 0, BUF_Q = 1, BUF_L = 2 };
+
+__nv_bfloat16* buf_ptr(const MixedState& st, Buf b) {
+    return b == BUF_P ? st.digP : (b == BUF_Q ? st.digQ : st.digL);
+}
 
 // C op= A B^T with A = rows [a_row0, a_row0 + M) of digit buffer `ba`, B =
 // rows [b_row0, b_row0 + N) of buffer `bb`, both with K digits per row.
@@ -870,8 +869,8 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     g.M = M; g.N = N; g.plane_rows = (int)c.Np; g.a_row0 = a_row0; g.b_row0 = b_row0;
     g.c_x0 = c_x0; g.c_y0 = c_y0; g.lower = lower; g.sub = sub; g.shift0 = Fc - 14;
     g.expA = expA; g.expB = expB; g.stages = pick_stages(st.s); g.flag = c.d_flag;
-    g.digA = ba == BUF_P ? st.digP : st.digQ;
-    g.digB = bb == BUF_P ? st.digP : st.digQ;
+    g.digA = buf_ptr(st, ba);
+    g.digB = buf_ptr(st, bb);
     const int64_t ntiles = tile_count(M / kBM, N / kBN, lower);  // even: pairs of tiles
     if ((ntiles & 1) || (N % (2 * kBN))) {
         c.mixed_bad_launch = true;  // cannot happen with N a multiple of 128
@@ -896,7 +895,7 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const CUtensorMap& mapB = bb == BUF_P ? st.mapBP : st.mapBQ;
+    const CUtensorMap& mapB = bb == BUF_P ? st.mapBP : (bb == BUF_Q ? st.mapBQ : st.mapBL);
 #define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_>, mapC, mapB, g)
     if (K == 256) {
         switch (st.s) {
@@ -941,17 +940,10 @@ void slice_cols(Ctx& c, int K, int ncols, const long long* src, Buf b) {
     c.launches++;
 }
 
-void slice_linv(Ctx& c, const double* Linv, Buf b) {
-    MixedState& st = *c.mixed;
-    slice_ds_kernel<<<kNB / 8, 256, 0, c.stream>>>(reinterpret_cast<const float2*>(Linv), st.s, (int)c.Np, b == BUF_P ? st.digP : st.digQ,
-                                                     b == BUF_P ? st.expP : st.expQ);
-    c.launches++;
-}
-
 void potrf_block(Ctx& c, int64_t blk) {
+    MixedState& st = *c.mixed;
     long long* Zq = reinterpret_cast<long long*>(c.d_Z);
-    potrf_diag_q_kernel<<<1, 512, kDiagSmem, c.stream>>>(
-        Zq, c.Np, blk * kNB, c.d_Linv + blk * kNB * kNB, c.d_flag);
+    potrf_diag_q_kernel<<<1, 512, kDiagSmem, c.stream>>>(Zq, c.Np, blk * kNB, st.digL, st.expL, st.s, c.d_flag);
     c.launches++;
 }
 
@@ -970,16 +962,19 @@ cudaError_t mixed_alloc(Ctx& c) {
     if ((e = cudaMalloc(&st.expP, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.expQ, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.R, Np * Np * sizeof(long long))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&st.digL, plane * 2)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&st.expL, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.digP2, plane * 2)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.digQ2, plane * 2)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.expP2, Np * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&st.expQ2, Np * sizeof(int))) != cudaSuccess) return e;
-    c.bytes += (int64_t)(plane * 8 + Np * 16 + Np * Np * 8);
+    c.bytes += (int64_t)(plane * 10 + Np * 20 + Np * Np * 8);
     // on the context's stream (it need not synchronise with the legacy stream)
     if ((e = cudaMemsetAsync(st.digP, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(st.digQ, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(st.digP2, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(st.digQ2, 0, plane * 2, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(st.digL, 0, plane * 2, c.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
     int prio_lo = 0, prio_hi = 0;
     if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess) return e;
@@ -991,7 +986,8 @@ cudaError_t mixed_alloc(Ctx& c) {
     if (c.d_Z && !make_c_map(&st.mapZ, reinterpret_cast<long long*>(c.d_Z), Np, Np, Np)) return cudaErrorInvalidValue;
     if (!make_c_map(&st.mapR, st.R, Np, Np, Np)) return cudaErrorInvalidValue;
     if (!make_b_map(&st.mapBP, st.digP, st.s, Np) || !make_b_map(&st.mapBQ, st.digQ, st.s, Np) ||
-        !make_b_map(&st.mapBP2, st.digP2, st.s, Np) || !make_b_map(&st.mapBQ2, st.digQ2, st.s, Np))
+        !make_b_map(&st.mapBP2, st.digP2, st.s, Np) || !make_b_map(&st.mapBQ2, st.digQ2, st.s, Np) ||
+        !make_b_map(&st.mapBL, st.digL, st.s, Np))
         return cudaErrorInvalidValue;
     cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
                         set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
@@ -1014,7 +1010,7 @@ void mixed_free(Ctx& c) {
     MixedState& st = *c.mixed;
     if (st.side) cudaStreamSynchronize(st.side);
     if (st.hi) cudaStreamSynchronize(st.hi);
-    void* ptrs[] = {st.digP, st.digQ, st.expP, st.expQ, st.R, st.digP2, st.digQ2, st.expP2, st.expQ2};
+    void* ptrs[] = {st.digP, st.digQ, st.expP, st.expQ, st.R, st.digP2, st.digQ2, st.expP2, st.expQ2, st.digL, st.expL};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto ev : st.ev)
@@ -1055,9 +1051,8 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         if (remP <= 0) { pair_done(p); break; }
         // L[rows > p, p] = A[rows > p, p] L_pp^-T
         slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
-        slice_linv(c, c.d_Linv + p * kNB * kNB, BUF_Q);
-        launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_Q, 0, kNB, st.mapZ, (int)kp, (int)(kp + kNB), 0, 0, kFL,
-                     nullptr, st.expQ);
+        launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_L, (int)kp, kNB, st.mapZ, (int)kp, (int)(kp + kNB), 0, 0, kFL,
+                     nullptr, st.expL);
         // column strip q: A[rows >= q, q] -= L[rows >= q, p] L[q, p]^T
         slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
         launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_P, 0, kNB, st.mapZ, (int)(q * kNB), (int)(q * kNB), 0, 1,
@@ -1066,9 +1061,8 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         const int64_t kq = q * kNB, remQ = Np - kq - kNB;
         if (remQ <= 0) { pair_done(p); break; }
         slice_rows(c, 128, (int)remQ, Zat(kq + kNB, kq), BUF_P);
-        slice_linv(c, c.d_Linv + q * kNB * kNB, BUF_Q);
-        launch_ozaki(c, 128, BUF_P, 0, (int)remQ, BUF_Q, 0, kNB, st.mapZ, (int)kq, (int)(kq + kNB), 0, 0, kFL,
-                     nullptr, st.expQ);
+        launch_ozaki(c, 128, BUF_P, 0, (int)remQ, BUF_L, (int)kq, kNB, st.mapZ, (int)kq, (int)(kq + kNB), 0, 0, kFL,
+                     nullptr, st.expL);
         // trailing update with both sub-panels: A22 -= L[:, p:q] L[:, p:q]^T (lower tiles)
         slice_rows(c, 256, (int)remQ, Zat(kq + kNB, kp), BUF_P);
         // columns p, q of L are final once the trailing update is issued: it
@@ -1094,8 +1088,7 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         const int64_t k0 = blk * kNB, nc = k0 + kNB;
         // X[blk, :nc] = L_blk^-1 R[blk, :nc]
         slice_cols(c, 128, (int)nc, Rat(k0, 0), BUF_Q);
-        slice_linv(c, c.d_Linv + blk * kNB * kNB, BUF_P);
-        launch_ozaki(c, 128, BUF_P, 0, kNB, BUF_Q, 0, (int)nc, st.mapR, 0, (int)k0, 0, 0, kFX, st.expP, st.expQ);
+        launch_ozaki(c, 128, BUF_L, (int)k0, kNB, BUF_Q, 0, (int)nc, st.mapR, 0, (int)k0, 0, 0, kFX, st.expL, st.expQ);
         gram_q_kernel<<<(int)((nc + kGW - 1) / kGW), 128, 0, c.stream>>>(c.n, Np, k0, nc, st.R, c.d_Sig);
         c.launches++;
     };
