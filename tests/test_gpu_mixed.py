@@ -111,10 +111,16 @@ def test_ozaki_gemm_overwrite_with_exponents_k256():
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("case", ["ring20", "shell100", "shell300"])
+@pytest.mark.parametrize("case", ["ring20", "shell10", "shell30", "shell100", "shell300"])
 def test_mixed_covariance_vs_oracle(case):
+    # shell10: one 128-column block; shell30: three (an odd count: the last
+    # sub-panel has no partner); the others span 2, 8 and 22 blocks
     if case == "ring20":
         sc = synth.workload("ring20")
+    elif case == "shell10":
+        sc = synth.shell_scene(n=10, m=1000, seed=3)
+    elif case == "shell30":
+        sc = synth.shell_scene(n=30, m=3000, seed=4)
     elif case == "shell100":
         sc = synth.shell_scene(n=100, m=10000, seed=5)
     else:
