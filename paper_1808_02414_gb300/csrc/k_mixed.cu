@@ -485,22 +485,36 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
 }
 
 // Lower triangle of Z_s = D (Z + F G^T) D written as Q60 int64 in place
-// (padded rows/columns: identity).
-__global__ void zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
-                                const double* __restrict__ G, const double* __restrict__ D) {
-    int64_t bi = blockIdx.y, bj = blockIdx.x;
+// (padded rows/columns: identity).  A block covers 32 x 32 entries, a thread
+// four consecutive columns of one row (its row's F and 2^60 D_i loaded once);
+// the scaling by 2^60 is folded into D_i, so each entry costs 7 + 2 FP64
+// operations and one conversion.
+__global__ void __launch_bounds__(256)
+zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
+                const double* __restrict__ G, const double* __restrict__ D) {
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;
     if (bj > bi) return;
-    int64_t i = bi * 32 + threadIdx.y, j = bj * 32 + threadIdx.x;
-    if (i >= Np || j > i) return;
-    double* z = Z + i * Np + j;
-    long long* q = reinterpret_cast<long long*>(z);
-    if (i >= N || j >= N) { *q = (i == j) ? (1ll << kFL) : 0; return; }
-    double v = *z;
-    const double* fi = F + 7 * i;
-    const double* gj = G + 7 * j;
+    const int64_t i = bi * 32 + threadIdx.y;
+    const int64_t j0 = bj * 32 + 4 * threadIdx.x;   // 8 x 32 threads
+    if (i >= Np || j0 > i) return;
+    double fi[7];
+    const bool row_in = i < N;
+    const double di = row_in ? D[i] * 0x1p60 : 0.0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) v += fi[k] * gj[k];
-    *q = llrint(ldexp(D[i] * v * D[j], kFL));
+    for (int k = 0; k < 7; ++k) fi[k] = row_in ? F[7 * i + k] : 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int64_t j = j0 + c;
+        if (j > i) break;
+        double* z = Z + i * Np + j;
+        long long* q = reinterpret_cast<long long*>(z);
+        if (!row_in || j >= N) { *q = (i == j) ? (1ll << kFL) : 0; continue; }
+        double v = *z;
+        const double* gj = G + 7 * j;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v = fma(fi[k], gj[k], v);
+        *q = __double2ll_rn(di * v * D[j]);
+    }
 }
 
 // Double-single arithmetic: a value is an unevaluated sum hi + lo of two
@@ -1036,8 +1050,8 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     c.stream = st.hi;
     {
         int64_t nt = (Np + 31) / 32;
-        zscale_q_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(32, 32), 0, c.stream>>>(c.N, Np, c.d_Z, c.d_F,
-                                                                                       c.d_G, c.d_D);
+        zscale_q_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(8, 32), 0, c.stream>>>(c.N, Np, c.d_Z, c.d_F,
+                                                                                      c.d_G, c.d_D);
         c.launches++;
     }
     auto Zat = [&](int64_t row, int64_t col) { return Zq + row * Np + col; };
