@@ -148,6 +148,50 @@ __device__ __forceinline__ void tile_coords(int64_t t, int tiles_n, int lower, i
     }
 }
 
+// Combining the accumulators of one element into T = sum_g P_g 2^(8 (S-1-g)).
+// Every accumulator holds an integer P with |P| <= 2^24.  combine_converted
+// converts each with a float-to-int instruction.  When -2^22 <= P < 2^22,
+// P + 1.5 * 2^23 is exact and lies in [2^23, 2^24), so its bit pattern is
+// 0x4B400000 + P (sign 0, exponent field 150, checked on the pattern itself);
+// combine_biased sums those patterns with the weights of the orders and
+// removes the constants' share at the end, modulo 2^64, which is exact because
+// the true T fits in 63 bits.
+constexpr float kMagic = 12582912.f;   // 1.5 * 2^23, bit pattern 0x4B400000
+constexpr unsigned kMagicTop = 0x96;   // sign and exponent field of [2^23, 2^24)
+
+template <int S, int K>
+__device__ __forceinline__ long long combine_converted(const float (&v)[Slots<S, K>::total][8], int j) {
+    using SL = Slots<S, K>;
+    long long T = 0;
+#pragma unroll
+    for (int gi = 0; gi < S; ++gi) {
+        int p = __float2int_rn(v[gi][j]);
+        if (gi >= SL::cap) p += __float2int_rn(v[S + gi - SL::cap][j]);
+        T = (long long)((unsigned long long)T << 8) + p;
+    }
+    return T;
+}
+
+template <int S, int K>
+__host__ __device__ constexpr unsigned long long magic_share() {
+    unsigned long long t = 0;
+    for (int gi = 0; gi < S; ++gi) t = (t << 8) + 0x4B400000ull * (gi >= Slots<S, K>::cap ? 2u : 1u);
+    return t;
+}
+
+template <int S, int K>
+__device__ __forceinline__ long long combine_biased(const unsigned (&u)[Slots<S, K>::total][8], int j) {
+    using SL = Slots<S, K>;
+    unsigned long long T = 0;
+#pragma unroll
+    for (int gi = 0; gi < S; ++gi) {
+        unsigned c = u[gi][j];
+        if (gi >= SL::cap) c += u[S + gi - SL::cap][j];   // two patterns < 2^31 each
+        T += (unsigned long long)c << (8 * (S - 1 - gi));
+    }
+    return (long long)(T - magic_share<S, K>());
+}
+
 struct GemmArgs {
     const __nv_bfloat16* digA;  // digit planes of A and B (layout of blk_off)
     const __nv_bfloat16* digB;
@@ -175,8 +219,9 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
 // they need the same A tile, and each CTA loads half of its digit planes and
 // multicasts them to both.  Warp 0 lane 0: producer of the digit tiles.  Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps
 // 2..17: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter
-// of the 64 columns, and the result tile goes through shared memory with TMA
-// (load of C overlapped with the MMAs of the same tile, store asynchronous).
+// of the 64 columns.  The result tile leaves through shared memory with TMA:
+// C -= A B^T as a reduce-add of -A B^T into C (the addition happens in L2,
+// so C is never read into the SM), C = A B^T as a plain store.
 template <int S, int K>
 __global__ void __launch_bounds__(kThreads, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB, GemmArgs g) {
@@ -192,8 +237,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
     uint64_t* accf = bars + 2 * g.stages;
     uint64_t* acce = accf + 1;
     uint64_t* drain = acce + 1;
-    uint64_t* cfull = drain + 1;
-    uint32_t* tmem_slot = (uint32_t*)(cfull + 1);
+    uint32_t* tmem_slot = (uint32_t*)(drain + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = g.N / kBN;
@@ -211,9 +255,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             mbar_init(empty + i, 2);  // released by the MMAs of both CTAs
         }
         mbar_init(accf, 1);
-        mbar_init(acce, 32 * kEpiWarps);
+        mbar_init(acce, kEpiWarps);
         mbar_init(drain, 1);
-        mbar_init(cfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -299,25 +342,20 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
         const int part = (warp - 2) >> 2;   // which kEpiCols columns
         const int r = 32 * quarter + lane;  // row in the tile = TMEM lane
         const bool leader = (warp == 2 && lane == 0);
-        uint32_t acc_phase = 0, c_phase = 0;
+        uint32_t acc_phase = 0;
         for (int64_t pr = pair0; pr < npairs; pr += pair_step) {
             const int64_t t = 2 * pr + rank;
             int ti, tj;
             tile_coords(t, tiles_n, g.lower, ti, tj);
             const int cx = g.c_x0 + tj * kBN, cy = g.c_y0 + ti * kBM;
-            if (leader) {
-                bulk_wait_read0();  // the previous tile's store has left shared memory
-                if (g.sub) {
-                    mbar_expect_tx(cfull, kCTile);
-                    for (int b = 0; b < 4; ++b) tma_load_2d(ctile + b * kCBox, &mapC, cfull, cx + 16 * b, cy);
-                }
-            }
+            if (leader) bulk_wait_read0();  // the previous tile's copy-out has left shared memory
             epi_bar();
-            if (!mbar_wait(accf, acc_phase, g.flag, 5)) break;
+            // warp-uniform: the vote, the re-read and the arrival below are per warp
+            if (!__all_sync(0xffffffffu, mbar_wait(accf, acc_phase, g.flag, 5))) break;
             tc_fence_after();
             // phase 1: drain the accumulators into exact int64 sums (registers),
-            // then release TMEM so that the next tile's MMAs start at once
-            const int eA = g.expA ? g.expA[g.a_row0 + ti * kBM + r] : 0;
+            // then release TMEM so that the next tile's MMAs start at once;
+            // everything else waits until after the release
             const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
             long long res[kEpiCols];
 #pragma unroll
@@ -327,43 +365,58 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
 #pragma unroll
                 for (int sl = 0; sl < SL::total; ++sl) tmem_ld8(trow + (uint32_t)(sl * kBN + col0), v[sl]);
                 tmem_wait_ld();
+                // T = sum_g P_g 2^(8 (S-1-g)) exactly (|T| < 2^63); the usual
+                // case takes the biased bit patterns, the rare one (some
+                // |P| > 2^22 in the warp) reads the chunk again and converts
+                unsigned u[SL::total][8];
+                unsigned all_and = 0xffffffffu, all_or = 0u;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int eB = g.expB ? g.expB[g.b_row0 + tj * kBN + col0 + j] : 0;
-                    // T = sum_g P_g 2^(8 (S-1-g)) exactly (|T| < 2^63), then one
-                    // rounding shift to the fixed point of C
-                    long long T = 0;
+                for (int sl = 0; sl < SL::total; ++sl)
 #pragma unroll
-                    for (int gi = 0; gi < S; ++gi) {
-                        int p = __float2int_rn(v[gi][j]);
-                        if (gi >= SL::cap) p += __float2int_rn(v[S + gi - SL::cap][j]);
-                        T = (long long)((unsigned long long)T << 8) + p;
+                    for (int j = 0; j < 8; ++j) {
+                        u[sl][j] = __float_as_uint(__fadd_rn(v[sl][j], kMagic));
+                        all_and &= u[sl][j];
+                        all_or |= u[sl][j];
                     }
-                    res[8 * cc + j] = shift_round(T, eA + eB + g.shift0 - 8 * (S - 1));
+                if (__all_sync(0xffffffffu, (all_and >> 23) == kMagicTop && (all_or >> 23) == kMagicTop)) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) res[8 * cc + j] = combine_biased<S, K>(u, j);
+                } else {
+#pragma unroll
+                    for (int sl = 0; sl < SL::total; ++sl) tmem_ld8(trow + (uint32_t)(sl * kBN + col0), v[sl]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) res[8 * cc + j] = combine_converted<S, K>(v, j);
                 }
             }
             tc_fence_before();
-            mbar_arrive(acce);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce);   // one arrival per warp, after all its TMEM reads
             acc_phase ^= 1;
-            // phase 2: combine with C in the staged tile and store it
-            if (g.sub) {
-                if (!mbar_wait(cfull, c_phase, g.flag, 6)) break;
-                c_phase ^= 1;
-            }
+            // one rounding shift of each sum to the fixed point of C
+            {
+                const int sh = (g.expA ? g.expA[g.a_row0 + ti * kBM + r] : 0) + g.shift0 - 8 * (S - 1);
+                const int* eBp = g.expB ? g.expB + g.b_row0 + tj * kBN + kEpiCols * part : nullptr;
 #pragma unroll
-            for (int q = 0; q < kEpiCols; ++q) {
+                for (int q = 0; q < kEpiCols; ++q) res[q] = shift_round(res[q], sh + (eBp ? eBp[q] : 0));
+            }
+            // phase 2: stage -A B^T (or A B^T) for the copy-out; two columns (one 16-byte chunk) per access; with the 128-byte
+            // swizzle (chunk index XOR row % 8) the 32 rows of a warp spread
+            // over all banks
+#pragma unroll
+            for (int q = 0; q < kEpiCols; q += 2) {
                 const int col = kEpiCols * part + q;
-                // 128-byte swizzle: 16-byte chunk index XOR (row % 8)
                 const int box = col >> 4, jj = col & 15;
-                long long* cp = (long long*)(ctile + box * kCBox + r * 128 +
-                                             ((((jj >> 1) ^ (r & 7)) << 4) | ((jj & 1) << 3)));
-                if (g.sub) *cp -= res[q];
-                else *cp = res[q];
+                longlong2* cp = (longlong2*)(ctile + box * kCBox + r * 128 + (((jj >> 1) ^ (r & 7)) << 4));
+                *cp = g.sub ? make_longlong2(-res[q], -res[q + 1]) : make_longlong2(res[q], res[q + 1]);
             }
             fence_proxy_async();
             epi_bar();
             if (leader) {
-                for (int b = 0; b < 4; ++b) tma_store_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
+                for (int b = 0; b < 4; ++b) {
+                    if (g.sub) tma_reduce_add_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
+                    else tma_store_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
+                }
                 bulk_commit();
             }
         }
@@ -831,7 +884,9 @@ bool make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, in
     cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
     cuuint32_t box[2] = {16, (cuuint32_t)kBM};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    // unsigned: the reduce-add of the epilogue adds 64-bit words modulo 2^64,
+    // which is two's-complement addition of the signed fixed-point values
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
