@@ -440,47 +440,86 @@ __device__ __forceinline__ long long round_shift(long long v, int sh) {
     return (v + (1ll << (-sh - 1))) >> (-sh);
 }
 
+// Two small integers (|d| <= 256) as a bf16 pair, element 0 in the low half:
+// 1.5 * 2^23 + d is exact with bit pattern 0x4B400000 + d, subtracting
+// 1.5 * 2^23 leaves d as a float, and the upper half of a float that holds
+// such an integer is its exact bf16 encoding.
+__device__ __forceinline__ unsigned bf16x2_small(int d0, int d1) {
+    const float a = __int_as_float(0x4B400000 + d0) - 12582912.f;
+    const float b = __int_as_float(0x4B400000 + d1) - 12582912.f;
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
 // Digits of eight values consecutive along K (w already in units of the
-// last digit), plane by plane from the least significant one; each plane's
-// eight digits (a core-matrix row) go out as one 16-byte store.
+// last digit, |w| <= 2^(7 + 8 (s-1)) + 1), plane by plane from the least
+// significant one: digit = ((w + 128) mod 256) - 128, w <- (w + 128) >> 8.
+// The lowest s - 3 digits are taken in 64-bit arithmetic, after which |w| <
+// 2^31 and the rest in 32-bit.  Each plane's eight digits (a core-matrix
+// row) go out as one 16-byte store.
 __device__ __forceinline__ void split_store8(long long* w, int s, __nv_bfloat16* dst0, int64_t plane_stride) {
+    int d[8], wi[8];
     for (int a = s - 1; a >= 0; --a) {
-        float dv[8];
+        if (a >= 3) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (a > 0) {
-                const long long lo = ((w[j] + 128) & 255) - 128;
-                dv[j] = (float)lo;
-                w[j] = (w[j] - lo) >> 8;
-            } else {
-                dv[j] = (float)w[j];
+            for (int j = 0; j < 8; ++j) {
+                const long long t = w[j] + 128;
+                d[j] = (int)(t & 255) - 128;
+                w[j] = t >> 8;
+                wi[j] = (int)w[j];
             }
-        }
-        __nv_bfloat162 h[4];
+        } else if (a > 0) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(dv[2 * j], dv[2 * j + 1]);
-        *reinterpret_cast<uint4*>(dst0 + a * plane_stride) = *reinterpret_cast<const uint4*>(h);
+            for (int j = 0; j < 8; ++j) {
+                const int t = wi[j] + 128;
+                d[j] = (t & 255) - 128;
+                wi[j] = t >> 8;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) d[j] = wi[j];
+        }
+        uint4 out;
+        out.x = bf16x2_small(d[0], d[1]);
+        out.y = bf16x2_small(d[2], d[3]);
+        out.z = bf16x2_small(d[4], d[5]);
+        out.w = bf16x2_small(d[6], d[7]);
+        *reinterpret_cast<uint4*>(dst0 + a * plane_stride) = out;
     }
 }
 
+// Lane of a warp that covers 16 digit rows x one 16-wide K slice: rows
+// (lane & 7) + 8 (lane >> 4), K half (lane >> 3) & 1.  Its 16-byte stores of
+// one plane then fill 512 contiguous bytes of the digit layout (two 8-row
+// groups of one K slice).
+__device__ __forceinline__ int tile16_row(int lane) { return (lane & 7) + 8 * (lane >> 4); }
+__device__ __forceinline__ int tile16_khalf(int lane) { return (lane >> 3) & 1; }
+
 // Rows of an int64 Q(F) matrix, K = 128 or 256 values per row, exponent 0
 // (entries of the scaled factor are bounded by 1).  A thread takes eight
-// consecutive values of a row and writes each digit plane with one store.
+// consecutive values of a row (64 bytes, read as four 16-byte loads) and
+// writes each digit plane with one 16-byte store; a warp covers 16 rows of
+// one K slice.  rows is a multiple of 16.
 template <int K>
 __global__ void __launch_bounds__(256)
 slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
                   __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
-    constexpr int G = K / 8;  // groups of eight per row
-    const int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int r = (int)(item / G), g = (int)(item % G);
+    constexpr int KS = K / 16;
+    const int lane = threadIdx.x & 31;
+    const int64_t wt = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int r = (int)(wt / KS) * 16 + tile16_row(lane);
+    const int k0 = 16 * (int)(wt % KS) + 8 * tile16_khalf(lane);
     if (r >= rows) return;
-    if (g == 0) expo[r] = 0;
+    if (k0 == 0) expo[r] = 0;
     const int T = 7 + 8 * (s - 1);
-    const long long* p = src + (int64_t)r * ld + 8 * g;
+    const longlong2* p = reinterpret_cast<const longlong2*>(src + (int64_t)r * ld + k0);
     long long w[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) w[j] = round_shift(p[j], T - F);
-    split_store8(w, s, dst + blk_off(0, r, 8 * g, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
+    for (int j = 0; j < 4; ++j) {
+        const longlong2 v = p[j];
+        w[2 * j] = round_shift(v.x, T - F);
+        w[2 * j + 1] = round_shift(v.y, T - F);
+    }
+    split_store8(w, s, dst + blk_off(0, r, k0, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
 }
 
 // Column split: a K-row block (K = 128 or 256) of an int64 Q(F) matrix,
@@ -488,7 +527,8 @@ slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F
 // K = source rows), per-column exponent from the column maximum.  The block
 // stages 32 columns in shared memory; a warp finds each column's exponent,
 // then a thread splits eight consecutive source rows of a column and writes
-// each digit plane with one 16-byte store.
+// each digit plane with one 16-byte store (a warp: 16 columns of one K
+// slice, so that its stores are contiguous).
 template <int K>
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
@@ -524,16 +564,17 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
     }
     __syncthreads();
     const int T = 7 + 8 * (s - 1);
-    constexpr int G = K / 8;
-    for (int item = tid; item < 32 * G; item += 256) {
-        const int c = item / G, g = item % G;
+    // warp tiles: 2 halves of the 32 columns x K / 16 slices
+    for (int wt = w; wt < 2 * (K / 16); wt += 8) {
+        const int c = 16 * (wt & 1) + tile16_row(lane);
+        const int k0 = 16 * (wt >> 1) + 8 * tile16_khalf(lane);
         const int col = c0 + c;
         if (col >= ncols) continue;
         const int e = cexp[c];
-        long long w[8];
+        long long wv[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) w[j] = round_shift(tile[(8 * g + j) * 33 + c], T - e - F);
-        split_store8(w, s, dst + blk_off(0, col, 8 * g, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
+        for (int j = 0; j < 8; ++j) wv[j] = round_shift(tile[(k0 + j) * 33 + c], T - e - F);
+        split_store8(wv, s, dst + blk_off(0, col, k0, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
     }
 }
 
@@ -988,7 +1029,9 @@ void slice_rows(Ctx& c, int K, int rows, const long long* src, Buf b) {
     MixedState& st = *c.mixed;
     __nv_bfloat16* dst = b == BUF_P ? st.digP : st.digQ;
     int* ex = b == BUF_P ? st.expP : st.expQ;
-    const int grid = (int)(((int64_t)rows * (K / 8) + 255) / 256);
+    // one warp per 16 rows x 16 values
+    const int grid = (int)(((int64_t)rows / 16 * (K / 16) * 32 + 255) / 256);
+    if (rows % 16) { c.mixed_bad_launch = true; return; }
     if (K == 256)
         slice_rows_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex);
     else
