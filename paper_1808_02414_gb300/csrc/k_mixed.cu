@@ -764,13 +764,26 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
             }
         }
         if (b0 + kPW == kNB) break;
-        // rows below: L[i][b0 + c] = sum_{k <= c} A[i][b0 + k] X_pp[c][k], one thread per entry
+        // rows below: L[i][b0 + c] = sum_{k <= c} A[i][b0 + k] X_pp[c][k].
+        // Warp w takes columns w and 31 - w (sums of 32 terms together), its
+        // lanes 32 rows at a time, so that no lane of a warp idles
         const int rows = kNB - b0 - kPW;
-        for (int e = tid; e < rows * kPW; e += 512) {
-            const int i = b0 + kPW + e / kPW, c = e % kPW;
-            dsf v = ds_mul(S[i * kLD + b0 + c], invd[b0 + c]);
-            for (int k = 0; k < c; ++k) v = ds_fma(v, S[i * kLD + b0 + k], S[(b0 + k) * kLD + b0 + c]);
-            T[e] = v;
+        {
+            const int c0 = warp, c1 = kPW - 1 - warp;
+            for (int ri = lane; ri < rows; ri += 32) {
+                const dsf* ai = S + (b0 + kPW + ri) * kLD + b0;
+                dsf v0 = ds_mul(ai[c0], invd[b0 + c0]);
+                dsf v1 = ds_mul(ai[c1], invd[b0 + c1]);
+                int k = 0;
+                for (; k < c0; ++k) {
+                    const dsf aik = ai[k];
+                    v0 = ds_fma(v0, aik, S[(b0 + k) * kLD + b0 + c0]);
+                    v1 = ds_fma(v1, aik, S[(b0 + k) * kLD + b0 + c1]);
+                }
+                for (; k < c1; ++k) v1 = ds_fma(v1, ai[k], S[(b0 + k) * kLD + b0 + c1]);
+                T[ri * kPW + c0] = v0;
+                T[ri * kPW + c1] = v1;
+            }
         }
         __syncthreads();
         for (int e = tid; e < rows * kPW; e += 512) S[(b0 + kPW + e / kPW) * kLD + b0 + e % kPW] = T[e];
@@ -798,19 +811,22 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
     // off-diagonal blocks of X by block rows; X[r][c] (r > c) lives at S[c][r]
     for (int bi = 1; bi < kNB / kPW; ++bi) {
         const int r0 = kPW * bi;
-        // a thread takes rows r and r + 16 of the same column: equal sums
+        // warp w takes columns w and 31 - w (sums of equal total length),
+        // its lanes the 32 rows
         for (int bj = 0; bj < bi; ++bj) {
-            const int r = tid / kPW, cc = tid % kPW, col = kPW * bj + cc;   // r < 16
+            const int r = lane, cc = warp;
+            const int col0 = kPW * bj + cc, col1 = kPW * bj + kPW - 1 - cc;
             const dsf* ra = S + (r0 + r) * kLD;
-            const dsf* rb = S + (r0 + r + 16) * kLD;
-            dsf v0 = ds_mul(ra[col], invd[col]), v1 = ds_mul(rb[col], invd[col]);
-            for (int k = col + 1; k < r0; ++k) {
-                const dsf x = S[col * kLD + k];
-                v0 = ds_fma(v0, ra[k], x);
-                v1 = ds_fma(v1, rb[k], x);
+            dsf v0 = ds_mul(ra[col0], invd[col0]), v1 = ds_mul(ra[col1], invd[col1]);
+            int k = col0 + 1;
+            for (; k <= col1; ++k) v0 = ds_fma(v0, ra[k], S[col0 * kLD + k]);
+            for (; k < r0; ++k) {
+                const dsf a = ra[k];
+                v0 = ds_fma(v0, a, S[col0 * kLD + k]);
+                v1 = ds_fma(v1, a, S[col1 * kLD + k]);
             }
             T[bj * kPW * kPW + r * kPW + cc] = v0;
-            T[bj * kPW * kPW + (r + 16) * kPW + cc] = v1;
+            T[bj * kPW * kPW + r * kPW + kPW - 1 - cc] = v1;
         }
         __syncthreads();
         for (int bj = 0; bj < bi; ++bj) {
@@ -855,8 +871,10 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
     __syncthreads();
     const int Tb = 7 + 8 * (s - 1);
     const int64_t pstride = blk_off(1, 0, 0, (int)ld, s) - blk_off(0, 0, 0, (int)ld, s);
+    // lanes take consecutive rows of one group of eight columns: X[r][k]
+    // lives at S[k][r], so a warp's reads of one k are contiguous
     for (int item = tid; item < kNB * (kNB / 8); item += 512) {
-        const int r = item >> 4, g8 = item & 15;
+        const int r = item & (kNB - 1), g8 = item >> 7;
         const int sh = Tb - rexp[r];
         const float scale = __int_as_float((127 + sh) << 23);   // 2^sh (ex >= 1: the diagonal 1 / L_rr >= 1)
         long long w[8];
