@@ -578,39 +578,6 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
     }
 }
 
-// Lower triangle of Z_s = D (Z + F G^T) D written as Q60 int64 in place
-// (padded rows/columns: identity).  A block covers 32 x 32 entries, a thread
-// four consecutive columns of one row (its row's F and 2^60 D_i loaded once);
-// the scaling by 2^60 is folded into D_i, so each entry costs 7 + 2 FP64
-// operations and one conversion.
-__global__ void __launch_bounds__(256)
-zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
-                const double* __restrict__ G, const double* __restrict__ D) {
-    const int64_t bi = blockIdx.y, bj = blockIdx.x;
-    if (bj > bi) return;
-    const int64_t i = bi * 32 + threadIdx.y;
-    const int64_t j0 = bj * 32 + 4 * threadIdx.x;   // 8 x 32 threads
-    if (i >= Np || j0 > i) return;
-    double fi[7];
-    const bool row_in = i < N;
-    const double di = row_in ? D[i] * 0x1p60 : 0.0;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) fi[k] = row_in ? F[7 * i + k] : 0.0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int64_t j = j0 + c;
-        if (j > i) break;
-        double* z = Z + i * Np + j;
-        long long* q = reinterpret_cast<long long*>(z);
-        if (!row_in || j >= N) { *q = (i == j) ? (1ll << kFL) : 0; continue; }
-        double v = *z;
-        const double* gj = G + 7 * j;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) v = fma(fi[k], gj[k], v);
-        *q = __double2ll_rn(di * v * D[j]);
-    }
-}
-
 // Double-single arithmetic: a value is an unevaluated sum hi + lo of two
 // floats (about 44 significant bits; Dekker 1971, with the products split
 // by FMA).  GB300 issues FP32 about eighty times faster than FP64 per SM,
@@ -677,6 +644,77 @@ __device__ __forceinline__ void ds_sqrt_inv(dsf d, dsf& l, dsf& inv, dsf& inv2) 
     inv2 = ds_mul(inv, inv);
 }
 
+
+// A double as an unevaluated sum of two floats without FP64 arithmetic:
+// the high float keeps the top 24 significand bits (truncated), the low one
+// the other 29 bits (rounded to 24), so hi + lo equals z to 2^-48 relative.
+// Below 2^-74 only the high float is kept and below 2^-126 the value becomes
+// 0: against entries of Z_s of order 1 such terms are far below the 39-bit
+// digits taken from it.
+__device__ __forceinline__ dsf ds_from_double(double z) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(z);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int E = (int)((b >> 52) & 0x7FF) - 1023;
+    if (E < -126) return {0.f, 0.f};
+    if (E > 127) return {__uint_as_float(sign | 0x7F800000u), 0.f};   // beyond float range (or not finite)
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;                // 52 fraction bits
+    const float hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29));
+    const int es = E - 52 + 127;                                         // exponent field of 2^(E - 52)
+    float lo = 0.f;
+    if (es >= 1) lo = __fmul_rn(__uint2float_rn((unsigned)(m & 0x1FFFFFFFu)), __uint_as_float((unsigned)es << 23));
+    return {hi, sign ? -lo : lo};
+}
+
+// Lower triangle of Z_s = D (Z + F G^T) D written as Q60 int64 in place
+// (padded rows/columns: identity), in double-single arithmetic (Z_s is split
+// into digits of 39 bits afterwards).  A block covers 32 x 32 entries, a
+// thread four consecutive columns of one row; the block's rows of F and D
+// (with the 2^60 folded into D_i) and columns of G and D are converted once
+// into shared memory.
+__global__ void __launch_bounds__(256)
+zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
+                const double* __restrict__ G, const double* __restrict__ D) {
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;
+    if (bj > bi) return;
+    __shared__ dsf Fs[32][7], Gs[32][7], Dr[32], Dc[32];
+    const int tid = threadIdx.y * 8 + threadIdx.x;
+    for (int e = tid; e < 2 * 32 * 7 + 64; e += 256) {
+        if (e < 224) {
+            const int64_t i = bi * 32 + e / 7;
+            Fs[e / 7][e % 7] = i < N ? ds_from_double(F[7 * i + e % 7]) : dsf{0.f, 0.f};
+        } else if (e < 448) {
+            const int q = e - 224;
+            const int64_t j = bj * 32 + q / 7;
+            Gs[q / 7][q % 7] = j < N ? ds_from_double(G[7 * j + q % 7]) : dsf{0.f, 0.f};
+        } else if (e < 480) {
+            const int64_t i = bi * 32 + (e - 448);
+            Dr[e - 448] = i < N ? ds_from_double(D[i] * 0x1p60) : dsf{0.f, 0.f};
+        } else {
+            const int64_t j = bj * 32 + (e - 480);
+            Dc[e - 480] = j < N ? ds_from_double(D[j]) : dsf{0.f, 0.f};
+        }
+    }
+    __syncthreads();
+    const int y = threadIdx.y;
+    const int64_t i = bi * 32 + y;
+    const int64_t j0 = bj * 32 + 4 * threadIdx.x;   // 8 x 32 threads
+    if (i >= Np || j0 > i) return;
+    const bool row_in = i < N;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int64_t j = j0 + c;
+        if (j > i) break;
+        double* z = Z + i * Np + j;
+        long long* q = reinterpret_cast<long long*>(z);
+        if (!row_in || j >= N) { *q = (i == j) ? (1ll << kFL) : 0; continue; }
+        const int jc = (int)(j - bj * 32);
+        dsf v = ds_from_double(*z);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v = ds_fma(v, Fs[y][k], Gs[jc][k]);
+        v = ds_mul(ds_mul(Dr[y], v), Dc[jc]);
+        *q = __float2ll_rn(v.h) + __float2ll_rn(v.l);
+    }
+}
 
 // Cholesky of the 128 x 128 diagonal block from Q60 (L in the lower
 // triangle, its inverse X = L^-1 transposed in the upper one, both in
