@@ -165,6 +165,20 @@ CCOV_API ccov_status ccov_covariance(ccov_ctx* ctx, double* out, int out_memory,
 CCOV_API ccov_status ccov_get_blocks(ccov_ctx* ctx, double* U, double* A_inv, double* W);
 CCOV_API ccov_status ccov_get_schur(ccov_ctx* ctx, double* Z, double* G, double* W7);
 
+/* Selected 9 x 9 blocks Z_ij of the reduced camera matrix (Sec. 4.2, Eq.
+ * schur-complement-inversion: Z = M_PP - M_PX A^-1 M_XP), for checking a
+ * large scene on sampled blocks without copying all of Z.  Valid between
+ * ccov_schur and ccov_covariance (which consumes Z in place; afterwards the
+ * call returns INVALID_ARG until ccov_schur runs again).
+ *   ij       nblocks pairs (i, j) of camera indices with 0 <= j <= i < n
+ *            (the stored lower triangle; Z_ji = Z_ij^T), host memory
+ *   nblocks  >= 0
+ *   out      nblocks x 81 float64, row-major blocks, host memory (caller's);
+ *            a diagonal block (i = j) holds its lower triangle, the entries
+ *            above its diagonal are undefined
+ * INVALID_ARG for a pair outside the lower triangle or before ccov_schur. */
+CCOV_API ccov_status ccov_get_schur_blocks(ccov_ctx* ctx, const int64_t* ij, int64_t nblocks, double* out);
+
 CCOV_API ccov_status ccov_get_stats(const ccov_ctx* ctx, ccov_stats* out);
 
 /* Batched form, Sec. 5 (uncertainty for sub-reconstructions): the camera

@@ -90,6 +90,57 @@ def schur_blocks_unscaled(scene):
     return Zp[:N, :N], Zp[:N, N:], -Zp[N:, N:]
 
 
+class _SubScene:
+    """The part of a scene that the oracle reads: cameras, points and
+    observations (with their information weights)."""
+
+    def __init__(self, cams, pts, obs_cam, obs_pt, sigma, obs_cov):
+        self.cams, self.pts, self.obs_cam, self.obs_pt = cams, pts, obs_cam, obs_pt
+        self.sigma, self.obs_cov = sigma, obs_cov
+        self.n, self.m, self.t = cams.shape[0], pts.shape[0], obs_cam.shape[0]
+
+
+def schur_rows_unscaled(scene, cams):
+    """Block rows Z[i, :] (9 x 9n) of the unconditioned reduced camera matrix
+    Z = M_PP - M_PX A^-1 M_XP (Eq. schur-complement-inversion) for the cameras
+    i in `cams`, for scenes too large for the dense route.  The definition
+    written out per block: Z_ij = [i = j] M_PP,ii - sum over the points p that
+    i and j both observe of W_ip A_p^-1 W_jp^T, with W_ip the camera-point
+    block of M summed over the observations of p by i.  Only the points that
+    camera i observes enter, each with A_p from all of its observations, so
+    the information blocks come from the sub-scene of those points.
+    Returns {i: array (9, 9n)}."""
+    cams = np.unique(np.asarray(cams, dtype=np.int64))
+    pts_sel = np.unique(scene.obs_pt[np.isin(scene.obs_cam, cams)])
+    keep = np.isin(scene.obs_pt, pts_sel)
+    cam_sel = np.unique(scene.obs_cam[keep])
+    cam_of = np.full(scene.n, -1, dtype=np.int64)
+    cam_of[cam_sel] = np.arange(cam_sel.size)
+    pt_of = np.full(scene.m, -1, dtype=np.int64)
+    pt_of[pts_sel] = np.arange(pts_sel.size)
+    sub = _SubScene(scene.cams[cam_sel], scene.pts[pts_sel], cam_of[scene.obs_cam[keep]],
+                    pt_of[scene.obs_pt[keep]], scene.sigma,
+                    None if scene.obs_cov is None else scene.obs_cov[keep])
+    U, A, W, _, _ = information.blocks(sub)
+    Ainv = np.linalg.inv(A)
+    # observations of each point of the sub-scene
+    order = np.argsort(sub.obs_pt, kind="stable")
+    start = np.searchsorted(sub.obs_pt[order], np.arange(sub.m + 1))
+    rows = {}
+    for i in cams:
+        a = cam_of[i]
+        row = np.zeros((9, 9 * scene.n))
+        row[:, 9 * i:9 * i + 9] = U[a]
+        for o in np.nonzero(sub.obs_cam == a)[0]:
+            p = sub.obs_pt[o]
+            K = W[o] @ Ainv[p]                       # W_ip A_p^-1 (9 x 3)
+            for o2 in order[start[p]:start[p + 1]]:
+                j = cam_sel[sub.obs_cam[o2]]
+                row[:, 9 * j:9 * j + 9] -= K @ W[o2].T
+        rows[int(i)] = row
+    return rows
+
+
 def camera_covariance(scene, scaling="jacobi", full=False):
     """Sigma_P = S_P Z_s S_P, Z_s the top-left 9n x 9n block of Z_p^-1.
     Returns the diagonal 9x9 blocks (n, 9, 9), or the whole 9n x 9n matrix."""

@@ -25,7 +25,7 @@ CCOV_MEM_HOST, CCOV_MEM_DEVICE = 0, 1
 CCOV_NULL_PAPER, CCOV_NULL_CLOSED = 0, 1
 
 EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_nullspace",
-            "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_stats",
+            "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_schur_blocks", "ccov_get_stats",
             "ccov_destroy", "ccov_status_string", "ccov_last_error",
             "ccov_spd_inverse_blocks_noalloc", "ccov_batch_covariance", "ccov_batch_create",
             "ccov_batch_run", "ccov_batch_destroy"]
@@ -76,6 +76,7 @@ def load() -> C.CDLL:
         "ccov_covariance": ([P, P, I, P], I),
         "ccov_get_blocks": ([P, P, P, P], I),
         "ccov_get_schur": ([P, P, P, P], I),
+        "ccov_get_schur_blocks": ([P, P, I64, P], I),
         "ccov_get_stats": ([P, C.POINTER(Stats)], I),
         "ccov_destroy": ([P], None),
         "ccov_status_string": ([I], C.c_char_p),
@@ -210,6 +211,14 @@ class Context:
         st = Stats()
         self._check(load().ccov_get_stats(self._h, C.byref(st)))
         return st.as_dict()
+
+    def ccov_get_schur_blocks(self, pairs):
+        """Blocks Z_ij (k x 9 x 9) for pairs (i, j), 0 <= j <= i < n (of a
+        diagonal block only the lower triangle is defined)."""
+        ij = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        out = np.empty((ij.shape[0], 9, 9))
+        self._check(load().ccov_get_schur_blocks(self._h, _ptr(ij), ij.shape[0], _ptr(out)))
+        return out
 
     def run(self, out=None):
         """Steps (a)-(d) in order."""

@@ -697,6 +697,21 @@ ccov_status ccov_get_schur(ccov_ctx* h, double* Z, double* G, double* W7) {
     return CCOV_OK;
 }
 
+ccov_status ccov_get_schur_blocks(ccov_ctx* h, const int64_t* ij, int64_t nblocks, double* out) {
+    if (!h || nblocks < 0 || (nblocks > 0 && (!ij || !out))) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 3) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_get_schur_blocks: call ccov_schur first");
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const int64_t i = ij[2 * b], j = ij[2 * b + 1];
+        if (i < 0 || j < 0 || i >= c.n || j > i)
+            return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_get_schur_blocks: need 0 <= j <= i < n");
+        CK(cudaMemcpy2D(out + 81 * b, sizeof(double) * 9, c.d_Z + 9 * i * c.Np + 9 * j, sizeof(double) * c.Np,
+                        sizeof(double) * 9, 9, cudaMemcpyDeviceToHost),
+           "copy Z block");
+    }
+    return CCOV_OK;
+}
+
 ccov_status ccov_get_stats(const ccov_ctx* h, ccov_stats* out) {
     if (!h || !out) return CCOV_ERR_INVALID_ARG;
     *out = h->c.stats;

@@ -53,6 +53,23 @@ def test_sparse_schur_equals_dense_schur():
     np.testing.assert_allclose(Zp, want, rtol=0, atol=1e-9 * np.abs(want).max())
 
 
+def test_sampled_schur_rows_equal_rows_of_the_whole_schur_complement():
+    """The block rows that schur_rows_unscaled builds from the sub-scene of a
+    camera's points equal the rows of Z over the whole scene (pinned above
+    against the dense bordered matrix), on a scene whose sub-scenes drop
+    points, and on one whose tracks leave camera pairs without shared points."""
+    for sc in (synth.shell_scene(n=40, m=600, seed=8), synth.ring_scene(n=12, m=60, track_len=2, seed=3)):
+        _check_sampled_rows(sc, [0, 7, sc.n - 1])
+
+
+def _check_sampled_rows(sc, picks):
+    Z, _, _ = covariance.schur_blocks_unscaled(sc)
+    rows = covariance.schur_rows_unscaled(sc, picks)
+    assert sorted(rows) == picks
+    for i in picks:
+        np.testing.assert_allclose(rows[i], Z[9 * i:9 * i + 9], rtol=0, atol=1e-12 * np.abs(Z).max())
+
+
 def test_invariants_of_natural_covariance():
     sc = synth.workload("ring20")
     Sigma = covariance.camera_covariance(sc, full=True)
