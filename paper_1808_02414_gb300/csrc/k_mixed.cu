@@ -43,7 +43,7 @@ constexpr int kBM = 128, kBN = 64, kKS = 16;              // tile M x N, K per p
 constexpr int kAPl = kBM * kKS * 2;                        // 4 KB: one digit plane of A per stage
 constexpr int kBPl = kBN * kKS * 2;                        // 2 KB
 constexpr int kCBox = kBM * 16 * 8;                        // 16 KB: 16 int64 columns x 128 rows
-constexpr int kCTile = 4 * kCBox;                          // 64 KB result tile staged for TMA
+constexpr int kCTile = 2 * kCBox;                          // 32 KB: half of the result tile, staged for TMA
 constexpr int kFX = 42;                                    // fixed point of X = L^-1
 constexpr int kFL = 60;                                    // fixed point of Z_s and L
 constexpr int kKMax = 256;
@@ -400,24 +400,35 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
 #pragma unroll
                 for (int q = 0; q < kEpiCols; ++q) res[q] = shift_round(res[q], sh + (eBp ? eBp[q] : 0));
             }
-            // phase 2: stage -A B^T (or A B^T) for the copy-out; two columns (one 16-byte chunk) per access; with the 128-byte
-            // swizzle (chunk index XOR row % 8) the 32 rows of a warp spread
-            // over all banks
-#pragma unroll
-            for (int q = 0; q < kEpiCols; q += 2) {
-                const int col = kEpiCols * part + q;
-                const int box = col >> 4, jj = col & 15;
-                longlong2* cp = (longlong2*)(ctile + box * kCBox + r * 128 + (((jj >> 1) ^ (r & 7)) << 4));
-                *cp = g.sub ? make_longlong2(-res[q], -res[q + 1]) : make_longlong2(res[q], res[q + 1]);
-            }
-            fence_proxy_async();
-            epi_bar();
-            if (leader) {
-                for (int b = 0; b < 4; ++b) {
-                    if (g.sub) tma_reduce_add_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
-                    else tma_store_2d(&mapC, ctile + b * kCBox, cx + 16 * b, cy);
+            // phase 2: stage -A B^T (or A B^T) for the copy-out, 32 columns at a
+            // time through a 32 KB buffer (the space saved holds one more
+            // pipeline stage); two columns (one 16-byte chunk) per access; with
+            // the 128-byte swizzle (chunk index XOR row % 8) the 32 rows of a
+            // warp spread over all banks
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1) {
+                    if (leader) bulk_wait_read0();   // the first half has left shared memory
+                    epi_bar();
                 }
-                bulk_commit();
+                if ((part >> 1) == half) {
+#pragma unroll
+                    for (int q = 0; q < kEpiCols; q += 2) {
+                        const int col = kEpiCols * part + q;
+                        const int box = (col >> 4) & 1, jj = col & 15;
+                        longlong2* cp = (longlong2*)(ctile + box * kCBox + r * 128 + (((jj >> 1) ^ (r & 7)) << 4));
+                        *cp = g.sub ? make_longlong2(-res[q], -res[q + 1]) : make_longlong2(res[q], res[q + 1]);
+                    }
+                }
+                fence_proxy_async();
+                epi_bar();
+                if (leader) {
+                    for (int b = 0; b < 2; ++b) {
+                        const int x = cx + 16 * (2 * half + b);
+                        if (g.sub) tma_reduce_add_2d(&mapC, ctile + b * kCBox, x, cy);
+                        else tma_store_2d(&mapC, ctile + b * kCBox, x, cy);
+                    }
+                    bulk_commit();
+                }
             }
         }
         if (leader) bulk_wait0();
