@@ -139,6 +139,8 @@ ccov_status check_device(Ctx& c, const char* where) {
             return fail(&c, CCOV_ERR_DEGENERATE, "%s: J_r^T J_r singular (camera %d)", where, flag[1]);
         case ccov::DEV_TIMEOUT:
             return fail(&c, CCOV_ERR_TIMEOUT, "%s: device wait gave up (site %d)", where, flag[1]);
+        case ccov::DEV_SMEM_ALIGN:
+            return fail(&c, CCOV_ERR_CUDA, "%s: shared memory window of the GEMM not 1024-byte aligned", where);
         default:
             return fail(&c, CCOV_ERR_CUDA, "%s: device error code %d", where, flag[0]);
     }

@@ -23,6 +23,7 @@ enum DevErr : int {
     DEV_SINGULAR_JR = 5,  // J_r^T J_r of a camera singular (nullspace solve)
     DEV_TIMEOUT = 6,      // a bounded spin-wait gave up
     DEV_BAD_INDEX = 7,    // a sample index outside the training set (surrogate)
+    DEV_SMEM_ALIGN = 8,   // dynamic shared memory window not 1024-byte aligned (GEMM)
 };
 
 struct MixedState;  // emulated-FP64 tensor-core path, k_mixed.cu

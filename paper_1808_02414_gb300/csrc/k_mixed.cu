@@ -43,7 +43,7 @@ constexpr int kBM = 128, kBN = 64, kKS = 16;              // tile M x N, K per p
 constexpr int kAPl = kBM * kKS * 2;                        // 4 KB: one digit plane of A per stage
 constexpr int kBPl = kBN * kKS * 2;                        // 2 KB
 constexpr int kCBox = kBM * 16 * 8;                        // 16 KB: 16 int64 columns x 128 rows
-constexpr int kCTile = 2 * kCBox;                          // 32 KB: half of the result tile, staged for TMA
+constexpr int kCTile = kCBox;                              // 16 KB: a quarter of the result tile, staged for TMA
 constexpr int kFX = 42;                                    // fixed point of X = L^-1
 constexpr int kFL = 60;                                    // fixed point of Z_s and L
 constexpr int kKMax = 256;
@@ -217,17 +217,26 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
 // Persistent warp-specialised kernel, launched in clusters of two CTAs that
 // work on the two halves (adjacent 64-column tiles) of one 128 x 128 block:
 // they need the same A tile, and each CTA loads half of its digit planes and
-// multicasts them to both.  Warp 0 lane 0: producer of the digit tiles.  Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps
-// 2..17: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter
-// of the 64 columns.  The result tile leaves through shared memory with TMA:
-// C -= A B^T as a reduce-add of -A B^T into C (the addition happens in L2,
-// so C is never read into the SM), C = A B^T as a plain store.
+// multicasts them to both.  Warp 0 lane 0: producer of the digit tiles.
+// Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps 2..17:
+// epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter of the
+// 64 columns.  The result tile leaves through shared memory with TMA, a
+// quarter at a time: C -= A B^T as a reduce-add of -A B^T into C (the
+// addition happens in L2, so C is never read into the SM), C = A B^T as a
+// plain store.
 template <int S, int K>
 __global__ void __launch_bounds__(kThreads, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB, GemmArgs g) {
     using SL = Slots<S, K>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // the 128-byte-swizzled staging buffer needs a 1024-byte aligned start;
+    // the launch reserves no padding for it (the space holds a pipeline
+    // stage), so a misaligned window is reported instead of used
+    if (smem_u32(smem_raw) & 1023u) {
+        if (threadIdx.x == 0) set_flag(g.flag, DEV_SMEM_ALIGN, 0);
+        return;
+    }
+    unsigned char* base = smem_raw;
     constexpr int stage_bytes = S * (kAPl + kBPl);
     unsigned char* ctile = base;
     unsigned char* tiles = base + kCTile;
@@ -400,33 +409,28 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
 #pragma unroll
                 for (int q = 0; q < kEpiCols; ++q) res[q] = shift_round(res[q], sh + (eBp ? eBp[q] : 0));
             }
-            // phase 2: stage -A B^T (or A B^T) for the copy-out, 32 columns at a
-            // time through a 32 KB buffer (the space saved holds one more
-            // pipeline stage); two columns (one 16-byte chunk) per access; with
-            // the 128-byte swizzle (chunk index XOR row % 8) the 32 rows of a
-            // warp spread over all banks
-            for (int half = 0; half < 2; ++half) {
-                if (half == 1) {
-                    if (leader) bulk_wait_read0();   // the first half has left shared memory
+            // phase 2: stage -A B^T (or A B^T) for the copy-out, 16 columns (one
+            // part's warps) at a time through a 16 KB buffer, so that the
+            // space of the rest of the tile holds two more pipeline stages; two
+            // columns (one 16-byte chunk) per access; with the 128-byte swizzle
+            // (chunk index XOR row % 8) the 32 rows of a warp spread over all banks
+            for (int rd = 0; rd < kBN / kEpiCols; ++rd) {
+                if (rd > 0) {
+                    if (leader) bulk_wait_read0();   // the previous columns have left shared memory
                     epi_bar();
                 }
-                if ((part >> 1) == half) {
+                if (part == rd) {
 #pragma unroll
                     for (int q = 0; q < kEpiCols; q += 2) {
-                        const int col = kEpiCols * part + q;
-                        const int box = (col >> 4) & 1, jj = col & 15;
-                        longlong2* cp = (longlong2*)(ctile + box * kCBox + r * 128 + (((jj >> 1) ^ (r & 7)) << 4));
+                        longlong2* cp = (longlong2*)(ctile + r * 128 + ((((q >> 1)) ^ (r & 7)) << 4));
                         *cp = g.sub ? make_longlong2(-res[q], -res[q + 1]) : make_longlong2(res[q], res[q + 1]);
                     }
                 }
                 fence_proxy_async();
                 epi_bar();
                 if (leader) {
-                    for (int b = 0; b < 2; ++b) {
-                        const int x = cx + 16 * (2 * half + b);
-                        if (g.sub) tma_reduce_add_2d(&mapC, ctile + b * kCBox, x, cy);
-                        else tma_store_2d(&mapC, ctile + b * kCBox, x, cy);
-                    }
+                    if (g.sub) tma_reduce_add_2d(&mapC, ctile, cx + kEpiCols * rd, cy);
+                    else tma_store_2d(&mapC, ctile, cx + kEpiCols * rd, cy);
                     bulk_commit();
                 }
             }
@@ -1014,7 +1018,7 @@ bool make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) {
 }
 
 size_t gemm_smem(int s, int stages) {
-    return 1024 + (size_t)kCTile + (size_t)stages * s * (kAPl + kBPl) + 8 * (2 * stages + 4) + 16;
+    return (size_t)kCTile + (size_t)stages * s * (kAPl + kBPl) + 8 * (2 * stages + 4) + 16;
 }
 
 int pick_stages(int s) {
