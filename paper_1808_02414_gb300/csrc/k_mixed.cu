@@ -115,6 +115,14 @@ struct Slots {
     static constexpr int total = S + extra;
     static_assert(total * kBN <= 512, "TMEM columns");
     static_assert(S <= 2 * cap, "two accumulator levels at most");
+    // digit products summed in accumulator sl (main accumulators of the
+    // orders 0..S-1, then the second ones of the orders cap..S-1)
+    __host__ __device__ static constexpr int products(int sl) {
+        return sl < S ? (sl < cap - 1 ? sl : cap - 1) - (sl > S - 1 ? sl - (S - 1) : 0) + 1
+                      : (sl - S + cap) - cap + 1;
+    }
+    // |P| <= products * K * 2^14 <= 2^22: the biased pattern is exact unchecked
+    __host__ __device__ static constexpr bool small(int sl) { return products(sl) * K <= 256; }
 };
 
 // Tile schedule: M tiles of 128 rows x N tiles of 64 columns; `lower` keeps
@@ -378,14 +386,16 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
                 // case takes the biased bit patterns, the rare one (some
                 // |P| > 2^22 in the warp) reads the chunk again and converts
                 unsigned u[SL::total][8];
-                unsigned all_and = 0xffffffffu, all_or = 0u;
+                unsigned all_and = 0x4B400000u, all_or = 0x4B400000u;   // the pattern of 0
 #pragma unroll
                 for (int sl = 0; sl < SL::total; ++sl)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         u[sl][j] = __float_as_uint(__fadd_rn(v[sl][j], kMagic));
-                        all_and &= u[sl][j];
-                        all_or |= u[sl][j];
+                        if (!SL::small(sl)) {   // accumulators of one product need no check
+                            all_and &= u[sl][j];
+                            all_or |= u[sl][j];
+                        }
                     }
                 if (__all_sync(0xffffffffu, (all_and >> 23) == kMagicTop && (all_or >> 23) == kMagicTop)) {
 #pragma unroll
@@ -786,35 +796,54 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
             }
             __syncthreads();
         }
-        // X_pp = L_pp^-1 by column sweeps: row j of X is scaled by 1/L_jj, then
-        // removed from the rows below; X[r][c] (r > c) lives at S[c][r]
-        {
-            const int r = tid >> 4, c2 = (tid & 15) * 2;   // 32 rows x 16 threads, 2 columns each
-            for (int jj = 0; jj < kPW; ++jj) {
-                // X[jj][c] = (delta_jc - sum_{k<jj} L[jj][k] X[k][c]) / L[jj][jj] was formed
-                // by the earlier sweeps; finish row jj, then eliminate it below
-                if (r == jj) {
-                    for (int q = 0; q < 2; ++q) {
-                        const int c = c2 + q;
-                        if (c < jj) {
-                            S[(b0 + c) * kLD + b0 + jj] = ds_mul(S[(b0 + c) * kLD + b0 + jj], invd[b0 + jj]);
-                        }
-                    }
-                }
-                __syncthreads();
-                if (r > jj) {
-                    const dsf l = ds_neg(S[(b0 + r) * kLD + b0 + jj]);
-                    for (int q = 0; q < 2; ++q) {
-                        const int c = c2 + q;
-                        if (c > jj || c >= r) continue;
-                        // X[r][c] += -L[r][jj] X[jj][c]; X[jj][jj] = invd, X[r][c] starts at 0
-                        const dsf xjc = c == jj ? invd[b0 + jj] : S[(b0 + c) * kLD + b0 + jj];
-                        dsf* xr = &S[(b0 + c) * kLD + b0 + r];
-                        *xr = ds_fma(c == jj ? dsf{0.f, 0.f} : *xr, l, xjc);
-                    }
-                }
-                __syncthreads();
+        // X_pp = L_pp^-1 by blocks: the four 8 x 8 diagonal blocks by column
+        // sweeps (one warp each: row j of X is scaled by 1 / L_jj, then removed
+        // from the rows below), then X21 = -X22 L21 X11 for the two 16 x 16
+        // blocks and for the whole 32 x 32 block (T holds L21 X11); X[r][c]
+        // (r > c) lives at S[c][r]
+        if (warp < 4) {
+            const int o = b0 + 8 * warp;
+            int r = 0, c = 0;                       // lane -> entry (r, c), c < r < 8
+            if (lane < 28) {
+                r = 1;
+                while ((r + 1) * r / 2 <= lane) ++r;
+                c = lane - r * (r - 1) / 2;
             }
+            for (int j = 0; j < 8; ++j) {
+                if (lane < 28 && r == j) S[(o + c) * kLD + o + j] = ds_mul(S[(o + c) * kLD + o + j], invd[o + j]);
+                __syncwarp();
+                if (lane < 28 && r > j && c <= j) {
+                    const dsf m = ds_neg(S[(o + r) * kLD + o + j]);
+                    const dsf xjc = c == j ? invd[o + j] : S[(o + c) * kLD + o + j];
+                    dsf* xr = &S[(o + c) * kLD + o + r];
+                    *xr = ds_fma(c == j ? dsf{0.f, 0.f} : *xr, m, xjc);
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int w = 8; w < kPW; w *= 2) {          // blocks of 2w rows: X21 (w x w) from X11, X22
+            const int nb = kPW / (2 * w);           // such blocks in the panel
+            if (tid < nb * w * w) {
+                const int h = tid / (w * w), i = (tid / w) % w, j = tid % w, o = b0 + 2 * w * h;
+                dsf v = {0.f, 0.f};
+                for (int k = j; k < w; ++k) {
+                    const dsf x = k == j ? invd[o + j] : S[(o + j) * kLD + o + k];
+                    v = ds_fma(v, S[(o + w + i) * kLD + o + k], x);
+                }
+                T[tid] = v;
+            }
+            __syncthreads();
+            if (tid < nb * w * w) {
+                const int h = tid / (w * w), i = (tid / w) % w, j = tid % w, o = b0 + 2 * w * h;
+                dsf v = {0.f, 0.f};
+                for (int k = 0; k <= i; ++k) {
+                    const dsf x = k == i ? invd[o + w + i] : S[(o + w + k) * kLD + o + w + i];
+                    v = ds_fma(v, x, T[h * w * w + k * w + j]);
+                }
+                S[(o + j) * kLD + o + w + i] = ds_neg(v);
+            }
+            __syncthreads();
         }
         if (b0 + kPW == kNB) break;
         // rows below: L[i][b0 + c] = sum_{k <= c} A[i][b0 + k] X_pp[c][k].
