@@ -630,6 +630,16 @@ __device__ __forceinline__ dsf ds_fma(dsf acc, dsf a, dsf b) {
 
 __device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.h, -a.l}; }
 
+// a + b (two-sum of the high parts, low parts added, then renormalised)
+__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float v = __fsub_rn(s, a.h);
+    float t = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
+    t = __fadd_rn(t, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
 // Row and column of entry t of a lower triangle stored row by row.
 __device__ __forceinline__ void tri_index(int t, int& i, int& l) {
     i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -973,7 +983,9 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
 
 // Camera Gram blocks Sig_c += X[k, c]^T X[k, c] from the finished Q42 row
 // block k of X (128 rows), 4 cameras (36 columns) per CTA, summed in
-// double-single arithmetic and added to the FP64 blocks once.
+// double-single arithmetic and added to the FP64 blocks once.  A thread
+// takes entries (a, b), a <= b, of the symmetric blocks (45 per camera) and
+// sums the 128 rows in four interleaved chains.
 constexpr int kGW = 36;
 __global__ void __launch_bounds__(128)
 gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long* __restrict__ R,
@@ -988,13 +1000,25 @@ gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long*
         T[r][c] = (gc < ncols) ? ds_from_fixed(R[(k0 + r) * Np + gc], kS) : dsf{0.f, 0.f};
     }
     __syncthreads();
-    for (int e = tid; e < 4 * 81; e += 128) {
-        int g = e / 81, ab = e % 81, a = ab / 9, b = ab % 9;
-        int64_t cam = (c0 / 9) + g;
+    for (int e = tid; e < 4 * 45; e += 128) {
+        const int g = e / 45;
+        int q = e % 45, a = 0;                 // q -> (a, b) of the upper triangle, row by row
+        while (q >= 9 - a) { q -= 9 - a; ++a; }
+        const int b = a + q;
+        const int64_t cam = (c0 / 9) + g;
         if (cam >= n || c0 + 9 * g >= ncols) continue;
-        dsf v = {0.f, 0.f};
-        for (int r = 0; r < kNB; ++r) v = ds_fma(v, T[r][9 * g + a], T[r][9 * g + b]);
-        Sig[81 * cam + ab] += (double)v.h + (double)v.l;
+        const int ca = 9 * g + a, cb = 9 * g + b;
+        dsf v0 = {0.f, 0.f}, v1 = v0, v2 = v0, v3 = v0;
+        for (int r = 0; r < kNB; r += 4) {
+            v0 = ds_fma(v0, T[r][ca], T[r][cb]);
+            v1 = ds_fma(v1, T[r + 1][ca], T[r + 1][cb]);
+            v2 = ds_fma(v2, T[r + 2][ca], T[r + 2][cb]);
+            v3 = ds_fma(v3, T[r + 3][ca], T[r + 3][cb]);
+        }
+        const dsf v = ds_add(ds_add(v0, v1), ds_add(v2, v3));
+        const double sum = (double)v.h + (double)v.l;
+        Sig[81 * cam + 9 * a + b] += sum;
+        if (a != b) Sig[81 * cam + 9 * b + a] += sum;
     }
 }
 
