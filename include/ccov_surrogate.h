@@ -5,7 +5,7 @@
  * The paper has no learned component.  Its uses of camera covariances
  * (Sec. 1: choosing the next best view, detecting wrongly added cameras,
  * filtering unconstrained cameras) only need a fast, approximate screen,
- * with the exact method kept as the fallback and as the judge of the error.
+ * with the exact method kept as the fallback and as the reference for its error.
  *
  * Per camera i (after ccov_information):
  *   Z_ii     the 9x9 diagonal block of the reduced camera matrix of Sec. 4.2
