@@ -70,6 +70,26 @@ def _check_sampled_rows(sc, picks):
         np.testing.assert_allclose(rows[i], Z[9 * i:9 * i + 9], rtol=0, atol=1e-12 * np.abs(Z).max())
 
 
+def test_planted_mistake_in_sampled_schur_rows_is_caught(monkeypatch):
+    """Drop one observation's camera-point block from the sampled rows (as a
+    wrong track lookup would): the comparison with the whole Schur complement
+    fails."""
+    sc = synth.shell_scene(n=20, m=300, seed=8)
+    Z, _, _ = covariance.schur_blocks_unscaled(sc)
+    orig = covariance.information.blocks
+
+    def broken(scene, *a, **k):
+        U, A, W, Jc, Jp = orig(scene, *a, **k)
+        W = W.copy()
+        W[0] = 0.0
+        return U, A, W, Jc, Jp
+
+    monkeypatch.setattr(covariance.information, "blocks", broken)
+    rows = covariance.schur_rows_unscaled(sc, [int(sc.obs_cam[0])])
+    i = int(sc.obs_cam[0])
+    assert np.abs(rows[i] - Z[9 * i:9 * i + 9]).max() > 1e-6 * np.abs(Z).max()
+
+
 def test_invariants_of_natural_covariance():
     sc = synth.workload("ring20")
     Sigma = covariance.camera_covariance(sc, full=True)
