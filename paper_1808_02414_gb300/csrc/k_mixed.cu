@@ -753,12 +753,12 @@ zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __r
 
 // Cholesky of the 128 x 128 diagonal block from Q60 (L in the lower
 // triangle, its inverse X = L^-1 transposed in the upper one, both in
-// double-single shared memory), L written back as Q60, X as double-single
-// pairs (full, zero above the diagonal).  Blocked by 32-column panels: all
-// threads factor the panel's diagonal block column by column, invert it
-// column sweep by column sweep, solve the rows below with that inverse and
-// update the trailing block; the off-diagonal blocks of X then follow by
-// block rows, X_ij = -X_ii sum_k L_ik X_kj.
+// double-single shared memory), L written back as Q60, X as digit planes
+// with row exponents.  Blocked by 32-column panels: all threads factor the
+// panel's diagonal block column by column, invert it by blocks (8 x 8 column
+// sweeps, then X21 = -X22 L21 X11 twice), solve the rows below with that
+// inverse and update the trailing block; the off-diagonal blocks of X then
+// follow by block rows, X_ij = -X_ii sum_k L_ik X_kj.
 constexpr int kLD = kNB + 1;
 constexpr int kPW = 32;                                   // panel width
 constexpr size_t kDiagSmem = sizeof(dsf) * (kNB * kLD + kNB + 3 * kPW * kPW);
