@@ -82,7 +82,9 @@ typedef struct {
                              CCOV_MEM_HOST (default) or CCOV_MEM_DEVICE */
     int profile;          /* 1: bracket every dense trailing-update GEMM with CUDA
                              events and report their time in ccov_stats */
-    int reserved[7];      /* set to zero */
+    int est_cameras;      /* cameras sampled by the error estimate of ccov_covariance
+                             (only when its est_rel_err is not NULL): 1..16, 0 = 4 */
+    int reserved[6];      /* set to zero */
 } ccov_options;
 
 /* Per-context counters of the last calls (device times from CUDA events). */
@@ -94,9 +96,19 @@ typedef struct {
     int64_t launches;                   /* kernels launched by the last four calls */
     double ms_gemm;                     /* profile = 1: summed device time of the
                                            trailing-update GEMMs of the last ccov_covariance */
-    double gemm_flops;                  /* their algorithmic flops (lower-triangle
-                                           updates counted once) */
+    double gemm_flops;                  /* their executed flops: the MIXED path counts
+                                           every kept 128 x 64 tile times its s(s+1)/2
+                                           digit products, the FP64 path 2 M N K per
+                                           update (lower-triangle updates counted once) */
     int64_t gemm_launches;
+    /* error estimate of the last ccov_covariance that asked for one (est_rel_err
+     * not NULL): the sampled cameras and, per sampled camera, the estimated
+     * relative Frobenius error of its block and the same after the scaling
+     * diag(Sigma_i)^-1/2; est_cameras = 0 when no estimate was made */
+    int64_t est_cameras;
+    int64_t est_index[16];
+    double est_rel[16];
+    double est_norm[16];
 } ccov_stats;
 
 /* Create a context for one scene and copy its inputs to the device.
@@ -150,10 +162,23 @@ CCOV_API ccov_status ccov_nullspace(ccov_ctx* ctx, double* H_P_out);
  * Cholesky factorisation, triangular inverse and the 9x9 diagonal blocks of
  * the inverse.  out: n*81 float64 (row-major 9 x 9 blocks) on the host
  * (out_memory = CCOV_MEM_HOST) or the device (CCOV_MEM_DEVICE).
- * est_rel_err: NULL, or n doubles receiving a per-block estimate of the
- * relative error (0 for the FP64 path, -1 = not estimated for the mixed
- * path, whose per-block error against FP64 is about 5e-9 at 5 digits).  DEGENERATE if the scaled reduced
- * matrix is not positive definite. */
+ * est_rel_err: NULL, or n doubles receiving an a-posteriori estimate of each
+ * block's relative Frobenius error against the exact inverse.  It is computed
+ * (at extra cost O(N^2 k)) for k sampled cameras (ccov_options.est_cameras,
+ * default 4): those with the largest diagonal entry of their Jacobi-scaled
+ * block, i.e. the most ill-determined parameters.  For a sampled camera i the
+ * estimate is the first-order error y^T R of its block, from the residual
+ * R = Z_s y - E_i of the computed columns y = X^T X E_i against a copy of the
+ * scaled matrix Z_s taken before the factorisation (double-single arithmetic
+ * for the MIXED path, FP64 for the FP64 path, where it is an upper estimate
+ * at the residual's own rounding level).  Every other camera receives the
+ * largest of the sampled estimates (the error of a block varies from camera
+ * to camera by up to about 30x at the same conditioning, so this is a
+ * scene-level figure for them).  ccov_stats lists the sampled cameras.
+ * DEGENERATE if the scaled reduced matrix is not positive definite;
+ * NOT_CONVERGED if the MIXED path's fixed-point range is exceeded (a scene too
+ * ill-conditioned for it: an entry of L^-1 beyond 2^19, or a scaled entry
+ * beyond 2), in which case precision FP64 is the remedy. */
 CCOV_API ccov_status ccov_covariance(ccov_ctx* ctx, double* out, int out_memory, double* est_rel_err);
 
 /* Copies of intermediate results for checking (host buffers, NULL to skip):
@@ -227,12 +252,15 @@ CCOV_API void ccov_batch_destroy(ccov_batch* batch);
  *           rejected with CCOV_ERR_INVALID_ARG
  *   blocks  device, (N / 9) x 81 doubles (row-major 9 x 9 blocks), written
  *   stream  a cudaStream_t, or NULL for the legacy default stream; the call
- *           returns after the stream has finished its work
+ *           returns after the stream has finished its work, so it cannot be
+ *           recorded into a CUDA graph: a call on a stream that is being
+ *           captured returns CCOV_ERR_INVALID_ARG and does nothing
  * The first call on a device (that device current) takes the array's address
  * with cudaGetSymbolAddress and sets kernel attributes; it should come before
- * any stream capture.  Every call shares the array and clears what must start
- * at zero; calls that overlap on the GPU race on it.  DEGENERATE if A is not
- * positive definite. */
+ * any stream capture.  Every call shares the array and first clears what must
+ * start at zero, so a call that failed part-way leaves nothing the next call
+ * depends on; calls that overlap on the GPU race on it.  DEGENERATE if A is
+ * not positive definite. */
 CCOV_API ccov_status ccov_spd_inverse_blocks_noalloc(const double* A, int64_t lda, int64_t N, double* blocks,
                                                      void* stream);
 CCOV_API void ccov_destroy(ccov_ctx* ctx);

@@ -22,10 +22,22 @@ extern "C" {
  *         a + b > s - 1 are left out
  *   lower 1: only tiles of 128 x 64 that reach the diagonal (M == N)
  * M and N must be multiples of 128 (tiles of 128 x 64 are worked on in pairs
- * by two-CTA clusters).  Returns TIMEOUT if a bounded device wait gave up. */
+ * by adjacent CTAs).  Returns TIMEOUT if a bounded device wait gave up. */
 CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N, const uint16_t* digA, const int* expA,
                                           const uint16_t* digB, const int* expB, int Fc, int sub, int lower,
                                           long long* C);
+
+/* The same GEMM with its barrier waits limited to wait_ns nanoseconds and, if
+ * skip_fill >= 0, the producer of every CTA leaving out its pipeline fill
+ * number skip_fill (counted from 0 over the CTA's tiles and K slices): the
+ * MMA issuer then waits for data that never comes, gives up after wait_ns,
+ * and the call returns CCOV_ERR_TIMEOUT with C unchanged on the host.  This
+ * exercises the timeout exit of the kernel (producer, MMA issuer and
+ * epilogue leave their loops, the issued MMAs are drained, TMEM is freed)
+ * without hanging the device.  wait_ns: 1e5 .. 1e10. */
+CCOV_API ccov_status ccov_test_ozaki_gemm_wait(int s, int K, int M, int N, const uint16_t* digA, const int* expA,
+                                               const uint16_t* digB, const int* expB, int Fc, int sub, int lower,
+                                               long long* C, long long skip_fill, unsigned long long wait_ns);
 
 #ifdef __cplusplus
 }

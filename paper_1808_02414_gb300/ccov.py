@@ -39,7 +39,8 @@ class CcovError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("mixed_slices", C.c_int), ("nullspace_route", C.c_int),
-                ("input_memory", C.c_int), ("profile", C.c_int), ("reserved", C.c_int * 7)]
+                ("input_memory", C.c_int), ("profile", C.c_int), ("est_cameras", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class Stats(C.Structure):
@@ -48,10 +49,15 @@ class Stats(C.Structure):
                 ("ms_nullspace", C.c_double), ("ms_covariance", C.c_double),
                 ("ms_factor", C.c_double), ("ms_inverse", C.c_double),
                 ("bytes_device", C.c_int64), ("launches", C.c_int64), ("ms_gemm", C.c_double),
-                ("gemm_flops", C.c_double), ("gemm_launches", C.c_int64)]
+                ("gemm_flops", C.c_double), ("gemm_launches", C.c_int64), ("est_cameras", C.c_int64),
+                ("est_index", C.c_int64 * 16), ("est_rel", C.c_double * 16), ("est_norm", C.c_double * 16)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        k = int(self.est_cameras)
+        for name in ("est_index", "est_rel", "est_norm"):
+            d[name] = list(d[name])[:k]
+        return d
 
 
 _lib = None
@@ -82,6 +88,7 @@ def load() -> C.CDLL:
         "ccov_status_string": ([I], C.c_char_p),
         "ccov_last_error": ([P], C.c_char_p),
         "ccov_test_ozaki_gemm": ([I, I, I, I, P, P, P, P, I, I, I, P], I),
+        "ccov_test_ozaki_gemm_wait": ([I, I, I, I, P, P, P, P, I, I, I, P, C.c_longlong, C.c_ulonglong], I),
         "ccov_spd_inverse_blocks_noalloc": ([P, I64, I64, P, P], I),
         "ccov_batch_covariance": ([P, I, P, I], I),
         "ccov_batch_create": ([P, I, P, C.POINTER(C.c_void_p)], I),
@@ -141,7 +148,7 @@ class Context:
     """One scene on the device (ccov_ctx).  Method names follow the C ABI."""
 
     def __init__(self, cameras, points, obs, sigma=1.0, obs_cov=None, precision=CCOV_PREC_FP64,
-                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None, profile=False):
+                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None, profile=False, est_cameras=0):
         L = load()
         dev = _is_device(cameras)
         if not dev:
@@ -152,7 +159,7 @@ class Context:
         n, m = int(cameras.shape[0]), int(points.shape[0])
         t = int(obs.shape[0]) if not dev else int(obs.numel() // 24)
         opt = Options(precision, mixed_slices, nullspace_route,
-                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST, 1 if profile else 0)
+                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST, 1 if profile else 0, est_cameras)
         h = C.c_void_p()
         s = L.ccov_create(_ptr(cameras), n, _ptr(points), m, _ptr(obs), t, float(sigma),
                           _ptr(obs_cov), C.byref(opt), stream, C.byref(h))

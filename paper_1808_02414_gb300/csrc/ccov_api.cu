@@ -56,6 +56,7 @@ void free_all(Ctx& c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ccov::mixed_free(c);
+    ccov::est_free(c);
     for (auto& e : c.ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : c.prof_ev)
@@ -141,6 +142,10 @@ ccov_status check_device(Ctx& c, const char* where) {
             return fail(&c, CCOV_ERR_TIMEOUT, "%s: device wait gave up (site %d)", where, flag[1]);
         case ccov::DEV_SMEM_ALIGN:
             return fail(&c, CCOV_ERR_CUDA, "%s: shared memory window of the GEMM not 1024-byte aligned", where);
+        case ccov::DEV_RANGE:
+            return fail(&c, CCOV_ERR_NOT_CONVERGED,
+                        "%s: the mixed form's fixed-point range was exceeded (row %d): the scene is too "
+                        "ill-conditioned for it; use precision FP64", where, flag[1]);
         default:
             return fail(&c, CCOV_ERR_CUDA, "%s: device error code %d", where, flag[0]);
     }
@@ -218,6 +223,9 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown precision %d", c.opt.precision);
     if (c.opt.mixed_slices < 4 || c.opt.mixed_slices > 6)
         return fail(&c, CCOV_ERR_INVALID_ARG, "mixed_slices must be 4..6");
+    if (c.opt.est_cameras == 0) c.opt.est_cameras = ccov::kEstDefaultCams;
+    if (c.opt.est_cameras < 1 || c.opt.est_cameras > ccov::kEstMaxCams)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "est_cameras must be 1..%d", ccov::kEstMaxCams);
     if (c.opt.nullspace_route != CCOV_NULL_PAPER && c.opt.nullspace_route != CCOV_NULL_CLOSED)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown nullspace route");
     c.n = n; c.m = m; c.t = t; c.N = 9 * n;
@@ -401,6 +409,7 @@ ccov_status factor_inverse_fp64(Ctx& c) {
 
 ccov_status enq_covariance(Ctx& c, double* out, int out_memory) {
     ccov::launch_form_scaled(c);
+    if (c.est_on && c.opt.precision == CCOV_PREC_FP64) ccov::est_keep_fp64(c);
     CK(cudaGetLastError(), "ccov_covariance launch");
     rec(c, 2);
     CK(cudaMemsetAsync(c.d_Sig, 0, sizeof(double) * 81 * c.n, c.stream), "memset");
@@ -413,7 +422,9 @@ ccov_status enq_covariance(Ctx& c, double* out, int out_memory) {
         cudaError_t e = ccov::mixed_factor_inverse(c);
         if (e != cudaSuccess) return cuda_fail(&c, e, "mixed path");
     }
+    if (c.est_on) ccov::est_launch(c, ccov::mixed_inverse_factor(c));
     ccov::launch_extract(c);
+    if (c.est_on) ccov::est_launch_final(c);
     CK(cudaGetLastError(), "ccov_covariance launch");
     if (out) {
         cudaMemcpyKind k = out_memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -497,19 +508,32 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     if (!c.null_done) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_nullspace first");
     if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
+    c.est_on = est_rel_err != nullptr;
+    c.est_k = (int)(c.opt.est_cameras < c.n ? c.opt.est_cameras : c.n);
+    c.stats.est_cameras = 0;
+    if (c.est_on) CK(ccov::est_alloc(c, c.est_k), "alloc error-estimate workspace");
     rec(c, 0);
     ccov_status s = enq_covariance(c, out, out_memory);
     c.stage = 2;  // Z is consumed in place
-    if (s != CCOV_OK) return s;
+    if (s != CCOV_OK) { c.est_on = false; return s; }
     rec(c, 1);
     s = check_device(c, "ccov_covariance");
-    if (s != CCOV_OK) return s;
+    if (s != CCOV_OK) { c.est_on = false; return s; }
     covariance_stats(c);
-    if (est_rel_err) {
-        if (c.opt.precision == CCOV_PREC_FP64) {
-            for (int64_t i = 0; i < c.n; ++i) est_rel_err[i] = 0.0;
-        } else {
-            for (int64_t i = 0; i < c.n; ++i) est_rel_err[i] = -1.0;
+    if (c.est_on) {
+        c.est_on = false;
+        double est[3 * ccov::kEstMaxCams];
+        CK(cudaMemcpy(est, c.d_est_out, sizeof(double) * 3 * c.est_k, cudaMemcpyDeviceToHost), "copy estimate");
+        double worst = 0.0;
+        for (int j = 0; j < c.est_k; ++j) worst = est[3 * j] > worst ? est[3 * j] : worst;
+        for (int64_t i = 0; i < c.n; ++i) est_rel_err[i] = worst;
+        c.stats.est_cameras = c.est_k;
+        for (int j = 0; j < c.est_k; ++j) {
+            const int64_t cam = (int64_t)est[3 * j + 2];
+            est_rel_err[cam] = est[3 * j];
+            c.stats.est_index[j] = cam;
+            c.stats.est_rel[j] = est[3 * j];
+            c.stats.est_norm[j] = est[3 * j + 1];
         }
     }
     return CCOV_OK;
@@ -527,6 +551,7 @@ static ccov_status batch_check_args(ccov_ctx* const* ctxs, int k, double* const*
 }
 
 static ccov_status batch_enqueue(Ctx& c, double* out, int out_memory) {
+    c.est_on = false;
     rec(c, 0);
     ccov_status s = enq_information(c);
     if (s == CCOV_OK) s = enq_schur(c);

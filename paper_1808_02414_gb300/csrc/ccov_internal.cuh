@@ -12,6 +12,8 @@ namespace ccov {
 
 constexpr int kNB = 128;         // dense block size: panel width and K of every trailing update
 constexpr int kCamPrep = 24;     // doubles per prepared camera: R(9) t(3) f k1 k2 (3) J_l(9)
+constexpr int kEstMaxCams = 16;  // sampled cameras of the a-posteriori error estimate, at most
+constexpr int kEstDefaultCams = 4;
 
 // Device-side error codes written with atomicMax into ctx->d_flag[0].
 enum DevErr : int {
@@ -24,6 +26,7 @@ enum DevErr : int {
     DEV_TIMEOUT = 6,      // a bounded spin-wait gave up
     DEV_BAD_INDEX = 7,    // a sample index outside the training set (surrogate)
     DEV_SMEM_ALIGN = 8,   // dynamic shared memory window not 1024-byte aligned (GEMM)
+    DEV_RANGE = 9,        // a value left the range of the mixed path's fixed-point formats
 };
 
 struct MixedState;  // emulated-FP64 tensor-core path, k_mixed.cu
@@ -73,6 +76,17 @@ struct Ctx {
     bool mixed_bad_launch = false;  // a GEMM launch was refused (odd tile count)
     bool capturing = false;         // launches are being captured into a graph: no timing events
 
+    // a-posteriori error estimate (k_estimate.cu), allocated on first request
+    bool est_on = false;
+    int est_k = 0, est_cap = 0;
+    void* d_Zkeep = nullptr;        // Np x Np: copy of the scaled matrix that is factorised
+    void* d_estW = nullptr;         // Np x 9k each (double or double-single)
+    void* d_estY = nullptr;
+    void* d_estR = nullptr;
+    int* d_est_idx = nullptr;       // sampled cameras
+    double* d_est_dS = nullptr;     // k x 81 scaled error blocks
+    double* d_est_out = nullptr;    // k x 3: relative, scaled-relative, camera
+
     cudaEvent_t ev[8] = {};
     ccov_stats stats{};
     // profile = 1: event pairs around the dense trailing-update GEMMs
@@ -111,6 +125,14 @@ void surr_launch_features(Ctx& c, float* feat, double* scale);
 cudaError_t mixed_alloc(Ctx& c);
 void mixed_free(Ctx& c);
 cudaError_t mixed_factor_inverse(Ctx& c);
+const long long* mixed_inverse_factor(const Ctx& c);   // X = L^-1, Q42, after mixed_factor_inverse
+
+// ---- a-posteriori error estimate (k_estimate.cu) ----
+cudaError_t est_alloc(Ctx& c, int k);
+void est_free(Ctx& c);
+void est_keep_fp64(Ctx& c);                  // after the FP64 scaling: keep Z_s
+void est_launch(Ctx& c, const long long* Xq);  // after the inverse, before the extraction
+void est_launch_final(Ctx& c);               // after the extraction
 
 }  // namespace ccov
 

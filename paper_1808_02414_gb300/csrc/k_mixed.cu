@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "ccov_internal.cuh"
+#include "ds_arith.cuh"
 #include "tc_ptx.cuh"
 #include "../../include/ccov_testing.h"
 
@@ -68,6 +69,8 @@ struct MixedState {
     __nv_bfloat16 *digP2 = nullptr, *digQ2 = nullptr;
     int *expP2 = nullptr, *expQ2 = nullptr;
     CUtensorMap mapBP2, mapBQ2;
+    unsigned long long wait_ns = ptx::kWaitNs;  // limit of the GEMM's barrier waits
+    long long skip_fill = -1;        // test hook: a pipeline fill the GEMM producer leaves out
     cudaStream_t side = nullptr;     // triangular inverse, lowest priority
     cudaStream_t hi = nullptr;       // Cholesky (the critical path), highest priority
     std::vector<cudaEvent_t> ev;     // [0] fork, [1] inverse done, [2] Cholesky done, [3 + k] pair k final
@@ -214,6 +217,8 @@ struct GemmArgs {
     const int* expB;      // per row of B (nullptr = 0)
     int stages;
     int* flag;
+    unsigned long long wait_ns;  // limit of every barrier wait
+    long long skip_fill;         // test hook: the producer leaves out this pipeline fill (-1: none)
 };
 
 __device__ __forceinline__ long long shift_round(long long p, int sh) {
@@ -222,10 +227,11 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
     return (p + (1ll << (-sh - 1))) >> (-sh);
 }
 
-// Persistent warp-specialised kernel, launched in clusters of two CTAs that
-// work on the two halves (adjacent 64-column tiles) of one 128 x 128 block:
-// they need the same A tile, and each CTA loads half of its digit planes and
-// multicasts them to both.  Warp 0 lane 0: producer of the digit tiles.
+// Persistent warp-specialised kernel.  CTAs 2P and 2P + 1 work on the two
+// halves (adjacent 64-column tiles) of one 128 x 128 block at about the same
+// time, so the A tile that both read is fetched from DRAM once and served to
+// the second from L2; each CTA copies every operand it uses into its own
+// shared memory.  Warp 0 lane 0: producer of the digit tiles.
 // Warp 1: TMEM allocation; lane 0 issues tcgen05.mma.  Warps 2..17:
 // epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31 and one quarter of the
 // 64 columns.  The result tile leaves through shared memory with TMA, a
@@ -259,17 +265,17 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = g.N / kBN;
     const int64_t ntiles = tile_count(g.M / kBM, tiles_n, g.lower);
-    // tiles come in pairs (2P, 2P + 1) in one row of tiles; CTA `rank` of the
-    // cluster takes tile 2P + rank of every pair P of its cluster
-    const uint32_t rank = cluster_rank();
+    // tiles come in pairs (2P, 2P + 1) in one row of tiles; CTA 2c + rank
+    // takes tile 2P + rank of every pair P of CTA pair c (the grid is even)
+    const uint32_t rank = blockIdx.x & 1;
     const int64_t npairs = ntiles / 2;
     const int64_t pair0 = blockIdx.x >> 1, pair_step = gridDim.x >> 1;
-    constexpr uint16_t kBoth = 0x3;
+    const unsigned long long wlim = g.wait_ns;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < g.stages; ++i) {
             mbar_init(full + i, 1);
-            mbar_init(empty + i, 2);  // released by the MMAs of both CTAs
+            mbar_init(empty + i, 1);  // released by this CTA's MMAs
         }
         mbar_init(accf, 1);
         mbar_init(acce, kEpiWarps);
@@ -283,7 +289,6 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -292,22 +297,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            long long fill = 0;
             for (int64_t pr = pair0; pr < npairs && ok; pr += pair_step) {
                 const int64_t t = 2 * pr + rank;
                 int ti, tj;
                 tile_coords(t, tiles_n, g.lower, ti, tj);
-                for (int ks = 0; ks < K / kKS; ++ks) {
-                    if (!mbar_wait(empty + stage, phase ^ 1, g.flag, 1)) { ok = false; break; }
-                    unsigned char* st = tiles + stage * stage_bytes;
-                    mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
-                    // A: planes [pa0, pa1) of the tile, one copy sent to both CTAs
-                    const int pa0 = rank ? (S + 1) / 2 : 0, pa1 = rank ? S : (S + 1) / 2;
-                    bulk_load_mc(st + pa0 * kAPl, g.digA + blk_off(pa0, g.a_row0 + ti * kBM, ks * kKS, g.plane_rows, S),
-                                 (uint32_t)((pa1 - pa0) * kAPl), full + stage, kBoth);
-                    // B: this CTA's 64 rows of every plane, one tensor copy
-                    const int br = g.b_row0 + tj * kBN;
-                    tma_load_5d(st + S * kAPl, &mapB, full + stage, 0, 0, (br >> 6) & 1, 0,
-                                ks * (g.plane_rows >> 7) + (br >> 7));
+                for (int ks = 0; ks < K / kKS; ++ks, ++fill) {
+                    if (!mbar_wait(empty + stage, phase ^ 1, g.flag, 1, wlim)) { ok = false; break; }
+                    if (fill != g.skip_fill) {
+                        unsigned char* st = tiles + stage * stage_bytes;
+                        mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
+                        // A: all digit planes of the 128-row tile, adjacent in memory
+                        bulk_load(st, g.digA + blk_off(0, g.a_row0 + ti * kBM, ks * kKS, g.plane_rows, S),
+                                  (uint32_t)(S * kAPl), full + stage);
+                        // B: this CTA's 64 rows of every plane, one tensor copy
+                        const int br = g.b_row0 + tj * kBN;
+                        tma_load_5d(st + S * kAPl, &mapB, full + stage, 0, 0, (br >> 6) & 1, 0,
+                                    ks * (g.plane_rows >> 7) + (br >> 7));
+                    }
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
             }
@@ -319,10 +326,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             bool ok = true, issued = false;
 
             for (int64_t pr = pair0; pr < npairs && ok; pr += pair_step) {
-                if (!mbar_wait(acce, acc_phase ^ 1, g.flag, 2)) break;
+                if (!mbar_wait(acce, acc_phase ^ 1, g.flag, 2, wlim)) break;
                 tc_fence_after();
                 for (int ks = 0; ks < K / kKS; ++ks) {
-                    if (!mbar_wait(full + stage, phase, g.flag, 3)) { ok = false; break; }
+                    if (!mbar_wait(full + stage, phase, g.flag, 3, wlim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(tiles + stage * stage_bytes);
                     const uint32_t sb = sa + S * kAPl;
@@ -341,7 +348,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
                             issued = true;
                         }
                     }
-                    mma_commit_mc(empty + stage, kBoth);  // both producers write this stage
+                    mma_commit(empty + stage);  // the stage is free once these MMAs have read it
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
                 if (!ok) break;
@@ -351,7 +358,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             if (issued) {
                 // every issued MMA completes before TMEM is released
                 mma_commit(drain);
-                mbar_wait(drain, 0, g.flag, 4);
+                mbar_wait(drain, 0, g.flag, 4, wlim);
             }
         }
     } else {
@@ -368,7 +375,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             if (leader) bulk_wait_read0();  // the previous tile's copy-out has left shared memory
             epi_bar();
             // warp-uniform: the vote, the re-read and the arrival below are per warp
-            if (!__all_sync(0xffffffffu, mbar_wait(accf, acc_phase, g.flag, 5))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(accf, acc_phase, g.flag, 5, wlim))) break;
             tc_fence_after();
             // phase 1: drain the accumulators into exact int64 sums (registers),
             // then release TMEM so that the next tile's MMAs start at once;
@@ -447,10 +454,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
         }
         if (leader) bulk_wait0();
     }
+    // after a timeout: every copy this CTA issued was issued before the wait
+    // that gave up began (the producer only issues after a stage is freed),
+    // so it has landed long before the limit ran out
     tc_fence_before();
     __syncthreads();
-    __syncwarp();
-    cluster_sync();  // no multicast or remote arrival is still aimed at this CTA
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -527,7 +535,7 @@ __device__ __forceinline__ int tile16_khalf(int lane) { return (lane >> 3) & 1; 
 template <int K>
 __global__ void __launch_bounds__(256)
 slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
-                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
+                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
     constexpr int KS = K / 16;
     const int lane = threadIdx.x & 31;
     const int64_t wt = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -538,12 +546,18 @@ slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F
     const int T = 7 + 8 * (s - 1);
     const longlong2* p = reinterpret_cast<const longlong2*>(src + (int64_t)r * ld + k0);
     long long w[8];
+    bool out_of_range = false;
+    // entries of the scaled factor are bounded by 1 (2^F): beyond 2^(F+1)
+    // the value has left the fixed-point range (or wrapped)
+    const long long lim = 1ll << (F + 1);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const longlong2 v = p[j];
+        out_of_range |= v.x > lim || v.x < -lim || v.y > lim || v.y < -lim;
         w[2 * j] = round_shift(v.x, T - F);
         w[2 * j + 1] = round_shift(v.y, T - F);
     }
+    if (out_of_range) ptx::set_flag(flag, DEV_RANGE, r);
     split_store8(w, s, dst + blk_off(0, r, k0, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
 }
 
@@ -557,7 +571,7 @@ slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F
 template <int K>
 __global__ void __launch_bounds__(256)
 slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
-                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo) {
+                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
     extern __shared__ __align__(16) long long tile[];   // [K][33]
     __shared__ int cexp[32];
     const int c0 = blockIdx.x * 32;
@@ -585,6 +599,9 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
             const int e = mx == 0 ? 0 : (64 - __clzll((long long)mx)) - F;
             cexp[c] = e;
             if (c0 + c < ncols) expo[c0 + c] = e;
+            // an entry of X = L^-1 at 2^19 or beyond: two bits short of the
+            // int64 range of its fixed point (a larger one may have wrapped)
+            if (mx >= (1ull << 61)) ptx::set_flag(flag, DEV_RANGE, c0 + c);
         }
     }
     __syncthreads();
@@ -603,43 +620,6 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
     }
 }
 
-// Double-single arithmetic: a value is an unevaluated sum hi + lo of two
-// floats (about 44 significant bits; Dekker 1971, with the products split
-// by FMA).  GB300 issues FP32 about eighty times faster than FP64 per SM,
-// and the digits that the tensor-core products keep of L and L^-1 hold 39
-// bits, so the one-CTA factorisation of a diagonal block runs in this form.
-// Explicit _rn intrinsics keep the compiler from contracting the
-// error-free transformations.
-struct dsf {
-    float h, l;
-};
-
-// acc + a * b
-__device__ __forceinline__ dsf ds_fma(dsf acc, dsf a, dsf b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    const float s = __fadd_rn(acc.h, p);
-    const float v = __fsub_rn(s, acc.h);
-    float t = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, v)), __fsub_rn(p, v));
-    t = __fadd_rn(t, __fadd_rn(acc.l, e));
-    const float h = __fadd_rn(s, t);
-    return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-
-__device__ __forceinline__ dsf ds_neg(dsf a) { return {-a.h, -a.l}; }
-
-// a + b (two-sum of the high parts, low parts added, then renormalised)
-__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
-    const float s = __fadd_rn(a.h, b.h);
-    const float v = __fsub_rn(s, a.h);
-    float t = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
-    t = __fadd_rn(t, __fadd_rn(a.l, b.l));
-    const float h = __fadd_rn(s, t);
-    return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-
 // Row and column of entry t of a lower triangle stored row by row.
 __device__ __forceinline__ void tri_index(int t, int& i, int& l) {
     i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -648,15 +628,7 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& l) {
     l = t - i * (i + 1) / 2;
 }
 
-// Q60 fixed point <-> double-single, with integer conversions only: v =
-// f + r exactly with f = v rounded to a float (an integer value) and r the
-// remainder (|r| <= 2^39); the power-of-two scalings are exact in float.
-__device__ __forceinline__ dsf ds_from_fixed(long long v, float scale) {
-    const float f = __ll2float_rn(v);
-    const long long r = v - __float2ll_rz(f);
-    return {__fmul_rn(f, scale), __fmul_rn(__ll2float_rn(r), scale)};
-}
-
+// Q60 fixed point <-> double-single (see ds_from_fixed).
 __device__ __forceinline__ dsf ds_from_q60(long long v) {
     return ds_from_fixed(v, 8.673617379884035e-19f);  // 2^-60
 }
@@ -666,7 +638,6 @@ __device__ __forceinline__ long long ds_to_q60(dsf a) {
     return __float2ll_rn(__fmul_rn(a.h, kU)) + __float2ll_rn(__fmul_rn(a.l, kU));
 }
 
-__device__ __forceinline__ dsf ds_mul(dsf a, dsf b) { return ds_fma({0.f, 0.f}, a, b); }
 
 // sqrt(d), 1 / sqrt(d) and 1 / d: one Newton step on the float estimate of
 // 1 / sqrt(d) doubles its 22 correct bits.
@@ -680,26 +651,6 @@ __device__ __forceinline__ void ds_sqrt_inv(dsf d, dsf& l, dsf& inv, dsf& inv2) 
 }
 
 
-// A double as an unevaluated sum of two floats without FP64 arithmetic:
-// the high float keeps the top 24 significand bits (truncated), the low one
-// the other 29 bits (rounded to 24), so hi + lo equals z to 2^-48 relative.
-// Below 2^-74 only the high float is kept and below 2^-126 the value becomes
-// 0: against entries of Z_s of order 1 such terms are far below the 39-bit
-// digits taken from it.
-__device__ __forceinline__ dsf ds_from_double(double z) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(z);
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const int E = (int)((b >> 52) & 0x7FF) - 1023;
-    if (E < -126) return {0.f, 0.f};
-    if (E > 127) return {__uint_as_float(sign | 0x7F800000u), 0.f};   // beyond float range (or not finite)
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;                // 52 fraction bits
-    const float hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29));
-    const int es = E - 52 + 127;                                         // exponent field of 2^(E - 52)
-    float lo = 0.f;
-    if (es >= 1) lo = __fmul_rn(__uint2float_rn((unsigned)(m & 0x1FFFFFFFu)), __uint_as_float((unsigned)es << 23));
-    return {hi, sign ? -lo : lo};
-}
-
 // Lower triangle of Z_s = D (Z + F G^T) D written as Q60 int64 in place
 // (padded rows/columns: identity), in double-single arithmetic (Z_s is split
 // into digits of 39 bits afterwards).  A block covers 32 x 32 entries, a
@@ -708,7 +659,8 @@ __device__ __forceinline__ dsf ds_from_double(double z) {
 // into shared memory.
 __global__ void __launch_bounds__(256)
 zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
-                const double* __restrict__ G, const double* __restrict__ D) {
+                const double* __restrict__ G, const double* __restrict__ D, long long* __restrict__ Zkeep,
+                int* flag) {
     const int64_t bi = blockIdx.y, bj = blockIdx.x;
     if (bj > bi) return;
     __shared__ dsf Fs[32][7], Gs[32][7], Dr[32], Dc[32];
@@ -741,13 +693,22 @@ zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __r
         if (j > i) break;
         double* z = Z + i * Np + j;
         long long* q = reinterpret_cast<long long*>(z);
-        if (!row_in || j >= N) { *q = (i == j) ? (1ll << kFL) : 0; continue; }
+        if (!row_in || j >= N) {
+            const long long e = (i == j) ? (1ll << kFL) : 0;
+            *q = e;
+            if (Zkeep) Zkeep[i * Np + j] = e;
+            continue;
+        }
         const int jc = (int)(j - bj * 32);
         dsf v = ds_from_double(*z);
 #pragma unroll
         for (int k = 0; k < 7; ++k) v = ds_fma(v, Fs[y][k], Gs[jc][k]);
         v = ds_mul(ds_mul(Dr[y], v), Dc[jc]);
-        *q = __float2ll_rn(v.h) + __float2ll_rn(v.l);
+        // |Z_s| <= 1 for a positive definite scaled matrix (2^60 in Q60)
+        if (!(fabsf(v.h) <= 2.3058430e18f)) ptx::set_flag(flag, DEV_RANGE, (int)i);   // 2^61
+        const long long e = __float2ll_rn(v.h) + __float2ll_rn(v.l);
+        *q = e;
+        if (Zkeep) Zkeep[i * Np + j] = e;
     }
 }
 
@@ -958,6 +919,8 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
         if (lane == 0) {
             rexp[r] = ex;
             expL[k0 + r] = ex;
+            // X = L^-1 is held in Q42 (|x| < 2^21); stop two bits short
+            if (ex > 19) ptx::set_flag(flag, DEV_RANGE, (int)(k0 + r));
         }
     }
     __syncthreads();
@@ -1103,6 +1066,7 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     g.M = M; g.N = N; g.plane_rows = (int)c.Np; g.a_row0 = a_row0; g.b_row0 = b_row0;
     g.c_x0 = c_x0; g.c_y0 = c_y0; g.lower = lower; g.sub = sub; g.shift0 = Fc - 14;
     g.expA = expA; g.expB = expB; g.stages = pick_stages(st.s); g.flag = c.d_flag;
+    g.wait_ns = st.wait_ns; g.skip_fill = st.skip_fill;
     g.digA = buf_ptr(st, ba);
     g.digB = buf_ptr(st, bb);
     const int64_t ntiles = tile_count(M / kBM, N / kBN, lower);  // even: pairs of tiles
@@ -1122,13 +1086,8 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = c.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
     const CUtensorMap& mapB = bb == BUF_P ? st.mapBP : (bb == BUF_Q ? st.mapBQ : st.mapBL);
 #define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_>, mapC, mapB, g)
     if (K == 256) {
@@ -1157,9 +1116,11 @@ void slice_rows(Ctx& c, int K, int rows, const long long* src, Buf b) {
     const int grid = (int)(((int64_t)rows / 16 * (K / 16) * 32 + 255) / 256);
     if (rows % 16) { c.mixed_bad_launch = true; return; }
     if (K == 256)
-        slice_rows_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex);
+        slice_rows_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex,
+                                                           c.d_flag);
     else
-        slice_rows_kernel<128><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex);
+        slice_rows_kernel<128><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex,
+                                                           c.d_flag);
     c.launches++;
 }
 
@@ -1170,9 +1131,11 @@ void slice_cols(Ctx& c, int K, int ncols, const long long* src, Buf b) {
     const int grid = (ncols + 31) / 32;
     const size_t smem = (size_t)K * 33 * 8;
     if (K == 256)
-        slice_cols_kernel<256><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex);
+        slice_cols_kernel<256><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex,
+                                                              c.d_flag);
     else
-        slice_cols_kernel<128><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex);
+        slice_cols_kernel<128><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex,
+                                                              c.d_flag);
     c.launches++;
 }
 
@@ -1241,6 +1204,8 @@ cudaError_t mixed_alloc(Ctx& c) {
     return cudaSuccess;
 }
 
+const long long* mixed_inverse_factor(const Ctx& c) { return c.mixed ? c.mixed->R : nullptr; }
+
 void mixed_free(Ctx& c) {
     if (!c.mixed) return;
     MixedState& st = *c.mixed;
@@ -1272,8 +1237,9 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     c.stream = st.hi;
     {
         int64_t nt = (Np + 31) / 32;
-        zscale_q_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(8, 32), 0, c.stream>>>(c.N, Np, c.d_Z, c.d_F,
-                                                                                      c.d_G, c.d_D);
+        zscale_q_kernel<<<dim3((unsigned)nt, (unsigned)nt), dim3(8, 32), 0, c.stream>>>(
+            c.N, Np, c.d_Z, c.d_F, c.d_G, c.d_D, c.est_on ? static_cast<long long*>(c.d_Zkeep) : nullptr,
+            c.d_flag);
         c.launches++;
     }
     auto Zat = [&](int64_t row, int64_t col) { return Zq + row * Np + col; };
@@ -1361,14 +1327,14 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
 
 }  // namespace ccov
 
-// Test hook (include/ccov_testing.h): one call of the digit-split tensor-core
-// GEMM on caller data, with its own temporary workspace.
-extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N, const uint16_t* digA,
-                                                    const int* expA, const uint16_t* digB, const int* expB,
-                                                    int Fc, int sub, int lower, long long* C) {
+// Test hooks (include/ccov_testing.h): one call of the digit-split
+// tensor-core GEMM on caller data, with its own temporary workspace.
+static ccov_status test_gemm(int s, int K, int M, int N, const uint16_t* digA, const int* expA,
+                             const uint16_t* digB, const int* expB, int Fc, int sub, int lower, long long* C,
+                             long long skip_fill, unsigned long long wait_ns) {
     using namespace ccov;
     if (s < 4 || s > 6 || (K != 128 && K != 256) || M <= 0 || N <= 0 || M % kBM || N % (2 * kBN) || !digA ||
-        !digB || !C)
+        !digB || !C || wait_ns < 100000ull || wait_ns > 10000000000ull)
         return CCOV_ERR_INVALID_ARG;
     if (lower && N != M) return CCOV_ERR_INVALID_ARG;
     Ctx c;
@@ -1384,6 +1350,8 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
     do {
         if (mixed_alloc(c) != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         MixedState& ms = *c.mixed;
+        ms.wait_ns = wait_ns;
+        ms.skip_fill = skip_fill;
         if (cudaMalloc(&c.d_flag, 2 * sizeof(int)) != cudaSuccess) { st = CCOV_ERR_OOM; break; }
         cudaMemset(c.d_flag, 0, 2 * sizeof(int));
         {
@@ -1414,6 +1382,7 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
         int flag[2];
         cudaMemcpy(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost);
         if (flag[0] == DEV_TIMEOUT) { st = CCOV_ERR_TIMEOUT; break; }
+        if (flag[0] != DEV_OK) { st = CCOV_ERR_CUDA; break; }
         cudaMemcpy(C, dC, (size_t)M * N * 8, cudaMemcpyDeviceToHost);
     } while (0);
     if (dC) cudaFree(dC);
@@ -1423,4 +1392,17 @@ extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N,
     mixed_free(c);
     cudaStreamDestroy(c.stream);
     return st;
+}
+
+extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm(int s, int K, int M, int N, const uint16_t* digA,
+                                                    const int* expA, const uint16_t* digB, const int* expB,
+                                                    int Fc, int sub, int lower, long long* C) {
+    return test_gemm(s, K, M, N, digA, expA, digB, expB, Fc, sub, lower, C, -1, ccov::ptx::kWaitNs);
+}
+
+extern "C" CCOV_API ccov_status ccov_test_ozaki_gemm_wait(int s, int K, int M, int N, const uint16_t* digA,
+                                                         const int* expA, const uint16_t* digB, const int* expB,
+                                                         int Fc, int sub, int lower, long long* C,
+                                                         long long skip_fill, unsigned long long wait_ns) {
+    return test_gemm(s, K, M, N, digA, expA, digB, expB, Fc, sub, lower, C, skip_fill, wait_ns);
 }

@@ -13,8 +13,11 @@
 // array's device address with cudaGetSymbolAddress and sets the kernels'
 // shared-memory attributes; that first call should come before any stream
 // capture.
-// Every call shares the array and starts by clearing what must start at zero;
+// Every call shares the array and starts by clearing what must start at zero
+// (so a call that failed half-way leaves nothing that the next call reads);
 // calls that overlap on the GPU (other streams, other threads) race on it.
+// Every call waits for its stream to finish before it returns, so a call on a
+// stream that is being captured is refused.
 #include <mutex>
 
 #include "ccov_internal.cuh"
@@ -100,6 +103,9 @@ extern "C" CCOV_API ccov_status ccov_spd_inverse_blocks_noalloc(const double* A,
     using namespace ccov;
     if (!A || !blocks || N <= 0 || N % 9 != 0 || lda < N) return CCOV_ERR_INVALID_ARG;
     if (N > kNAMaxN) return CCOV_ERR_INVALID_ARG;  // beyond the fixed workspace
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return CCOV_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return CCOV_ERR_INVALID_ARG;  // the call synchronises
     double* base = nullptr;
     ccov_status st = scratch_for_current_device(&base);
     if (st != CCOV_OK) return st;
@@ -150,9 +156,10 @@ extern "C" CCOV_API ccov_status ccov_spd_inverse_blocks_noalloc(const double* A,
     }
     na_unscale_kernel<<<(int)((c.n * 81 + 255) / 256), 256, 0, c.stream>>>(c.n, c.d_D, c.d_Sig, blocks);
     if (cudaGetLastError() != cudaSuccess) return CCOV_ERR_CUDA;
-    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return CCOV_ERR_CUDA;
     int flag[2] = {0, 0};
-    if (cudaMemcpy(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess) return CCOV_ERR_CUDA;
+    if (cudaMemcpyAsync(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
+        return CCOV_ERR_CUDA;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return CCOV_ERR_CUDA;
     if (flag[0] == DEV_NOT_SPD) return CCOV_ERR_DEGENERATE;
     if (flag[0] != DEV_OK) return CCOV_ERR_CUDA;
     return CCOV_OK;

@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
-           "subscene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
+           "subscene", "weak_camera_scene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
            "training_scene_specs", "training_scene"]
 
 
@@ -242,6 +242,32 @@ def subscene(sc: Scene, cam_ids: np.ndarray, min_track=2) -> Scene:
     return Scene(sc.cams[cam_ids].copy(), sc.pts[pts_used].copy(), ci[order], pi[order],
                  sc.obs_u[keep][order], sc.sigma, cov,
                  {"kind": "sub", "parent": sc.meta, "n": int(cam_ids.size)})
+
+
+def weak_camera_scene(n=30, m=3000, keep=6, spread=1e-4, seed=8) -> Scene:
+    """A shell scene in which camera 0 keeps only `keep` of its observations,
+    of points moved onto a short line segment (plus `spread` of noise): its
+    parameters are nearly undetermined, which makes the reduced camera matrix
+    badly conditioned (condition number of the scaled matrix about 2e8 at
+    spread 1e-4, against 2e4 for the plain shell).  Points left with fewer
+    than two observations are removed."""
+    sc = shell_scene(n=n, m=m, seed=seed)
+    rng = np.random.default_rng(seed)
+    mine = np.nonzero(sc.obs_cam == 0)[0]
+    pts0 = sc.obs_pt[mine]
+    cnt = np.bincount(sc.obs_pt, minlength=sc.m)
+    sel = pts0[cnt[pts0] >= 3][:keep]
+    keepmask = ~(np.isin(sc.obs_pt, np.setdiff1d(pts0, sel)) & (sc.obs_cam == 0))
+    pts = sc.pts.copy()
+    s = np.linspace(-0.4, 0.4, sel.size)
+    pts[sel] = np.stack([s, 0.1 * s, np.full(sel.size, 0.05)], 1) + spread * rng.standard_normal((sel.size, 3))
+    oc, op, ou = sc.obs_cam[keepmask], sc.obs_pt[keepmask], sc.obs_u[keepmask]
+    live = np.bincount(op, minlength=sc.m) >= 2
+    k2 = live[op]
+    newid = np.cumsum(live) - 1
+    return Scene(cams=sc.cams, pts=pts[live], obs_cam=oc[k2].astype(np.int32),
+                 obs_pt=newid[op[k2]].astype(np.int32), obs_u=ou[k2], sigma=sc.sigma,
+                 meta={"kind": "weak_camera", "spread": spread})
 
 
 def batch_scenes(k=256, n_lo=10, n_hi=300, pts_per_cam=100, p_geom=0.2, seed=4):

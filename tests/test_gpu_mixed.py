@@ -6,6 +6,7 @@ Frobenius bar per camera block, and against the FP64 GPU path."""
 import numpy as np
 import pytest
 
+from _checks import assert_blocks_close
 from oracle import covariance, metrics
 from paper_1808_02414_gb300 import ccov, synth
 
@@ -127,14 +128,14 @@ def test_mixed_covariance_vs_oracle(case):
         sc = synth.shell_scene(n=300, m=30000, seed=6)
     want = covariance.camera_covariance(sc)
     got = ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED)
-    assert metrics.rel_fro(got, want).max() < MIXED_TOL
+    assert_blocks_close(got, want, MIXED_TOL)
 
 
 def test_mixed_six_digits_tighter():
     sc = synth.shell_scene(n=100, m=10000, seed=5)
     want = ccov.camera_covariances(sc)
     got = ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED, mixed_slices=6)
-    assert metrics.rel_fro(got, want).max() < 1e-8
+    assert_blocks_close(got, want, 1e-8)
 
 
 def test_mixed_repeatable_on_a_user_stream_and_after_reload():
@@ -154,11 +155,41 @@ def test_mixed_repeatable_on_a_user_stream_and_after_reload():
         c = ctx.run()
         ctx.ccov_load(sc.cams, sc.pts, sc.obs_records())
         d = ctx.run()
-    assert metrics.rel_fro(a, want).max() < 1e-6
+    assert_blocks_close(a, want, 1e-6)
     # the FP64 Schur scatter adds in varying order: Z may differ in its last
     # bits, which the digit rounding turns into differences up to about 2e-9
     assert metrics.rel_fro(a, b).max() < 1e-8
     assert metrics.rel_fro(a, d).max() < 1e-8
     scaled = covariance.camera_covariance(synth.Scene(cams=moved, pts=sc.pts * 1.5, obs_cam=sc.obs_cam,
                                                       obs_pt=sc.obs_pt, obs_u=sc.obs_u, sigma=sc.sigma))
-    assert metrics.rel_fro(c, scaled).max() < 1e-6
+    assert_blocks_close(c, scaled, 1e-6)
+
+
+def test_gemm_wait_limit_runs_out_and_the_library_stays_usable():
+    """The producer of every CTA leaves out one pipeline fill, so the MMA
+    issuer waits for operands that never arrive: with a 2 ms limit the wait
+    gives up, the kernel leaves every loop, drains its MMAs, frees TMEM and
+    the call returns TIMEOUT.  The next calls (the same GEMM without the gap,
+    and a whole covariance) are exact again."""
+    s, K, M, N = 5, 128, 256, 256
+    rng = np.random.default_rng(31)
+    dA = rng.integers(-128, 129, size=(s, M, K)).astype(np.int64)
+    dB = rng.integers(-128, 129, size=(s, N, K)).astype(np.int64)
+    C0 = rng.integers(-(1 << 50), 1 << 50, size=(M, N)).astype(np.int64)
+    ba, bb = _bf16_bits(dA), _bf16_bits(dB)
+    L = ccov.load()
+    for skip in (0, 3, 7):      # the first fill, a middle one, the last of the tile
+        Cg = C0.copy()
+        st = L.ccov_test_ozaki_gemm_wait(s, K, M, N, ba.ctypes.data, None, bb.ctypes.data, None, 60, 1, 0,
+                                         Cg.ctypes.data, skip, 2_000_000)
+        assert st == ccov.CCOV_ERR_TIMEOUT
+        assert np.array_equal(Cg, C0)           # nothing copied back on failure
+    Cg = C0.copy()
+    st = L.ccov_test_ozaki_gemm_wait(s, K, M, N, ba.ctypes.data, None, bb.ctypes.data, None, 60, 1, 0,
+                                     Cg.ctypes.data, -1, 2_000_000)
+    assert st == ccov.CCOV_OK
+    want = _expected(dA, np.zeros(M, np.int64), dB, np.zeros(N, np.int64), s, 60, 1, 0, C0)
+    assert np.array_equal(Cg, want)
+    sc = synth.workload("ring20")
+    assert_blocks_close(ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED),
+                        covariance.camera_covariance(sc), MIXED_TOL)

@@ -7,6 +7,7 @@ Frobenius error per block for the FP64 path."""
 import numpy as np
 import pytest
 
+from _checks import assert_blocks_close
 from oracle import camera, covariance, information, metrics, nullspace
 from paper_1808_02414_gb300 import ccov, synth
 
@@ -65,8 +66,7 @@ def test_schur_blocks(n, m):
 @pytest.mark.parametrize("name,sc,gt", golden_entries(), ids=lambda x: x if isinstance(x, str) else "")
 def test_covariance_vs_extended_precision_ground_truth(name, sc, gt):
     got = ccov.camera_covariances(sc)
-    assert metrics.rel_fro(got, gt).max() < FP64_TOL
-    assert metrics.norm_err(got, gt).max() < 1e-8
+    assert_blocks_close(got, gt, FP64_TOL)
 
 
 @pytest.mark.parametrize("case", ["ring20", "aniso", "shell100", "shell300"])
@@ -81,7 +81,7 @@ def test_covariance_vs_oracle(case):
         sc = synth.shell_scene(n=300, m=30000, seed=6)   # N = 2700: 22 tiles, ragged tail
     want = covariance.camera_covariance(sc)
     got = ccov.camera_covariances(sc)
-    assert metrics.rel_fro(got, want).max() < FP64_TOL
+    assert_blocks_close(got, want, FP64_TOL)
     np.testing.assert_allclose(got, np.transpose(got, (0, 2, 1)), rtol=0, atol=1e-12 * np.abs(got).max())
 
 
@@ -89,7 +89,7 @@ def test_paper_route_and_closed_form_nullspace_agree_on_covariance():
     sc = synth.shell_scene(n=60, m=4000, seed=9)
     a = ccov.camera_covariances(sc, nullspace_route=ccov.CCOV_NULL_PAPER)
     b = ccov.camera_covariances(sc, nullspace_route=ccov.CCOV_NULL_CLOSED)
-    assert metrics.rel_fro(a, b).max() < FP64_TOL
+    assert_blocks_close(a, b, FP64_TOL)
 
 
 def test_repeatable_and_reloadable():

@@ -8,6 +8,7 @@ reuses the array that the first one left behind)."""
 import numpy as np
 import pytest
 
+from _checks import assert_blocks_close
 from oracle import metrics
 from paper_1808_02414_gb300 import ccov, synth
 
@@ -39,7 +40,7 @@ def test_noalloc_blocks_match_covariance_path_twice():
         st = fn(dA.data_ptr(), N, N, out.data_ptr(), None)
         assert st == ccov.CCOV_OK
         got = out.cpu().numpy()
-        assert metrics.rel_fro(got, want).max() < FP64_TOL
+        assert_blocks_close(got, want, FP64_TOL)
 
 
 def test_noalloc_rejects_sizes_beyond_its_workspace():
@@ -47,3 +48,45 @@ def test_noalloc_rejects_sizes_beyond_its_workspace():
     # checked before any device work: the pointers are never touched
     assert fn(8, 585, 585, 8, None) == ccov.CCOV_ERR_INVALID_ARG
     assert fn(8, 20, 20, 8, None) == ccov.CCOV_ERR_INVALID_ARG   # not a multiple of 9
+
+
+def test_noalloc_at_its_size_limit_with_a_leading_dimension_beyond_n():
+    """N = 576 (the maximum: five 128-row blocks after padding) read from a
+    larger buffer (lda > N), against numpy's inverse, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    N, lda = 576, 600
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((N, N))
+    A = B @ B.T / N + np.diag(rng.uniform(0.5, 2.0, N))   # SPD, condition number about 10
+    buf = np.full((N, lda), np.nan)                        # the columns beyond N are never read
+    buf[:, :N] = A
+    want = np.linalg.inv(A)
+    want = np.stack([want[9 * i:9 * i + 9, 9 * i:9 * i + 9] for i in range(N // 9)])
+    dA = torch.from_numpy(buf).cuda()
+    out = torch.empty((N // 9, 9, 9), dtype=torch.float64, device="cuda")
+    fn = ccov.load().ccov_spd_inverse_blocks_noalloc
+    for _ in range(2):
+        out.fill_(np.nan)
+        torch.cuda.synchronize()
+        assert fn(dA.data_ptr(), lda, N, out.data_ptr(), None) == ccov.CCOV_OK
+        assert_blocks_close(out.cpu().numpy(), want, FP64_TOL)
+
+
+def test_noalloc_refuses_a_stream_under_capture():
+    torch = pytest.importorskip("torch")
+    N = 18
+    A = torch.eye(N, dtype=torch.float64, device="cuda")
+    out = torch.empty((N // 9, 9, 9), dtype=torch.float64, device="cuda")
+    fn = ccov.load().ccov_spd_inverse_blocks_noalloc
+    assert fn(A.data_ptr(), N, N, out.data_ptr(), None) == ccov.CCOV_OK   # set-up outside capture
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = []
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        status.append(fn(A.data_ptr(), N, N, out.data_ptr(), s.cuda_stream))
+        g.capture_end()
+    assert status == [ccov.CCOV_ERR_INVALID_ARG]
+    torch.cuda.synchronize()
+    assert fn(A.data_ptr(), N, N, out.data_ptr(), None) == ccov.CCOV_OK
+    np.testing.assert_allclose(out.cpu().numpy(), np.tile(np.eye(9), (N // 9, 1, 1)), rtol=0, atol=1e-14)
