@@ -1,5 +1,6 @@
 // The C ABI of include/ccov.h: host-side validation, index construction,
 // device memory and the order of the kernel launches of steps (a)-(d).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -52,7 +53,8 @@ cudaError_t dalloc(Ctx& c, T** p, size_t count) {
 void free_all(Ctx& c) {
     void* ptrs[] = {c.d_cams, c.d_pts, c.d_obs, c.d_obscov, c.d_pt_ptr, c.d_cam_ptr, c.d_cam_perm,
                     c.d_camprep, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.d_Gp, c.d_W7, c.d_HP, c.d_R,
-                    c.d_P, c.d_Linv, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag};
+                    c.d_P, c.d_Linv, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag,
+                    c.d_V, c.d_pair_desc, c.d_pair_ent, c.d_w7part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ccov::mixed_free(c);
@@ -118,6 +120,53 @@ ccov_status build_index(Ctx& c, const double* cams, const double* pts, const cco
     std::vector<int> fill(cam_ptr.begin(), cam_ptr.end() - 1);
     for (int64_t o = 0; o < t; ++o) cam_perm[fill[obs[o].cam]++] = (int)o;
     return CCOV_OK;
+}
+
+// The blocks Z_ik (i >= k) that receive Schur terms and, per block, the
+// observation pairs of the points that cameras i and k share (Eq.
+// schur-complement-inversion: Z_ik = [i = k] U_i - sum_j W_ij A_j^-1 W_kj^T).
+// The entries are ordered by block (row i, then column k; two stable
+// counting sorts) and within a block by point, so the device sums every block
+// in a fixed order.  Depends on S only (ccov_load keeps it).
+void build_pairs(const ccov_obs* obs, int64_t n, int64_t m, const std::vector<int>& pt_ptr,
+                 std::vector<int4>& desc, std::vector<int2>& ent) {
+    int64_t total = 0;
+    for (int64_t j = 0; j < m; ++j) {
+        const int64_t L = pt_ptr[j + 1] - pt_ptr[j];
+        total += L * (L + 1) / 2;
+    }
+    std::vector<int> row(total), col(total);
+    std::vector<int2> raw(total);
+    int64_t e = 0;
+    for (int64_t j = 0; j < m; ++j)
+        for (int a = pt_ptr[j]; a < pt_ptr[j + 1]; ++a)
+            for (int b = a; b < pt_ptr[j + 1]; ++b) {
+                const int ca = obs[a].cam, cb = obs[b].cam;
+                const bool first = ca >= cb;
+                row[e] = first ? ca : cb;
+                col[e] = first ? cb : ca;
+                raw[e] = make_int2(first ? a : b, first ? b : a);
+                ++e;
+            }
+    // stable counting sort by column, then by row: (row, col, point) order
+    std::vector<int64_t> cnt(n + 1);
+    std::vector<int64_t> by_col(total), order(total);
+    for (int64_t q = 0; q < total; ++q) cnt[col[q] + 1]++;
+    for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    for (int64_t q = 0; q < total; ++q) by_col[cnt[col[q]]++] = q;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t q = 0; q < total; ++q) cnt[row[q] + 1]++;
+    for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    for (int64_t q : by_col) order[cnt[row[q]]++] = q;
+    ent.resize(total);
+    desc.clear();
+    for (int64_t q = 0; q < total; ++q) {
+        const int64_t src = order[q];
+        ent[q] = raw[src];
+        if (q == 0 || row[src] != row[order[q - 1]] || col[src] != col[order[q - 1]])
+            desc.push_back(make_int4(row[src], col[src], (int)q, 0));
+        desc.back().w++;
+    }
 }
 
 ccov_status check_device(Ctx& c, const char* where) {
@@ -257,6 +306,13 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     std::vector<int> pt_ptr, cam_ptr, cam_perm;
     ccov_status s = build_index(c, vc, vp, vo, vcov, pt_ptr, cam_ptr, cam_perm);
     if (s != CCOV_OK) return s;
+    std::vector<int4> pair_desc;
+    std::vector<int2> pair_ent;
+    build_pairs(vo, n, m, pt_ptr, pair_desc, pair_ent);
+    if ((int64_t)pair_ent.size() >= ((int64_t)1 << 31))
+        return fail(&c, CCOV_ERR_INVALID_ARG, "too many camera pairs per point (%lld)", (long long)pair_ent.size());
+    c.npairs = (int64_t)pair_desc.size();
+    c.nent = (int64_t)pair_ent.size();
 
     if (stream) {
         c.stream = static_cast<cudaStream_t>(stream);
@@ -279,6 +335,10 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     CK(dalloc(c, &c.d_Ainv, 6 * m), "alloc");
     CK(dalloc(c, &c.d_U, 45 * n), "alloc");
     CK(dalloc(c, &c.d_Z, Np * Np), "alloc Z");
+    CK(dalloc(c, &c.d_V, 27 * t), "alloc");
+    CK(dalloc(c, &c.d_pair_desc, c.npairs), "alloc");
+    CK(dalloc(c, &c.d_pair_ent, c.nent), "alloc");
+    CK(dalloc(c, &c.d_w7part, 56 * 2048), "alloc");
     CK(dalloc(c, &c.d_Gp, 7 * c.N), "alloc");
     CK(dalloc(c, &c.d_W7, 128), "alloc");
     CK(dalloc(c, &c.d_HP, 63 * n), "alloc");
@@ -302,6 +362,10 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     CK(cudaMemcpyAsync(c.d_pt_ptr, pt_ptr.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c.stream), "copy");
     CK(cudaMemcpyAsync(c.d_cam_ptr, cam_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c.stream), "copy");
     CK(cudaMemcpyAsync(c.d_cam_perm, cam_perm.data(), sizeof(int) * t, cudaMemcpyHostToDevice, c.stream), "copy");
+    CK(cudaMemcpyAsync(c.d_pair_desc, pair_desc.data(), sizeof(int4) * c.npairs, cudaMemcpyHostToDevice, c.stream),
+       "copy");
+    CK(cudaMemcpyAsync(c.d_pair_ent, pair_ent.data(), sizeof(int2) * c.nent, cudaMemcpyHostToDevice, c.stream),
+       "copy");
     CK(cudaStreamSynchronize(c.stream), "create");
     c.stage = 1;
     return CCOV_OK;

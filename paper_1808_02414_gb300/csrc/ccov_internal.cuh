@@ -56,6 +56,11 @@ struct Ctx {
     double* d_Ainv = nullptr;     // m x 6 (xx xy xz yy yz zz)
     double* d_U = nullptr;        // n x 45 (lower triangle, row by row)
     // step (b), (c)
+    double* d_V = nullptr;        // t x 27: W A^-1 per observation
+    int4* d_pair_desc = nullptr;  // blocks Z_ik with shared points: (i, k, first entry, entries)
+    int2* d_pair_ent = nullptr;   // per block, the observation pairs (o_i, o_k) in point order
+    int64_t npairs = 0, nent = 0;
+    double* d_w7part = nullptr;   // fixed-order partial sums of W7 and H_X^T H_X
     double* d_Z = nullptr;        // Np x Np row-major, lower triangle
     double* d_Gp = nullptr;       // N x 7: -W A^-1 H_X
     double* d_W7 = nullptr;       // 7 x 7

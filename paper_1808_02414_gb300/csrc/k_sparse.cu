@@ -230,17 +230,11 @@ cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restric
 
 // ---------------------------------------------------------------------------
 // Step (b): Z = blockdiag(U) - sum_j sum_{a,b in track j} V_a W_b^T with
-// V_a = W_a A_j^-1; W7 = sum_j H_Xj^T A_j^-1 H_Xj.  Warp per point; a track is
-// cut into chunks of 32 observations and every pair of chunks is handled with
-// V of one chunk and W of the other staged in shared memory.  Each (pair,
-// row, column) item of a 9x9 block is one FP64 atomic add into Z (lower
-// triangle: block row = larger camera index).
-struct SchurSmem {
-    double V[32][27];
-    double Wb[32][27];
-    int camA[32];
-    int camB[32];
-};
+// V_a = W_a A_j^-1 (Eq. schur-complement-inversion), and
+// W7 = sum_j H_Xj^T A_j^-1 H_Xj.  Deterministic: every 9x9 block of Z is
+// summed by one warp over a fixed list of observation pairs and written once,
+// and the 7x7 sums are reduced in a fixed order, so that repeated runs give
+// identical bits.
 
 __device__ __forceinline__ void hx_row(double X0, double X1, double X2, int k, double* h) {
     // row k of H_X = [I, -[X]x, X]
@@ -250,17 +244,76 @@ __device__ __forceinline__ void hx_row(double X0, double X1, double X2, int k, d
     else { h[3] = X1; h[4] = -X0; h[5] = 0.0; h[6] = X2; }
 }
 
+// V_o = W_o A_j^-1 for every observation o of point j (thread per observation).
+__global__ void vmat_kernel(int64_t t, const ccov_obs* __restrict__ obs, const double* __restrict__ W,
+                            const double* __restrict__ Ainv, double* __restrict__ V) {
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= t) return;
+    const double* ai = Ainv + 6 * (int64_t)obs[o].pt;
+    const double A00 = ai[0], A01 = ai[1], A02 = ai[2], A11 = ai[3], A12 = ai[4], A22 = ai[5];
+    const double* w = W + 27 * o;
+    double* v = V + 27 * o;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
+        v[3 * p] = w0 * A00 + w1 * A01 + w2 * A02;
+        v[3 * p + 1] = w0 * A01 + w1 * A11 + w2 * A12;
+        v[3 * p + 2] = w0 * A02 + w1 * A12 + w2 * A22;
+    }
+}
+
+// Warp per block Z_ik (i >= k) that has at least one shared point.  desc =
+// (i, k, first entry, entries); an entry is the observation pair (o_i, o_k)
+// of one shared point (o_i = o_k on the diagonal), listed in point order.
+// Lane l owns the entries e = l, l + 32, l + 64 < 81 of the block; the
+// observations' V and W rows are staged in the warp's shared memory.
 __global__ void __launch_bounds__(32 * kWarps)
-schur_scatter_kernel(int64_t m, const int* __restrict__ pt_ptr, const ccov_obs* __restrict__ obs,
-                     const double* __restrict__ W, const double* __restrict__ Ainv,
-                     const double* __restrict__ pts, double* __restrict__ Z, int64_t ldz,
-                     double* __restrict__ W7) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SchurSmem& sm = reinterpret_cast<SchurSmem*>(smem_raw)[threadIdx.x >> 5];
+schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __restrict__ ent,
+                   const double* __restrict__ V, const double* __restrict__ W, const double* __restrict__ U,
+                   double* __restrict__ Z, int64_t ldz) {
+    __shared__ double sv[kWarps][2][28];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    double* vs = sv[wi][0];
+    double* ws = sv[wi][1];
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int e0 = lane, e1 = lane + 32, e2 = lane + 64;
+    const int r0 = e0 / 9, c0 = e0 % 9, r1 = e1 / 9, c1 = e1 % 9, r2 = e2 / 9, c2 = e2 % 9;
+    for (int64_t p = warp; p < npairs; p += nwarp) {
+        const int4 d = desc[p];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int q = d.z; q < d.z + d.w; ++q) {
+            const int2 oo = ent[q];
+            __syncwarp();
+            if (lane < 27) {
+                vs[lane] = V[27 * (int64_t)oo.x + lane];
+                ws[lane] = W[27 * (int64_t)oo.y + lane];
+            }
+            __syncwarp();
+            a0 += vs[3 * r0] * ws[3 * c0] + vs[3 * r0 + 1] * ws[3 * c0 + 1] + vs[3 * r0 + 2] * ws[3 * c0 + 2];
+            a1 += vs[3 * r1] * ws[3 * c1] + vs[3 * r1 + 1] * ws[3 * c1 + 1] + vs[3 * r1 + 2] * ws[3 * c1 + 2];
+            if (e2 < 81)
+                a2 += vs[3 * r2] * ws[3 * c2] + vs[3 * r2 + 1] * ws[3 * c2 + 1] + vs[3 * r2 + 2] * ws[3 * c2 + 2];
+        }
+        const bool diag = d.x == d.y;
+        double* zb = Z + 9 * (int64_t)d.x * ldz + 9 * (int64_t)d.y;
+        const double* u = U + 45 * (int64_t)d.x;
+        // a diagonal block keeps its lower triangle, plus U_i (lower, row by row)
+        if (!diag || c0 <= r0) zb[r0 * ldz + c0] = (diag ? u[r0 * (r0 + 1) / 2 + c0] : 0.0) - a0;
+        if (!diag || c1 <= r1) zb[r1 * ldz + c1] = (diag ? u[r1 * (r1 + 1) / 2 + c1] : 0.0) - a1;
+        if (e2 < 81 && (!diag || c2 <= r2)) zb[r2 * ldz + c2] = (diag ? u[r2 * (r2 + 1) / 2 + c2] : 0.0) - a2;
+    }
+}
+
+// W7 = sum_j H_Xj^T A_j^-1 H_Xj and sum_j H_Xj^T H_Xj (for H^T H of the gauge
+// term): a fixed grid of warps, warp w summing the points j = w (mod warps);
+// lane e < 28 owns entry (p, q), p <= q.  Partial sums part[w][56].
+constexpr int kW7Warps = 2048;
+__global__ void __launch_bounds__(32 * kWarps)
+w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __restrict__ pts,
+                  double* __restrict__ part) {
     const int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // lane e < 28 owns W7 entry (p, q), p <= q, in row-major upper order
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int w7p = 0, w7q = 0;
     {
         int e = lane, p = 0;
@@ -268,21 +321,16 @@ schur_scatter_kernel(int64_t m, const int* __restrict__ pt_ptr, const ccov_obs* 
         w7p = p; w7q = p + e;
     }
     double w7acc = 0.0, hhacc = 0.0;
-    for (int64_t j = warp; j < m; j += nwarp) {
-        const int o0 = pt_ptr[j], L = pt_ptr[j + 1] - o0;
-        const double* ai = Ainv + 6 * j;
-        const double A00 = ai[0], A01 = ai[1], A02 = ai[2], A11 = ai[3], A12 = ai[4], A22 = ai[5];
-        const double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
-        if (lane < 28) {
-            double hp[7], hq[7];
-            double v = 0.0;
-            // (H_X^T H_X)_{pq}, for H^T H of the gauge term
+    if (lane < 28) {
+        for (int64_t j = warp; j < m; j += kW7Warps) {
+            const double* ai = Ainv + 6 * j;
+            const double Am[9] = {ai[0], ai[1], ai[2], ai[1], ai[3], ai[4], ai[2], ai[4], ai[5]};
+            const double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+            double hp[7], hq[7], v = 0.0;
             for (int k = 0; k < 3; ++k) {
                 hx_row(X0, X1, X2, k, hp);
                 hhacc += hp[w7p] * hp[w7q];
             }
-            // (H_X^T A^-1 H_X)_{pq} = sum_{k,l} H_X[k][p] A^-1[k][l] H_X[l][q]
-            double Am[9] = {A00, A01, A02, A01, A11, A12, A02, A12, A22};
             for (int k = 0; k < 3; ++k) {
                 hx_row(X0, X1, X2, k, hp);
                 for (int l = 0; l < 3; ++l) {
@@ -292,78 +340,27 @@ schur_scatter_kernel(int64_t m, const int* __restrict__ pt_ptr, const ccov_obs* 
             }
             w7acc += v;
         }
-        const int nch = (L + 31) >> 5;
-        for (int ca = 0; ca < nch; ++ca) {
-            const int La = min(32, L - 32 * ca);
-            __syncwarp();
-            if (lane < La) {
-                int o = o0 + 32 * ca + lane;
-                const double* w = W + 27 * (int64_t)o;
-                sm.camA[lane] = obs[o].cam;
-#pragma unroll
-                for (int p = 0; p < 9; ++p) {
-                    double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
-                    sm.V[lane][3 * p] = w0 * A00 + w1 * A01 + w2 * A02;
-                    sm.V[lane][3 * p + 1] = w0 * A01 + w1 * A11 + w2 * A12;
-                    sm.V[lane][3 * p + 2] = w0 * A02 + w1 * A12 + w2 * A22;
-                }
-            }
-            for (int cb = ca; cb < nch; ++cb) {
-                const int Lb = min(32, L - 32 * cb);
-                __syncwarp();
-                if (lane < Lb) {
-                    int o = o0 + 32 * cb + lane;
-                    const double* w = W + 27 * (int64_t)o;
-                    sm.camB[lane] = obs[o].cam;
-#pragma unroll
-                    for (int e = 0; e < 27; ++e) sm.Wb[lane][e] = w[e];
-                }
-                __syncwarp();
-                const int npairs = (ca == cb) ? La * (La + 1) / 2 : La * Lb;
-                const int nitems = npairs * 81;
-                for (int q = lane; q < nitems; q += 32) {
-                    int p = q / 81, e = q - 81 * p;
-                    int r = e / 9, c = e - 9 * r;
-                    int a, b;
-                    if (ca == cb) {
-                        // pairs a <= b ordered by b: p = b (b + 1) / 2 + a
-                        b = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
-                        while ((b + 1) * (b + 2) / 2 <= p) ++b;
-                        while (b * (b + 1) / 2 > p) --b;
-                        a = p - b * (b + 1) / 2;
-                    } else {
-                        a = p / Lb;
-                        b = p - a * Lb;
-                    }
-                    const int ia = sm.camA[a], ib = sm.camB[b];
-                    const double* Va = sm.V[a];
-                    const double* Wb = sm.Wb[b];
-                    double v;
-                    int64_t row, col;
-                    if (ia > ib) {
-                        v = Va[3 * r] * Wb[3 * c] + Va[3 * r + 1] * Wb[3 * c + 1] + Va[3 * r + 2] * Wb[3 * c + 2];
-                        row = 9 * (int64_t)ia + r; col = 9 * (int64_t)ib + c;
-                    } else if (ia < ib) {
-                        v = Va[3 * c] * Wb[3 * r] + Va[3 * c + 1] * Wb[3 * r + 1] + Va[3 * c + 2] * Wb[3 * r + 2];
-                        row = 9 * (int64_t)ib + r; col = 9 * (int64_t)ia + c;
-                    } else {
-                        if (c > r) continue;  // diagonal block: lower part only
-                        v = Va[3 * r] * Wb[3 * c] + Va[3 * r + 1] * Wb[3 * c + 1] + Va[3 * r + 2] * Wb[3 * c + 2];
-                        row = 9 * (int64_t)ia + r; col = 9 * (int64_t)ia + c;
-                    }
-                    atomicAdd(Z + row * ldz + col, -v);
-                }
-            }
-        }
-    }
-    if (lane < 28) {
-        atomicAdd(W7 + 7 * w7p + w7q, w7acc);
-        atomicAdd(W7 + 49 + 7 * w7p + w7q, hhacc);
+        part[56 * warp + lane] = w7acc;
+        part[56 * warp + 28 + lane] = hhacc;
     }
 }
 
+// The partial sums in warp order: W7 (upper, row-major 7x7) at W7[0, 49),
+// H_X^T H_X at W7[49, 98).  One thread per entry.
+__global__ void w7_reduce_kernel(const double* __restrict__ part, double* __restrict__ W7) {
+    const int lane = threadIdx.x;
+    if (lane >= 56) return;
+    const int e0 = lane % 28;
+    int e = e0, p = 0;
+    while (p < 7 && e >= 7 - p) { e -= 7 - p; ++p; }
+    const int q = p + e;
+    double s = 0.0;
+    for (int w = 0; w < kW7Warps; ++w) s += part[56 * w + lane];
+    W7[(lane < 28 ? 0 : 49) + 7 * p + q] = s;
+}
+
 // Step (b), camera part: warp per camera.  G_i = -sum_j V_ij H_Xj (the border
-// column block of Z_p without H_P) and Z_ii += U_i.
+// column block of Z_p without H_P), summed in a fixed lane order.
 __global__ void __launch_bounds__(32 * kWarps)
 cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
                  const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
@@ -412,11 +409,6 @@ cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
             }
             double c = warp_sum(sVX[p]);
             if (lane == 0) g[7 * p + 6] = -c;
-        }
-        for (int e = lane; e < 45; e += 32) {
-            int r = 0, s = e;
-            while (s > r) { s -= r + 1; ++r; }
-            Z[(9 * i + r) * ldz + 9 * i + s] += U[45 * i + e];
         }
     }
 }
@@ -549,15 +541,14 @@ void launch_cam_info(Ctx& c) {
 }
 
 void launch_schur(Ctx& c) {
-    size_t smem = sizeof(SchurSmem) * kWarps;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(schur_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr = true;
-    }
-    schur_scatter_kernel<<<grid_for(c.m, kWarps), 32 * kWarps, smem, c.stream>>>(
-        c.m, c.d_pt_ptr, c.d_obs, c.d_W, c.d_Ainv, c.d_pts, c.d_Z, c.Np, c.d_W7);
+    vmat_kernel<<<(int)((c.t + 255) / 256), 256, 0, c.stream>>>(c.t, c.d_obs, c.d_W, c.d_Ainv, c.d_V);
+    CCOV_LAUNCH_CHECK(c);
+    schur_pairs_kernel<<<grid_for(c.npairs, kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np);
+    CCOV_LAUNCH_CHECK(c);
+    w7_partial_kernel<<<kW7Warps / kWarps, 32 * kWarps, 0, c.stream>>>(c.m, c.d_Ainv, c.d_pts, c.d_w7part);
+    CCOV_LAUNCH_CHECK(c);
+    w7_reduce_kernel<<<1, 64, 0, c.stream>>>(c.d_w7part, c.d_W7);
     CCOV_LAUNCH_CHECK(c);
     cam_schur_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
         c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.Np,

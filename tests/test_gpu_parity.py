@@ -99,8 +99,9 @@ def test_repeatable_and_reloadable():
         b = ctx.run()
         ctx.ccov_load(sc.cams, sc.pts, sc.obs_records())
         c = ctx.run()
-    assert metrics.rel_fro(a, b).max() < 1e-12
-    assert metrics.rel_fro(a, c).max() < 1e-12
+    # every sum of the path runs in a fixed order: identical bits
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
 
 
 def test_device_resident_inputs_and_outputs():
@@ -113,7 +114,7 @@ def test_device_resident_inputs_and_outputs():
     with ccov.Context(cams, pts, obs, sc.sigma) as ctx:
         ctx.run(out=out)
     want = ccov.camera_covariances(sc)
-    assert metrics.rel_fro(out.cpu().numpy(), want).max() < 1e-12
+    assert np.array_equal(out.cpu().numpy(), want)
 
 
 def test_degenerate_and_invalid_inputs_are_rejected():
