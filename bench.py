@@ -454,6 +454,7 @@ def run_batch(args):
                                  precision=prec))
         outs.append(torch.empty((sc.n, 9, 9), dtype=torch.float64, device=dev))
     batch = ccov.Batch(ctxs, outs)
+    info = batch.info()
     for _ in range(args.warmup):
         batch.run(stream.cuda_stream)
     barrier(world)
@@ -473,49 +474,46 @@ def run_batch(args):
     value = cams_total * args.steps * world / (ms_total / 1e3)
     batch.close()
 
-    # the same batch without the graph: direct batched call, then scene by scene
+    # the per-scene form of the same batch (each scene's own kernels on its own
+    # stream, one graph), and the direct calls without a graph
+    with ccov.Batch(ctxs, outs, form=ccov.CCOV_BATCH_PER_SCENE) as bp:
+        bp.run(stream.cuda_stream)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        bp.run(stream.cuda_stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ms_per_scene_graph = p0.elapsed_time(p1)
+        per_scene_launches = bp.info()["launches"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ccov.ccov_batch_covariance(ctxs, outs)
     ms_direct = 1e3 * (time.perf_counter() - t0)
-    launches_per_step = sum(c.ccov_get_stats()["launches"] for c in ctxs)  # the graph's kernel nodes
-    t0 = time.perf_counter()
-    for c, o in zip(ctxs, outs):
-        c.run(out=o)
-    ms_serial = 1e3 * (time.perf_counter() - t0)
-
-    # GEMM roofline: one profiled direct pass (events bracket each GEMM launch
-    # while the other scenes run concurrently, so durations are upper bounds)
     for c in ctxs:
         c.close()
-    prof = []
-    for sc in scenes:
-        rec = sc.obs_records()
-        prof.append(ccov.Context(torch.from_numpy(sc.cams).to(dev), torch.from_numpy(sc.pts).to(dev),
-                                 torch.from_numpy(rec.view(np.uint8)).to(dev), sc.sigma,
-                                 precision=prec, profile=True))
-    ccov.ccov_batch_covariance(prof, outs)
-    st = [c.ccov_get_stats() for c in prof]
-    for c in prof:
-        c.close()
-    gemm_ms = sum(s["ms_gemm"] for s in st)
-    gemm_flops = sum(s["gemm_flops"] for s in st)
-    gemm_launches = sum(s["gemm_launches"] for s in st)
+
+    # roofline: the batch's algorithmic work sum (2/3) N_b^3 (Cholesky and
+    # triangular inverse of every scene) over the whole step time, a lower
+    # bound of the GEMMs' own rate (the step also holds steps (a)-(c), the
+    # diagonal blocks and the slicing)
     pk, src = peaks()
-    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
+    alg = sum(2.0 / 3.0 * float(9 * sc.n) ** 3 for sc in scenes)
+    achieved = alg / (ms_step / 1e3) / 1e12
     if prec == ccov.CCOV_PREC_FP64:
         peak, bound, dtype, kern, psrc = FP64_NOMINAL_GFLOPS / 1e3, "alu", "f64", "gemm64_kernel", "nominal FP64"
     else:
         peak, bound, dtype = pk["bf16_tflops_sustained"], "tensor", "bf16"
-        kern, psrc = "ozaki_gemm (split-bf16 tcgen05 trailing updates)", f"bf16 sustained ({src})"
+        kern, psrc = "ozaki_gemm (grouped split-bf16 tcgen05 trailing updates)", f"bf16 sustained ({src})"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kern, "peak_source": psrc, "launches_per_step": gemm_launches,
-            "note": "per-launch event durations summed over 256 concurrently running scenes "
-                    "(overlap makes them upper bounds, frac a lower bound)"}
+            "traffic": None, "kernel": kern, "peak_source": psrc,
+            "work": f"sum over scenes of (2/3) N_b^3 = {alg:.3e} flop per step",
+            "note": "work / whole step time (a lower bound of the dominant kernel's rate)"}
 
-    # end to end: host inputs loaded into every context, host outputs
-    pinned = []
-    e2e_ctx = []
+    # end to end through the same grouped batch: every step loads each
+    # scene's pinned host inputs into its context, replays the batch and
+    # copies every block back to pinned host memory
+    pinned, e2e_ctx = [], []
     for sc in scenes:
         rec = sc.obs_records()
         hc = torch.from_numpy(sc.cams).pin_memory()
@@ -523,22 +521,23 @@ def run_batch(args):
         ho = torch.from_numpy(rec.view(np.uint8)).pin_memory()
         pinned.append((hc.numpy(), hp.numpy(), ho.numpy().view(rec.dtype)))
         e2e_ctx.append(ccov.Context(sc.cams, sc.pts, rec, sc.sigma, precision=prec))
-    h_outs = [torch.empty((sc.n, 9, 9), dtype=torch.float64).pin_memory().numpy() for sc in scenes]
-    ptrs = (__import__("ctypes").c_void_p * len(scenes))(*[o.ctypes.data for o in h_outs])
-    handles = ccov._handles(e2e_ctx)
+    d_outs = [torch.empty((sc.n, 9, 9), dtype=torch.float64, device=dev) for sc in scenes]
+    h_outs = [torch.empty((sc.n, 9, 9), dtype=torch.float64).pin_memory() for sc in scenes]
     h2d = sum(sc.cams.nbytes + sc.pts.nbytes + sc.t * 24 for sc in scenes)
     d2h = cams_total * 81 * 8
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = args.e2e_steps or args.steps
-    f0.record(stream)
-    for _ in range(e2e_steps):
-        for c, (a, b, o) in zip(e2e_ctx, pinned):
-            c.ccov_load(a, b, o)
-        ccov._first_error(e2e_ctx, ccov.load().ccov_batch_covariance(handles, len(scenes), ptrs,
-                                                                     ccov.CCOV_MEM_HOST))
-    f1.record(stream)
-    torch.cuda.synchronize()
+    with ccov.Batch(e2e_ctx, d_outs) as be:
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(e2e_steps):
+            for c, (a, b, o) in zip(e2e_ctx, pinned):
+                c.ccov_load(a, b, o)
+            be.run(stream.cuda_stream)
+            for h, d in zip(h_outs, d_outs):
+                h.copy_(d, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
     ms_e2e = barrier_max(f0.elapsed_time(f1), world) / e2e_steps
     for c in e2e_ctx:
         c.close()
@@ -549,16 +548,23 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": "batch256", "scenes": len(scenes), "cameras": cams_total,
                        "points": sum(sc.m for sc in scenes), "observations": sum(sc.t for sc in scenes),
-                       "precision": args.precision, "form": "one CUDA graph replay per step",
+                       "precision": args.precision,
+                       "form": "grouped launches (one per step for all scenes), one CUDA graph replay per step"
+                               if info["form"] == ccov.CCOV_BATCH_GROUPED else "per-scene kernels, one CUDA graph",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set > L2: the reduced matrices total "
                              f"{sum((9 * sc.n) ** 2 for sc in scenes) * 8 / 1e9:.1f} GB"},
             "clocks": clk,
             "e2e": {"value": cams_total * world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": int(info["launches"]) * args.steps,
             "roofline": roof,
-            "without_graph_ms": {"batched_call": ms_direct, "scene_by_scene": ms_serial}}
+            "batch_form": {"launches_per_step": int(info["launches"]),
+                           "autotuned_gemm": {"ctas": info["gemm_ctas"], "stages": info["gemm_stages"],
+                                              "tune_ms": info["tune_ms"]},
+                           "per_scene_graph": {"ms_per_step": ms_per_scene_graph,
+                                               "launches_per_step": int(per_scene_launches)},
+                           "direct_batched_call_ms": ms_direct}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cams, used, dt = cpu_oracle_batch_sample(scenes)
         line["cpu_baseline"] = {"value": cams / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

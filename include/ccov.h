@@ -237,6 +237,36 @@ CCOV_API ccov_status ccov_batch_create(ccov_ctx* const* ctxs, int k, double* con
 CCOV_API ccov_status ccov_batch_run(ccov_batch* batch, void* stream);
 CCOV_API void ccov_batch_destroy(ccov_batch* batch);
 
+/* Form of a recorded batch.
+ *   CCOV_BATCH_GROUPED: every step of steps (a)-(d) is one launch for all
+ *     scenes (the scenes concatenated for (a)-(c); for (d), per sub-panel
+ *     pair of the blocked factorisation and inverse, one launch per sub-step
+ *     over the scenes that have it, the trailing-update GEMMs as one
+ *     persistent tensor-core kernel over the tiles of all of them); the
+ *     graph holds a few hundred kernels.  Needs MIXED precision with the same
+ *     mixed_slices, nullspace_route and image-point model (the same sigma, or
+ *     per-observation covariances) in every context.  The contexts' inputs
+ *     are read at every replay (so ccov_load applies); their own workspaces
+ *     are not used.  A device-side failure is reported for the batch as a
+ *     whole.  When the batch is created, an autotuner times the whole batch
+ *     under a few launch shapes of the grouped GEMMs (persistent CTA count,
+ *     pipeline depth) and keeps the fastest.
+ *   CCOV_BATCH_PER_SCENE: every context's own steps, forked onto the
+ *     contexts' streams and joined back (any precision, any options).
+ *   CCOV_BATCH_AUTO: grouped when the contexts allow it, else per scene. */
+enum { CCOV_BATCH_AUTO = 0, CCOV_BATCH_PER_SCENE = 1, CCOV_BATCH_GROUPED = 2 };
+CCOV_API ccov_status ccov_batch_create_ex(ccov_ctx* const* ctxs, int k, double* const* outs_device, int form,
+                                          ccov_batch** out);
+
+typedef struct {
+    int form;               /* CCOV_BATCH_PER_SCENE or CCOV_BATCH_GROUPED */
+    int gemm_ctas;          /* grouped: persistent CTAs of the GEMMs chosen by the autotuner */
+    int gemm_stages;        /* grouped: their pipeline depth */
+    int64_t launches;       /* kernels per replay */
+    double tune_ms;         /* grouped: the batch time of the chosen shape while tuning */
+} ccov_batch_info;
+CCOV_API ccov_status ccov_batch_get_info(const ccov_batch* batch, ccov_batch_info* out);
+
 /* Allocation-free entry point (the paper has no counterpart).  For callers that
  * cannot call cudaMalloc: a real-time loop that must not allocate, or code in a
  * process whose device memory is owned by another allocator (a framework's

@@ -23,12 +23,13 @@ CCOV_ERR_TIMEOUT, CCOV_ERR_OOM, CCOV_ERR_CUDA = 4, 5, 6
 CCOV_PREC_FP64, CCOV_PREC_MIXED = 0, 1
 CCOV_MEM_HOST, CCOV_MEM_DEVICE = 0, 1
 CCOV_NULL_PAPER, CCOV_NULL_CLOSED = 0, 1
+CCOV_BATCH_AUTO, CCOV_BATCH_PER_SCENE, CCOV_BATCH_GROUPED = 0, 1, 2
 
 EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_nullspace",
             "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_schur_blocks", "ccov_get_stats",
             "ccov_destroy", "ccov_status_string", "ccov_last_error",
             "ccov_spd_inverse_blocks_noalloc", "ccov_batch_covariance", "ccov_batch_create",
-            "ccov_batch_run", "ccov_batch_destroy"]
+            "ccov_batch_create_ex", "ccov_batch_get_info", "ccov_batch_run", "ccov_batch_destroy"]
 
 
 class CcovError(RuntimeError):
@@ -58,6 +59,14 @@ class Stats(C.Structure):
         for name in ("est_index", "est_rel", "est_norm"):
             d[name] = list(d[name])[:k]
         return d
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("form", C.c_int), ("gemm_ctas", C.c_int), ("gemm_stages", C.c_int), ("launches", C.c_int64),
+                ("tune_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -92,6 +101,8 @@ def load() -> C.CDLL:
         "ccov_spd_inverse_blocks_noalloc": ([P, I64, I64, P, P], I),
         "ccov_batch_covariance": ([P, I, P, I], I),
         "ccov_batch_create": ([P, I, P, C.POINTER(C.c_void_p)], I),
+        "ccov_batch_create_ex": ([P, I, P, I, C.POINTER(C.c_void_p)], I),
+        "ccov_batch_get_info": ([P, C.POINTER(BatchInfo)], I),
         "ccov_batch_run": ([P, P], I),
         "ccov_batch_destroy": ([P], None),
         "ccov_surrogate_features": ([P, P, P], I),
@@ -285,14 +296,21 @@ def ccov_batch_covariance(ctxs, outs=None):
 class Batch:
     """ccov_batch: a batch of contexts recorded once as a CUDA graph."""
 
-    def __init__(self, ctxs, outs_device):
+    def __init__(self, ctxs, outs_device, form=CCOV_BATCH_AUTO):
         self._ctxs = list(ctxs)
         self._outs = list(outs_device)  # kept alive: the graph writes into them
         ptrs = (C.c_void_p * len(ctxs))(*[_ptr(o) for o in self._outs])
         h = C.c_void_p()
-        s = load().ccov_batch_create(_handles(self._ctxs), len(self._ctxs), ptrs, C.byref(h))
+        s = load().ccov_batch_create_ex(_handles(self._ctxs), len(self._ctxs), ptrs, form, C.byref(h))
         self._h = h
         _first_error(self._ctxs, s)
+
+    def info(self) -> dict:
+        out = BatchInfo()
+        s = load().ccov_batch_get_info(self._h, C.byref(out))
+        if s != CCOV_OK:
+            raise CcovError(s, "ccov_batch_get_info")
+        return out.as_dict()
 
     def run(self, stream=None):
         _first_error(self._ctxs, load().ccov_batch_run(self._h, stream))

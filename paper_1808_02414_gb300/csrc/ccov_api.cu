@@ -219,6 +219,8 @@ ccov_status upload(Ctx& c, const double* cams, const double* pts, const ccov_obs
 }  // namespace
 
 namespace ccov {
+ccov_status device_status(Ctx& c, const char* where) { return check_device(c, where); }
+
 void prof_begin(Ctx& c) {
     if (!c.opt.profile || c.capturing) return;
     while (c.prof_ev.size() < c.prof_used + 2) {
@@ -663,12 +665,15 @@ struct ccov_batch {
     std::vector<cudaEvent_t> joins;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    ccov::GroupPlan* group = nullptr;   // the grouped form, or null (per scene)
+    ccov_batch_info info{};
 };
 
 static void batch_free(ccov_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->group) ccov::group_free(b->group);
     for (auto e : b->joins)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -678,9 +683,72 @@ static void batch_free(ccov_batch* b) {
 
 extern "C" {
 
+// The grouped form: plan, autotune, one direct pass, then capture.
+static ccov_status batch_create_grouped(ccov_ctx* const* ctxs, int k, double* const* outs_device, ccov_batch** out) {
+    std::vector<Ctx*> cs(k);
+    for (int i = 0; i < k; ++i) cs[i] = &ctxs[i]->c;
+    ccov_batch* b = new (std::nothrow) ccov_batch();
+    if (!b) return CCOV_ERR_OOM;
+    b->ctxs.assign(ctxs, ctxs + k);
+    b->joins.assign(k, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < k; ++i)
+        ok = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { batch_free(b); return CCOV_ERR_CUDA; }
+    cudaError_t e = ccov::group_create(cs.data(), outs_device, k, &b->group);
+    if (e != cudaSuccess) { batch_free(b); return e == cudaErrorMemoryAllocation ? CCOV_ERR_OOM : CCOV_ERR_CUDA; }
+    // inputs: after whatever the contexts' streams hold
+    for (int i = 0; i < k; ++i) {
+        cudaEventRecord(b->joins[i], cs[i]->stream);
+        cudaStreamWaitEvent(b->master, b->joins[i], 0);
+    }
+    // one direct pass validates the scenes (and sets every kernel attribute)
+    e = ccov::group_enqueue(*b->group, b->master);
+    ccov_status s = e == cudaSuccess ? ccov::group_status(*b->group, b->master, "ccov_batch_create") : CCOV_ERR_CUDA;
+    if (s != CCOV_OK) { batch_free(b); return s; }
+    float tune_ms = 0.f;
+    if (ccov::group_autotune(*b->group, b->master, 1, &tune_ms) != cudaSuccess) { batch_free(b); return CCOV_ERR_CUDA; }
+    s = ccov::group_status(*b->group, b->master, "ccov_batch_create");
+    if (s != CCOV_OK) { batch_free(b); return s; }
+    if (cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        batch_free(b);
+        return CCOV_ERR_CUDA;
+    }
+    e = ccov::group_enqueue(*b->group, b->master);
+    cudaError_t e2 = cudaStreamEndCapture(b->master, &b->graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) { batch_free(b); return CCOV_ERR_CUDA; }
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) { batch_free(b); return CCOV_ERR_CUDA; }
+    b->info.form = CCOV_BATCH_GROUPED;
+    b->info.launches = ccov::group_launches(*b->group);
+    ccov::group_shape(*b->group, &b->info.gemm_ctas, &b->info.gemm_stages);
+    b->info.tune_ms = tune_ms;
+    *out = b;
+    return CCOV_OK;
+}
+
 ccov_status ccov_batch_create(ccov_ctx* const* ctxs, int k, double* const* outs_device, ccov_batch** out) {
+    return ccov_batch_create_ex(ctxs, k, outs_device, CCOV_BATCH_AUTO, out);
+}
+
+ccov_status ccov_batch_create_ex(ccov_ctx* const* ctxs, int k, double* const* outs_device, int form,
+                                 ccov_batch** out) {
     if (!out) return CCOV_ERR_INVALID_ARG;
     *out = nullptr;
+    if (form != CCOV_BATCH_AUTO && form != CCOV_BATCH_PER_SCENE && form != CCOV_BATCH_GROUPED)
+        return CCOV_ERR_INVALID_ARG;
+    {
+        ccov_status s0 = batch_check_args(ctxs, k, outs_device);
+        if (s0 != CCOV_OK) return s0;
+    }
+    if (form != CCOV_BATCH_PER_SCENE) {
+        std::vector<Ctx*> cs(k);
+        for (int i = 0; i < k; ++i) cs[i] = &ctxs[i]->c;
+        if (ccov::group_eligible(cs.data(), k)) return batch_create_grouped(ctxs, k, outs_device, out);
+        if (form == CCOV_BATCH_GROUPED)
+            return fail(&ctxs[0]->c, CCOV_ERR_INVALID_ARG,
+                        "grouped batch: every context needs MIXED precision with the same digits, nullspace "
+                        "route and image-point model");
+    }
     // one direct pass validates the scenes and sets every kernel attribute
     ccov_status s = ccov_batch_covariance(ctxs, k, outs_device, CCOV_MEM_DEVICE);
     if (s != CCOV_OK) return s;
@@ -712,7 +780,15 @@ ccov_status ccov_batch_create(ccov_ctx* const* ctxs, int k, double* const* outs_
     cudaError_t e = cudaStreamEndCapture(b->master, &b->graph);
     if (s != CCOV_OK || e != cudaSuccess) { batch_free(b); return s != CCOV_OK ? s : CCOV_ERR_CUDA; }
     if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) { batch_free(b); return CCOV_ERR_CUDA; }
+    b->info.form = CCOV_BATCH_PER_SCENE;
+    for (int i = 0; i < k; ++i) b->info.launches += ctxs[i]->c.launches;
     *out = b;
+    return CCOV_OK;
+}
+
+ccov_status ccov_batch_get_info(const ccov_batch* b, ccov_batch_info* out) {
+    if (!b || !out) return CCOV_ERR_INVALID_ARG;
+    *out = b->info;
     return CCOV_OK;
 }
 
@@ -727,6 +803,12 @@ ccov_status ccov_batch_run(ccov_batch* b, void* stream) {
     }
     if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return CCOV_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CCOV_ERR_CUDA;
+    if (b->group) {
+        ccov_status s = ccov::group_status(*b->group, st, "ccov_batch_run");
+        if (s != CCOV_OK)
+            for (ccov_ctx* h : b->ctxs) fail(&h->c, s, "ccov_batch_run: a scene of the grouped batch failed");
+        return s;
+    }
     ccov_status first = CCOV_OK;
     for (ccov_ctx* h : b->ctxs) {
         ccov_status si = check_device(h->c, "ccov_batch_run");

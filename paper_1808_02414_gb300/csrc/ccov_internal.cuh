@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/ccov.h"
+#include "group.cuh"
 
 namespace ccov {
 
@@ -61,6 +62,15 @@ struct Ctx {
     int2* d_pair_ent = nullptr;   // per block, the observation pairs (o_i, o_k) in point order
     int64_t npairs = 0, nent = 0;
     double* d_w7part = nullptr;   // fixed-order partial sums of W7 and H_X^T H_X
+    // several scenes in one context (the grouped batch): per camera its scene,
+    // per scene the offset and leading dimension of its Z, its first camera and
+    // its point range; W7 holds 128 doubles per scene
+    const int* d_cam_scene = nullptr;
+    const int64_t* d_scene_zo = nullptr;
+    const int64_t* d_scene_ld = nullptr;
+    const int* d_scene_co = nullptr;
+    const int* d_scene_po = nullptr;
+    int nscenes = 1, w7_wps = 0;
     double* d_Z = nullptr;        // Np x Np row-major, lower triangle
     double* d_Gp = nullptr;       // N x 7: -W A^-1 H_X
     double* d_W7 = nullptr;       // 7 x 7
@@ -131,6 +141,30 @@ cudaError_t mixed_alloc(Ctx& c);
 void mixed_free(Ctx& c);
 cudaError_t mixed_factor_inverse(Ctx& c);
 const long long* mixed_inverse_factor(const Ctx& c);   // X = L^-1, Q42, after mixed_factor_inverse
+cudaError_t mixed_setup();                             // kernel attributes, SM count
+bool mixed_make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, int64_t ld);
+bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np);
+int mixed_stages(int s);
+
+// ---- grouped launches of the batched form (one launch per step for many
+// scenes; parameter records and block prefixes in device memory) ----
+int64_t grp_slice_rows_blocks(int K, int rows);
+int64_t grp_slice_cols_blocks(int ncols);
+int64_t grp_gram_blocks(int64_t ncols);
+void grp_slice_rows(cudaStream_t st, int K, const SliceRowsP* P, const int64_t* pre, int k, int64_t blocks, int* flag);
+void grp_slice_cols(cudaStream_t st, int K, const SliceColsP* P, const int64_t* pre, int k, int64_t blocks, int* flag);
+void grp_potrf(cudaStream_t st, const PotrfP* P, int k, int* flag);
+void grp_gram(cudaStream_t st, const GramP* P, const int64_t* pre, int k, int64_t blocks);
+void grp_zscale(cudaStream_t st, const ZscaleP* P, const int64_t* pre, int k, int64_t blocks, int* flag);
+void grp_identity(cudaStream_t st, const IdentP* P, const int64_t* pre, int k, int64_t blocks);
+cudaError_t grp_gemm(cudaStream_t st, int s, int K, const GemmProblem* probs, int nprobs, int64_t total_pairs,
+                     int* flag, int max_ctas, int stages);
+int64_t mixed_tile_pairs(int M, int N, int lower);   // tile pairs of one GEMM (M, N multiples of 128)
+void launch_g(Ctx& c);                               // G = G_part + H_P
+ccov_status device_status(Ctx& c, const char* where);  // wait for the stream, map the device flag
+void grp_gauge(cudaStream_t st, const GaugeP* P, int k, int* flag);
+void grp_fd(cudaStream_t st, const FdP* P, const int64_t* pre, int k, int64_t blocks, int* flag);
+void grp_extract(cudaStream_t st, const ExtractP* P, const int64_t* pre, int k, int64_t blocks);
 
 // ---- a-posteriori error estimate (k_estimate.cu) ----
 cudaError_t est_alloc(Ctx& c, int k);
@@ -138,6 +172,17 @@ void est_free(Ctx& c);
 void est_keep_fp64(Ctx& c);                  // after the FP64 scaling: keep Z_s
 void est_launch(Ctx& c, const long long* Xq);  // after the inverse, before the extraction
 void est_launch_final(Ctx& c);               // after the extraction
+
+// ---- the batched form as grouped launches (ccov_group.cu) ----
+struct GroupPlan;
+bool group_eligible(Ctx* const* ctxs, int k);
+cudaError_t group_create(Ctx* const* ctxs, double* const* outs, int k, GroupPlan** out);
+cudaError_t group_enqueue(GroupPlan& P, cudaStream_t main);
+cudaError_t group_autotune(GroupPlan& P, cudaStream_t st, int reps, float* best_ms);
+ccov_status group_status(GroupPlan& P, cudaStream_t st, const char* where);
+void group_free(GroupPlan* P);
+int64_t group_launches(const GroupPlan& P);
+void group_shape(const GroupPlan& P, int* cap, int* stages);
 
 }  // namespace ccov
 

@@ -10,6 +10,7 @@
 // Every trailing update is a rank-128 GEMM; in this FP64 path it runs on the
 // FP64 pipe (the mixed path replaces it by tensor-core GEMMs).
 #include "ccov_internal.cuh"
+#include "group.cuh"
 
 namespace ccov {
 namespace {
@@ -69,10 +70,9 @@ __global__ void g_kernel(int64_t N, const double* __restrict__ Gp, const double*
 // One CTA of 256 threads.  Output (small): K = (Lambda^-1 + W7)^-1 at [0, 49),
 // C at [49, 98).  W7 (upper) at W7s[0, 49), H_X^T H_X (upper) at W7s[49, 98).
 constexpr double kGaugeAlpha = 1e-2;
-__global__ void __launch_bounds__(256)
-gauge_kernel(int64_t N, const double* __restrict__ G, const double* __restrict__ HP,
-             const double* __restrict__ Z, int64_t ldz, double* __restrict__ W7s,
-             double* __restrict__ small, int* flag) {
+__device__ __forceinline__ void gauge_body(int64_t N, const double* __restrict__ G, const double* __restrict__ HP,
+                                           const double* __restrict__ Z, int64_t ldz, const double* __restrict__ W7s,
+                                           double* __restrict__ small, int* flag) {
     __shared__ double red[35][33];
     double acc[35];
 #pragma unroll
@@ -125,11 +125,17 @@ gauge_kernel(int64_t N, const double* __restrict__ G, const double* __restrict__
         }
 }
 
+__global__ void __launch_bounds__(256)
+gauge_kernel(int64_t N, const double* __restrict__ G, const double* __restrict__ HP,
+             const double* __restrict__ Z, int64_t ldz, const double* __restrict__ W7s,
+             double* __restrict__ small, int* flag) {
+    gauge_body(N, G, HP, Z, ldz, W7s, small, flag);
+}
+
 // F = G K, D_r = (Z_rr + F_r . G_r)^-1/2 (row r of Z').
-__global__ void fd_kernel(int64_t N, int64_t Np, const double* __restrict__ K,
-                          const double* __restrict__ Z, const double* __restrict__ G,
-                          double* __restrict__ F, double* __restrict__ D, int* flag) {
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fd_body(int64_t N, int64_t Np, const double* __restrict__ K,
+                                        const double* __restrict__ Z, const double* __restrict__ G,
+                                        double* __restrict__ F, double* __restrict__ D, int* flag, int64_t r) {
     if (r >= Np) return;
     if (r >= N) { D[r] = 1.0; return; }
     const double* g = G + 7 * r;
@@ -142,6 +148,12 @@ __global__ void fd_kernel(int64_t N, int64_t Np, const double* __restrict__ K,
     }
     if (!(d > 0.0)) { set_flag(flag, DEV_NOT_SPD, (int)r); d = 1.0; }
     D[r] = 1.0 / sqrt(d);
+}
+
+__global__ void fd_kernel(int64_t N, int64_t Np, const double* __restrict__ K,
+                          const double* __restrict__ Z, const double* __restrict__ G,
+                          double* __restrict__ F, double* __restrict__ D, int* flag) {
+    fd_body(N, Np, K, Z, G, F, D, flag, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // Lower triangle of Z_s = D (Z + F G^T) D in place; padded rows/columns get
@@ -339,9 +351,8 @@ trtri_row_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, double* __res
 }
 
 // Sigma_c = D_c S_c D_c - H_Pc C H_Pc^T for camera c.
-__global__ void extract_kernel(int64_t n, const double* __restrict__ D, const double* __restrict__ HP,
-                               const double* __restrict__ Cg, double* __restrict__ Sig) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void extract_body(int64_t n, const double* __restrict__ D, const double* __restrict__ HP,
+                                             const double* __restrict__ Cg, double* __restrict__ Sig, int64_t e) {
     if (e >= n * 81) return;
     int64_t cam = e / 81;
     int ab = (int)(e % 81), a = ab / 9, b = ab % 9;
@@ -356,6 +367,29 @@ __global__ void extract_kernel(int64_t n, const double* __restrict__ D, const do
     Sig[e] = Sig[e] * D[9 * cam + a] * D[9 * cam + b] - g;
 }
 
+__global__ void extract_kernel(int64_t n, const double* __restrict__ D, const double* __restrict__ HP,
+                               const double* __restrict__ Cg, double* __restrict__ Sig) {
+    extract_body(n, D, HP, Cg, Sig, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
+// ---- grouped forms: the same step of many scenes in one launch ----
+__global__ void __launch_bounds__(256) gauge_grouped(const GaugeP* __restrict__ P, int* flag) {
+    const GaugeP& a = P[blockIdx.x];
+    gauge_body(a.N, a.G, a.HP, a.Z, a.ldz, a.W7s, a.small, flag);
+}
+
+__global__ void fd_grouped(const FdP* __restrict__ P, const int64_t* __restrict__ pre, int k, int* flag) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const FdP& a = P[q];
+    fd_body(a.N, a.Np, a.K, a.Z, a.G, a.F, a.D, flag, (blockIdx.x - pre[q]) * (int64_t)blockDim.x + threadIdx.x);
+}
+
+__global__ void extract_grouped(const ExtractP* __restrict__ P, const int64_t* __restrict__ pre, int k) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const ExtractP& a = P[q];
+    extract_body(a.n, a.D, a.HP, a.Cg, a.Sig, (blockIdx.x - pre[q]) * (int64_t)blockDim.x + threadIdx.x);
+}
+
 }  // namespace
 
 cudaError_t setup_dense64() {
@@ -364,6 +398,11 @@ cudaError_t setup_dense64() {
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(trtri_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * (kNB * kCW + kNB * kNB)));
+}
+
+void launch_g(Ctx& c) {
+    g_kernel<<<(int)((7 * c.N + 255) / 256), 256, 0, c.stream>>>(c.N, c.d_Gp, c.d_HP, c.d_G);
+    c.launches++;
 }
 
 void launch_form_scaled(Ctx& c) {
@@ -418,6 +457,16 @@ void launch_trtri_row(Ctx& c, int64_t k0) {
     trtri_row_kernel<<<grid, 288, sizeof(double) * (kNB * kCW + kNB * kNB), c.stream>>>(
         c.n, c.Np, k0, ncols, c.d_R, c.d_Linv + (k0 / kNB) * kNB * kNB, c.d_Sig);
     c.launches++;
+}
+
+void grp_gauge(cudaStream_t st, const GaugeP* P, int k, int* flag) { gauge_grouped<<<k, 256, 0, st>>>(P, flag); }
+
+void grp_fd(cudaStream_t st, const FdP* P, const int64_t* pre, int k, int64_t blocks, int* flag) {
+    fd_grouped<<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
+}
+
+void grp_extract(cudaStream_t st, const ExtractP* P, const int64_t* pre, int k, int64_t blocks) {
+    extract_grouped<<<(unsigned)blocks, 256, 0, st>>>(P, pre, k);
 }
 
 void launch_extract(Ctx& c) {

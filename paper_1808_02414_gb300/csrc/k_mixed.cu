@@ -30,11 +30,13 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstring>
 #include <utility>
 #include <vector>
 
 #include "ccov_internal.cuh"
 #include "ds_arith.cuh"
+#include "group.cuh"
 #include "tc_ptx.cuh"
 #include "../../include/ccov_testing.h"
 
@@ -203,23 +205,38 @@ __device__ __forceinline__ long long combine_biased(const unsigned (&u)[Slots<S,
     return (long long)(T - magic_share<S, K>());
 }
 
-struct GemmArgs {
-    const __nv_bfloat16* digA;  // digit planes of A and B (layout of blk_off)
-    const __nv_bfloat16* digB;
-    int M, N;             // rows of A and of B (multiples of 128 and 64)
-    int plane_rows;       // rows per digit plane in the operand buffers (Np)
-    int a_row0, b_row0;   // first row of the operands inside their planes
-    int c_x0, c_y0;       // origin of C in its map (column, row)
-    int lower;            // keep only tiles touching the lower triangle
-    int sub;              // 1: C -= A B^T, 0: C = A B^T
-    int shift0;           // F_C - 14
-    const int* expA;      // per row of A (nullptr = 0)
-    const int* expB;      // per row of B (nullptr = 0)
-    int stages;
-    int* flag;
-    unsigned long long wait_ns;  // limit of every barrier wait
-    long long skip_fill;         // test hook: the producer leaves out this pipeline fill (-1: none)
+struct TileRef {
+    const GemmArgs* a;
+    const CUtensorMap* mB;
+    const CUtensorMap* mC;
+    int ti, tj;
 };
+
+// The problem and tile of global tile pair pr for CTA `rank` of its pair.
+template <bool Grouped>
+__device__ __forceinline__ TileRef locate_tile(int64_t pr, uint32_t rank, const GemmArgs* g, const CUtensorMap* mB,
+                                              const CUtensorMap* mC, const GemmProblem* probs, int nprobs) {
+    TileRef r;
+    int64_t lp = pr;
+    if (Grouped) {
+        int lo = 0, hi = nprobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].pair0 <= pr) lo = mid;
+            else hi = mid - 1;
+        }
+        r.a = &probs[lo].g;
+        r.mB = &probs[lo].mapB;
+        r.mC = &probs[lo].mapC;
+        lp = pr - probs[lo].pair0;
+    } else {
+        r.a = g;
+        r.mB = mB;
+        r.mC = mC;
+    }
+    tile_coords(2 * lp + rank, r.a->N / kBN, r.a->lower, r.ti, r.tj);
+    return r;
+}
 
 __device__ __forceinline__ long long shift_round(long long p, int sh) {
     if (sh >= 0) return (long long)((unsigned long long)p << (sh > 62 ? 62 : sh));
@@ -237,10 +254,14 @@ __device__ __forceinline__ long long shift_round(long long p, int sh) {
 // 64 columns.  The result tile leaves through shared memory with TMA, a
 // quarter at a time: C -= A B^T as a reduce-add of -A B^T into C (the
 // addition happens in L2, so C is never read into the SM), C = A B^T as a
-// plain store.
-template <int S, int K>
+// plain store.  Grouped: the tile pairs of `nprobs` problems are numbered
+// one after the other and every CTA finds the problem of each of its pairs.
+template <int S, int K, bool Grouped>
+// 18 warps: two of the SM's four register files host five warps each, which
+// caps a thread at 96 registers
 __global__ void __launch_bounds__(kThreads, 1)
-ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB, GemmArgs g) {
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ GemmArgs g, const GemmProblem* __restrict__ probs, int nprobs) {
     using SL = Slots<S, K>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the 128-byte-swizzled staging buffer needs a 1024-byte aligned start;
@@ -263,12 +284,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
     uint32_t* tmem_slot = (uint32_t*)(drain + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = g.N / kBN;
-    const int64_t ntiles = tile_count(g.M / kBM, tiles_n, g.lower);
     // tiles come in pairs (2P, 2P + 1) in one row of tiles; CTA 2c + rank
     // takes tile 2P + rank of every pair P of CTA pair c (the grid is even)
     const uint32_t rank = blockIdx.x & 1;
-    const int64_t npairs = ntiles / 2;
+    const int64_t npairs = Grouped ? g.total_pairs : tile_count(g.M / kBM, g.N / kBN, g.lower) / 2;
     const int64_t pair0 = blockIdx.x >> 1, pair_step = gridDim.x >> 1;
     const unsigned long long wlim = g.wait_ns;
 
@@ -299,21 +318,20 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             bool ok = true;
             long long fill = 0;
             for (int64_t pr = pair0; pr < npairs && ok; pr += pair_step) {
-                const int64_t t = 2 * pr + rank;
-                int ti, tj;
-                tile_coords(t, tiles_n, g.lower, ti, tj);
+                const TileRef tr = locate_tile<Grouped>(pr, rank, &g, &mapB, &mapC, probs, nprobs);
+                const GemmArgs& a = *tr.a;
                 for (int ks = 0; ks < K / kKS; ++ks, ++fill) {
                     if (!mbar_wait(empty + stage, phase ^ 1, g.flag, 1, wlim)) { ok = false; break; }
                     if (fill != g.skip_fill) {
                         unsigned char* st = tiles + stage * stage_bytes;
                         mbar_expect_tx(full + stage, (uint32_t)stage_bytes);
                         // A: all digit planes of the 128-row tile, adjacent in memory
-                        bulk_load(st, g.digA + blk_off(0, g.a_row0 + ti * kBM, ks * kKS, g.plane_rows, S),
+                        bulk_load(st, a.digA + blk_off(0, a.a_row0 + tr.ti * kBM, ks * kKS, a.plane_rows, S),
                                   (uint32_t)(S * kAPl), full + stage);
                         // B: this CTA's 64 rows of every plane, one tensor copy
-                        const int br = g.b_row0 + tj * kBN;
-                        tma_load_5d(st + S * kAPl, &mapB, full + stage, 0, 0, (br >> 6) & 1, 0,
-                                    ks * (g.plane_rows >> 7) + (br >> 7));
+                        const int br = a.b_row0 + tr.tj * kBN;
+                        tma_load_5d(st + S * kAPl, tr.mB, full + stage, 0, 0, (br >> 6) & 1, 0,
+                                    ks * (a.plane_rows >> 7) + (br >> 7));
                     }
                     if (++stage == g.stages) { stage = 0; phase ^= 1; }
                 }
@@ -368,10 +386,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
         const bool leader = (warp == 2 && lane == 0);
         uint32_t acc_phase = 0;
         for (int64_t pr = pair0; pr < npairs; pr += pair_step) {
-            const int64_t t = 2 * pr + rank;
-            int ti, tj;
-            tile_coords(t, tiles_n, g.lower, ti, tj);
-            const int cx = g.c_x0 + tj * kBN, cy = g.c_y0 + ti * kBM;
+            const TileRef tr = locate_tile<Grouped>(pr, rank, &g, &mapB, &mapC, probs, nprobs);
+            const GemmArgs& a = *tr.a;
+            const int ti = tr.ti, tj = tr.tj;
+            const int cx = a.c_x0 + tj * kBN, cy = a.c_y0 + ti * kBM;
             if (leader) bulk_wait_read0();  // the previous tile's copy-out has left shared memory
             epi_bar();
             // warp-uniform: the vote, the re-read and the arrival below are per warp
@@ -389,6 +407,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
 #pragma unroll
                 for (int sl = 0; sl < SL::total; ++sl) tmem_ld8(trow + (uint32_t)(sl * kBN + col0), v[sl]);
                 tmem_wait_ld();
+#pragma unroll
+                for (int sl = 0; sl < SL::total; ++sl) tmem_regs_after_wait<8>(v[sl]);
                 // T = sum_g P_g 2^(8 (S-1-g)) exactly (|T| < 2^63); the usual
                 // case takes the biased bit patterns, the rare one (some
                 // |P| > 2^22 in the warp) reads the chunk again and converts
@@ -412,6 +432,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
                     for (int sl = 0; sl < SL::total; ++sl) tmem_ld8(trow + (uint32_t)(sl * kBN + col0), v[sl]);
                     tmem_wait_ld();
 #pragma unroll
+                    for (int sl = 0; sl < SL::total; ++sl) tmem_regs_after_wait<8>(v[sl]);
+#pragma unroll
                     for (int j = 0; j < 8; ++j) res[8 * cc + j] = combine_converted<S, K>(v, j);
                 }
             }
@@ -421,8 +443,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
             acc_phase ^= 1;
             // one rounding shift of each sum to the fixed point of C
             {
-                const int sh = (g.expA ? g.expA[g.a_row0 + ti * kBM + r] : 0) + g.shift0 - 8 * (S - 1);
-                const int* eBp = g.expB ? g.expB + g.b_row0 + tj * kBN + kEpiCols * part : nullptr;
+                const int sh = (a.expA ? a.expA[a.a_row0 + ti * kBM + r] : 0) + a.shift0 - 8 * (S - 1);
+                const int* eBp = a.expB ? a.expB + a.b_row0 + tj * kBN + kEpiCols * part : nullptr;
 #pragma unroll
                 for (int q = 0; q < kEpiCols; ++q) res[q] = shift_round(res[q], sh + (eBp ? eBp[q] : 0));
             }
@@ -440,14 +462,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constan
 #pragma unroll
                     for (int q = 0; q < kEpiCols; q += 2) {
                         longlong2* cp = (longlong2*)(ctile + r * 128 + ((((q >> 1)) ^ (r & 7)) << 4));
-                        *cp = g.sub ? make_longlong2(-res[q], -res[q + 1]) : make_longlong2(res[q], res[q + 1]);
+                        *cp = a.sub ? make_longlong2(-res[q], -res[q + 1]) : make_longlong2(res[q], res[q + 1]);
                     }
                 }
                 fence_proxy_async();
                 epi_bar();
                 if (leader) {
-                    if (g.sub) tma_reduce_add_2d(&mapC, ctile, cx + kEpiCols * rd, cy);
-                    else tma_store_2d(&mapC, ctile, cx + kEpiCols * rd, cy);
+                    if (a.sub) tma_reduce_add_2d(tr.mC, ctile, cx + kEpiCols * rd, cy);
+                    else tma_store_2d(tr.mC, ctile, cx + kEpiCols * rd, cy);
                     bulk_commit();
                 }
             }
@@ -533,12 +555,12 @@ __device__ __forceinline__ int tile16_khalf(int lane) { return (lane >> 3) & 1; 
 // writes each digit plane with one 16-byte store; a warp covers 16 rows of
 // one K slice.  rows is a multiple of 16.
 template <int K>
-__global__ void __launch_bounds__(256)
-slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
-                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
+__device__ __forceinline__ void slice_rows_body(int rows, const long long* __restrict__ src, int64_t ld, int F, int s,
+                                                int plane_rows, __nv_bfloat16* __restrict__ dst,
+                                                int* __restrict__ expo, int* flag, int64_t bid) {
     constexpr int KS = K / 16;
     const int lane = threadIdx.x & 31;
-    const int64_t wt = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t wt = (bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int r = (int)(wt / KS) * 16 + tile16_row(lane);
     const int k0 = 16 * (int)(wt % KS) + 8 * tile16_khalf(lane);
     if (r >= rows) return;
@@ -561,6 +583,13 @@ slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F
     split_store8(w, s, dst + blk_off(0, r, k0, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
 }
 
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
+                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
+    slice_rows_body<K>(rows, src, ld, F, s, plane_rows, dst, expo, flag, blockIdx.x);
+}
+
 // Column split: a K-row block (K = 128 or 256) of an int64 Q(F) matrix,
 // columns [0, ncols), transposed into digit rows (row = source column,
 // K = source rows), per-column exponent from the column maximum.  The block
@@ -569,12 +598,12 @@ slice_rows_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F
 // each digit plane with one 16-byte store (a warp: 16 columns of one K
 // slice, so that its stores are contiguous).
 template <int K>
-__global__ void __launch_bounds__(256)
-slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
-                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
+__device__ __forceinline__ void slice_cols_body(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s,
+                                                int plane_rows, __nv_bfloat16* __restrict__ dst,
+                                                int* __restrict__ expo, int* flag, int64_t bid) {
     extern __shared__ __align__(16) long long tile[];   // [K][33]
     __shared__ int cexp[32];
-    const int c0 = blockIdx.x * 32;
+    const int c0 = (int)bid * 32;
     const int tid = threadIdx.x;
     for (int e = tid; e < K * 32; e += 256) {
         int rr = e >> 5, c = e & 31;
@@ -620,6 +649,13 @@ slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int 
     }
 }
 
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_cols_kernel(int ncols, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
+                  __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
+    slice_cols_body<K>(ncols, src, ld, F, s, plane_rows, dst, expo, flag, blockIdx.x);
+}
+
 // Row and column of entry t of a lower triangle stored row by row.
 __device__ __forceinline__ void tri_index(int t, int& i, int& l) {
     i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -657,11 +693,10 @@ __device__ __forceinline__ void ds_sqrt_inv(dsf d, dsf& l, dsf& inv, dsf& inv2) 
 // thread four consecutive columns of one row; the block's rows of F and D
 // (with the 2^60 folded into D_i) and columns of G and D are converted once
 // into shared memory.
-__global__ void __launch_bounds__(256)
-zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
-                const double* __restrict__ G, const double* __restrict__ D, long long* __restrict__ Zkeep,
-                int* flag) {
-    const int64_t bi = blockIdx.y, bj = blockIdx.x;
+__device__ __forceinline__ void zscale_q_body(int64_t N, int64_t Np, double* __restrict__ Z,
+                                              const double* __restrict__ F, const double* __restrict__ G,
+                                              const double* __restrict__ D, long long* __restrict__ Zkeep, int* flag,
+                                              int64_t bi, int64_t bj) {
     if (bj > bi) return;
     __shared__ dsf Fs[32][7], Gs[32][7], Dr[32], Dc[32];
     const int tid = threadIdx.y * 8 + threadIdx.x;
@@ -712,6 +747,13 @@ zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __r
     }
 }
 
+__global__ void __launch_bounds__(256)
+zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __restrict__ F,
+                const double* __restrict__ G, const double* __restrict__ D, long long* __restrict__ Zkeep,
+                int* flag) {
+    zscale_q_body(N, Np, Z, F, G, D, Zkeep, flag, blockIdx.y, blockIdx.x);
+}
+
 // Cholesky of the 128 x 128 diagonal block from Q60 (L in the lower
 // triangle, its inverse X = L^-1 transposed in the upper one, both in
 // double-single shared memory), L written back as Q60, X as digit planes
@@ -723,9 +765,9 @@ zscale_q_kernel(int64_t N, int64_t Np, double* __restrict__ Z, const double* __r
 constexpr int kLD = kNB + 1;
 constexpr int kPW = 32;                                   // panel width
 constexpr size_t kDiagSmem = sizeof(dsf) * (kNB * kLD + kNB + 3 * kPW * kPW);
-__global__ void __launch_bounds__(512)
-potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bfloat16* __restrict__ digL,
-                    int* __restrict__ expL, int s, int* flag) {
+__device__ __forceinline__ void potrf_diag_q_body(long long* __restrict__ Z, int64_t ld, int64_t k0,
+                                                  __nv_bfloat16* __restrict__ digL, int* __restrict__ expL, int s,
+                                                  int* flag) {
     extern __shared__ __align__(16) dsf S[];      // 128 x 129
     dsf* invd = S + kNB * kLD;                    // 1 / L_jj
     dsf* T = invd + kNB;                          // 3 x 32 x 32: one block row of sum_k L_ik X_kj
@@ -944,18 +986,23 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
     }
 }
 
+__global__ void __launch_bounds__(512)
+potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bfloat16* __restrict__ digL,
+                    int* __restrict__ expL, int s, int* flag) {
+    potrf_diag_q_body(Z, ld, k0, digL, expL, s, flag);
+}
+
 // Camera Gram blocks Sig_c += X[k, c]^T X[k, c] from the finished Q42 row
 // block k of X (128 rows), 4 cameras (36 columns) per CTA, summed in
 // double-single arithmetic and added to the FP64 blocks once.  A thread
 // takes entries (a, b), a <= b, of the symmetric blocks (45 per camera) and
 // sums the 128 rows in four interleaved chains.
 constexpr int kGW = 36;
-__global__ void __launch_bounds__(128)
-gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long* __restrict__ R,
-              double* __restrict__ Sig) {
+__device__ __forceinline__ void gram_q_body(int64_t n, int64_t Np, int64_t k0, int64_t ncols,
+                                            const long long* __restrict__ R, double* __restrict__ Sig, int64_t bid) {
     __shared__ dsf T[kNB][kGW + 1];
     const int tid = threadIdx.x;
-    const int64_t c0 = blockIdx.x * (int64_t)kGW;
+    const int64_t c0 = bid * (int64_t)kGW;
     constexpr float kS = 2.2737367544323206e-13f;  // 2^-42
     for (int e = tid; e < kNB * kGW; e += 128) {
         int r = e / kGW, c = e % kGW;
@@ -985,9 +1032,59 @@ gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long*
     }
 }
 
+__global__ void __launch_bounds__(128)
+gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long* __restrict__ R,
+              double* __restrict__ Sig) {
+    gram_q_body(n, Np, k0, ncols, R, Sig, blockIdx.x);
+}
+
 __global__ void identity_q_kernel(int64_t Np, long long* X) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < Np) X[i * Np + i] = 1ll << kFX;
+}
+
+// ---- grouped forms: one launch for the same step of many scenes ----
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_rows_grouped(const SliceRowsP* __restrict__ P, const int64_t* __restrict__ pre, int k, int* flag) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const SliceRowsP& a = P[q];
+    slice_rows_body<K>(a.rows, a.src, a.ld, a.F, a.s, a.plane_rows, a.dst, a.expo, flag, blockIdx.x - pre[q]);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_cols_grouped(const SliceColsP* __restrict__ P, const int64_t* __restrict__ pre, int k, int* flag) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const SliceColsP& a = P[q];
+    slice_cols_body<K>(a.ncols, a.src, a.ld, a.F, a.s, a.plane_rows, a.dst, a.expo, flag, blockIdx.x - pre[q]);
+}
+
+__global__ void __launch_bounds__(512) potrf_diag_q_grouped(const PotrfP* __restrict__ P, int* flag) {
+    const PotrfP& a = P[blockIdx.x];
+    potrf_diag_q_body(a.Z, a.ld, a.k0, a.digL, a.expL, a.s, flag);
+}
+
+__global__ void __launch_bounds__(128)
+gram_q_grouped(const GramP* __restrict__ P, const int64_t* __restrict__ pre, int k) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const GramP& a = P[q];
+    gram_q_body(a.n, a.Np, a.k0, a.ncols, a.R, a.Sig, blockIdx.x - pre[q]);
+}
+
+__global__ void __launch_bounds__(256)
+zscale_q_grouped(const ZscaleP* __restrict__ P, const int64_t* __restrict__ pre, int k, int* flag) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const ZscaleP& a = P[q];
+    const int64_t b = blockIdx.x - pre[q];
+    zscale_q_body(a.N, a.Np, a.Z, a.F, a.G, a.D, nullptr, flag, b / a.nt, b % a.nt);
+}
+
+__global__ void identity_q_grouped(const IdentP* __restrict__ P, const int64_t* __restrict__ pre, int k) {
+    const int q = find_group(pre, k, blockIdx.x);
+    const IdentP& a = P[q];
+    const int64_t i = (blockIdx.x - pre[q]) * (int64_t)blockDim.x + threadIdx.x;
+    if (i < a.Np) a.X[i * a.Np + i] = 1ll << kFX;
 }
 
 // ---------------------------------------------------------------------------
@@ -1047,7 +1144,10 @@ int g_num_sms = 0;
 
 template <int S, int K>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(ozaki_gemm_kernel<S, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<S, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem(S, pick_stages(S)));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(ozaki_gemm_kernel<S, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)gemm_smem(S, pick_stages(S)));
 }
 
@@ -1089,7 +1189,9 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     cfg.attrs = nullptr;
     cfg.numAttrs = 0;
     const CUtensorMap& mapB = bb == BUF_P ? st.mapBP : (bb == BUF_Q ? st.mapBQ : st.mapBL);
-#define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_>, mapC, mapB, g)
+    const GemmProblem* no_probs = nullptr;
+    int no_n = 0;
+#define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_, false>, mapC, mapB, g, no_probs, no_n)
     if (K == 256) {
         switch (st.s) {
             case 4: CCOV_OZ(4, 256); break;
@@ -1148,6 +1250,114 @@ void potrf_block(Ctx& c, int64_t blk) {
 
 }  // namespace
 
+// ---- grouped launchers (the batched form) ----
+int64_t grp_slice_rows_blocks(int K, int rows) { return ((int64_t)rows / 16 * (K / 16) * 32 + 255) / 256; }
+int64_t grp_slice_cols_blocks(int ncols) { return (ncols + 31) / 32; }
+int64_t grp_gram_blocks(int64_t ncols) { return (ncols + kGW - 1) / kGW; }
+
+void grp_slice_rows(cudaStream_t st, int K, const SliceRowsP* P, const int64_t* pre, int k, int64_t blocks,
+                    int* flag) {
+    if (K == 256) slice_rows_grouped<256><<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
+    else slice_rows_grouped<128><<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
+}
+
+void grp_slice_cols(cudaStream_t st, int K, const SliceColsP* P, const int64_t* pre, int k, int64_t blocks,
+                    int* flag) {
+    const size_t smem = (size_t)K * 33 * 8;
+    if (K == 256) slice_cols_grouped<256><<<(unsigned)blocks, 256, smem, st>>>(P, pre, k, flag);
+    else slice_cols_grouped<128><<<(unsigned)blocks, 256, smem, st>>>(P, pre, k, flag);
+}
+
+void grp_potrf(cudaStream_t st, const PotrfP* P, int k, int* flag) {
+    potrf_diag_q_grouped<<<k, 512, kDiagSmem, st>>>(P, flag);
+}
+
+void grp_gram(cudaStream_t st, const GramP* P, const int64_t* pre, int k, int64_t blocks) {
+    gram_q_grouped<<<(unsigned)blocks, 128, 0, st>>>(P, pre, k);
+}
+
+void grp_zscale(cudaStream_t st, const ZscaleP* P, const int64_t* pre, int k, int64_t blocks, int* flag) {
+    zscale_q_grouped<<<(unsigned)blocks, dim3(8, 32), 0, st>>>(P, pre, k, flag);
+}
+
+void grp_identity(cudaStream_t st, const IdentP* P, const int64_t* pre, int k, int64_t blocks) {
+    identity_q_grouped<<<(unsigned)blocks, 256, 0, st>>>(P, pre, k);
+}
+
+// The persistent GEMM over the tile pairs of `nprobs` problems (device
+// array, each with its own maps), at most max_ctas CTAs.
+cudaError_t grp_gemm(cudaStream_t st, int s, int K, const GemmProblem* probs, int nprobs, int64_t total_pairs,
+                     int* flag, int max_ctas, int stages) {
+    if (total_pairs <= 0) return cudaSuccess;
+    GemmArgs g = {};
+    g.stages = stages > 0 && gemm_smem(s, stages) <= gemm_smem(s, pick_stages(s)) ? stages : pick_stages(s);
+    g.flag = flag;
+    g.wait_ns = ptx::kWaitNs;
+    g.skip_fill = -1;
+    g.total_pairs = total_pairs;
+    const int cap = (max_ctas < g_num_sms ? max_ctas : g_num_sms) / 2;
+    const int grid = 2 * (int)(total_pairs < cap ? total_pairs : cap);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = gemm_smem(s, g.stages);
+    cfg.stream = st;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof none);
+#define CCOV_OZG(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_, true>, none, none, g, probs, nprobs)
+    cudaError_t e;
+    if (K == 256) {
+        switch (s) {
+            case 4: e = CCOV_OZG(4, 256); break;
+            case 5: e = CCOV_OZG(5, 256); break;
+            default: e = CCOV_OZG(6, 256); break;
+        }
+    } else {
+        switch (s) {
+            case 4: e = CCOV_OZG(4, 128); break;
+            case 5: e = CCOV_OZG(5, 128); break;
+            default: e = CCOV_OZG(6, 128); break;
+        }
+    }
+#undef CCOV_OZG
+    return e;
+}
+
+// Kernel attributes of the mixed path (shared memory sizes) and the SM count.
+cudaError_t mixed_setup() {
+    cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
+                        set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
+    for (cudaError_t x : a)
+        if (x != cudaSuccess) return x;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(potrf_diag_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kDiagSmem)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(potrf_diag_q_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kDiagSmem)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(slice_cols_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  256 * 33 * 8)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(slice_cols_grouped<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  256 * 33 * 8)) != cudaSuccess)
+        return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    return cudaSuccess;
+}
+
+bool mixed_make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, int64_t ld) {
+    return make_c_map(map, buf, rows, cols, ld);
+}
+
+bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) { return make_b_map(map, buf, s, Np); }
+
+int mixed_stages(int s) { return pick_stages(s); }
+
+int64_t mixed_tile_pairs(int M, int N, int lower) { return tile_count(M / kBM, N / kBN, lower) / 2; }
+
 cudaError_t mixed_alloc(Ctx& c) {
     c.mixed = new MixedState();
     MixedState& st = *c.mixed;
@@ -1188,20 +1398,7 @@ cudaError_t mixed_alloc(Ctx& c) {
         !make_b_map(&st.mapBP2, st.digP2, st.s, Np) || !make_b_map(&st.mapBQ2, st.digQ2, st.s, Np) ||
         !make_b_map(&st.mapBL, st.digL, st.s, Np))
         return cudaErrorInvalidValue;
-    cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
-                        set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
-    for (cudaError_t x : a)
-        if (x != cudaSuccess) return x;
-    if ((e = cudaFuncSetAttribute(potrf_diag_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kDiagSmem)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(slice_cols_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  256 * 33 * 8)) != cudaSuccess)
-        return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    return cudaSuccess;
+    return mixed_setup();
 }
 
 const long long* mixed_inverse_factor(const Ctx& c) { return c.mixed ? c.mixed->R : nullptr; }
@@ -1378,6 +1575,7 @@ static ccov_status test_gemm(int s, int K, int M, int N, const uint16_t* digA, c
         if (cudaDeviceSynchronize() != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         launch_ozaki(c, K, BUF_P, 0, M, BUF_Q, 0, N, mapC, 0, 0, lower, sub, Fc, dEA, dEB);
         if (c.mixed_bad_launch) { st = CCOV_ERR_INVALID_ARG; break; }
+        if (cudaGetLastError() != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         if (cudaStreamSynchronize(c.stream) != cudaSuccess) { st = CCOV_ERR_CUDA; break; }
         int flag[2];
         cudaMemcpy(flag, c.d_flag, sizeof flag, cudaMemcpyDeviceToHost);

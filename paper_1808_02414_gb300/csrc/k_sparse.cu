@@ -267,10 +267,15 @@ __global__ void vmat_kernel(int64_t t, const ccov_obs* __restrict__ obs, const d
 // of one shared point (o_i = o_k on the diagonal), listed in point order.
 // Lane l owns the entries e = l, l + 32, l + 64 < 81 of the block; the
 // observations' V and W rows are staged in the warp's shared memory.
+// Several scenes at once (cam_scene not null): camera i belongs to scene
+// cam_scene[i], whose matrix starts at Z + scene_zo[s] with leading
+// dimension scene_ld[s] and whose first camera is scene_co[s].
 __global__ void __launch_bounds__(32 * kWarps)
 schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __restrict__ ent,
                    const double* __restrict__ V, const double* __restrict__ W, const double* __restrict__ U,
-                   double* __restrict__ Z, int64_t ldz) {
+                   double* __restrict__ Z, int64_t ldz, const int* __restrict__ cam_scene,
+                   const int64_t* __restrict__ scene_zo, const int64_t* __restrict__ scene_ld,
+                   const int* __restrict__ scene_co) {
     __shared__ double sv[kWarps][2][28];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     double* vs = sv[wi][0];
@@ -296,24 +301,36 @@ schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __
                 a2 += vs[3 * r2] * ws[3 * c2] + vs[3 * r2 + 1] * ws[3 * c2 + 1] + vs[3 * r2 + 2] * ws[3 * c2 + 2];
         }
         const bool diag = d.x == d.y;
-        double* zb = Z + 9 * (int64_t)d.x * ldz + 9 * (int64_t)d.y;
+        double* zs = Z;
+        int64_t ld = ldz, li = d.x, lk = d.y;
+        if (cam_scene) {
+            const int sc = cam_scene[d.x];
+            zs = Z + scene_zo[sc];
+            ld = scene_ld[sc];
+            li -= scene_co[sc];
+            lk -= scene_co[sc];
+        }
+        double* zb = zs + 9 * li * ld + 9 * lk;
         const double* u = U + 45 * (int64_t)d.x;
         // a diagonal block keeps its lower triangle, plus U_i (lower, row by row)
-        if (!diag || c0 <= r0) zb[r0 * ldz + c0] = (diag ? u[r0 * (r0 + 1) / 2 + c0] : 0.0) - a0;
-        if (!diag || c1 <= r1) zb[r1 * ldz + c1] = (diag ? u[r1 * (r1 + 1) / 2 + c1] : 0.0) - a1;
-        if (e2 < 81 && (!diag || c2 <= r2)) zb[r2 * ldz + c2] = (diag ? u[r2 * (r2 + 1) / 2 + c2] : 0.0) - a2;
+        if (!diag || c0 <= r0) zb[r0 * ld + c0] = (diag ? u[r0 * (r0 + 1) / 2 + c0] : 0.0) - a0;
+        if (!diag || c1 <= r1) zb[r1 * ld + c1] = (diag ? u[r1 * (r1 + 1) / 2 + c1] : 0.0) - a1;
+        if (e2 < 81 && (!diag || c2 <= r2)) zb[r2 * ld + c2] = (diag ? u[r2 * (r2 + 1) / 2 + c2] : 0.0) - a2;
     }
 }
 
 // W7 = sum_j H_Xj^T A_j^-1 H_Xj and sum_j H_Xj^T H_Xj (for H^T H of the gauge
-// term): a fixed grid of warps, warp w summing the points j = w (mod warps);
-// lane e < 28 owns entry (p, q), p <= q.  Partial sums part[w][56].
+// term), per scene: wps warps per scene, warp q of scene s summing its points
+// po[s] + q, + 2 wps, ... (po null: one scene of m points); lane e < 28 owns
+// entry (p, q), p <= q.  Partial sums part[w][56], w = s wps + q.
 constexpr int kW7Warps = 2048;
 __global__ void __launch_bounds__(32 * kWarps)
 w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __restrict__ pts,
-                  double* __restrict__ part) {
+                  double* __restrict__ part, const int* __restrict__ po, int wps) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t sc = warp / wps, q0 = warp % wps;
+    const int64_t j0 = po ? po[sc] : 0, j1 = po ? po[sc + 1] : m;
     int w7p = 0, w7q = 0;
     {
         int e = lane, p = 0;
@@ -322,7 +339,7 @@ w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __re
     }
     double w7acc = 0.0, hhacc = 0.0;
     if (lane < 28) {
-        for (int64_t j = warp; j < m; j += kW7Warps) {
+        for (int64_t j = j0 + q0; j < j1; j += wps) {
             const double* ai = Ainv + 6 * j;
             const double Am[9] = {ai[0], ai[1], ai[2], ai[1], ai[3], ai[4], ai[2], ai[4], ai[5]};
             const double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
@@ -345,17 +362,20 @@ w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __re
     }
 }
 
-// The partial sums in warp order: W7 (upper, row-major 7x7) at W7[0, 49),
-// H_X^T H_X at W7[49, 98).  One thread per entry.
-__global__ void w7_reduce_kernel(const double* __restrict__ part, double* __restrict__ W7) {
+// The partial sums of scene s (block s) in warp order: W7 (upper, row-major
+// 7x7) at W7[128 s, 128 s + 49), H_X^T H_X at W7[128 s + 49, 128 s + 98).
+// One thread per entry.
+__global__ void w7_reduce_kernel(const double* __restrict__ part, double* __restrict__ W7, int wps) {
     const int lane = threadIdx.x;
     if (lane >= 56) return;
+    part += 56 * (int64_t)wps * blockIdx.x;
+    W7 += 128 * (int64_t)blockIdx.x;
     const int e0 = lane % 28;
     int e = e0, p = 0;
     while (p < 7 && e >= 7 - p) { e -= 7 - p; ++p; }
     const int q = p + e;
     double s = 0.0;
-    for (int w = 0; w < kW7Warps; ++w) s += part[56 * w + lane];
+    for (int w = 0; w < wps; ++w) s += part[56 * w + lane];
     W7[(lane < 28 ? 0 : 49) + 7 * p + q] = s;
 }
 
@@ -544,11 +564,14 @@ void launch_schur(Ctx& c) {
     vmat_kernel<<<(int)((c.t + 255) / 256), 256, 0, c.stream>>>(c.t, c.d_obs, c.d_W, c.d_Ainv, c.d_V);
     CCOV_LAUNCH_CHECK(c);
     schur_pairs_kernel<<<grid_for(c.npairs, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np);
+        c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np, c.d_cam_scene, c.d_scene_zo,
+        c.d_scene_ld, c.d_scene_co);
     CCOV_LAUNCH_CHECK(c);
-    w7_partial_kernel<<<kW7Warps / kWarps, 32 * kWarps, 0, c.stream>>>(c.m, c.d_Ainv, c.d_pts, c.d_w7part);
+    const int wps = kW7Warps;
+    w7_partial_kernel<<<(unsigned)(c.nscenes * wps / kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.m, c.d_Ainv, c.d_pts, c.d_w7part, c.d_scene_po, wps);
     CCOV_LAUNCH_CHECK(c);
-    w7_reduce_kernel<<<1, 64, 0, c.stream>>>(c.d_w7part, c.d_W7);
+    w7_reduce_kernel<<<c.nscenes, 64, 0, c.stream>>>(c.d_w7part, c.d_W7, wps);
     CCOV_LAUNCH_CHECK(c);
     cam_schur_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
         c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.Np,

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(GemmP g) {
                 float v[8];
                 tmem_ld8(trow + (uint32_t)c0, v);
                 tmem_wait_ld();
+                tmem_regs_after_wait<8>(v);
                 if (g.epi == EPI_RELU || g.epi == EPI_DX) {
                     if (g.epi == EPI_RELU) {
 #pragma unroll

@@ -146,6 +146,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// The registers written by tcgen05.ld hold their values only after
+// tcgen05.wait::ld, which names none of them: passing each through an empty
+// volatile statement after the wait keeps the compiler from moving any use
+// of them above it.
+template <int N>
+__device__ __forceinline__ void tmem_regs_after_wait(float* v) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 

@@ -11,8 +11,9 @@ form as one replayed graph).
   step (d) of the mixed path against the FP64 GPU path (1e-6) together with
   properties that hold at any size (symmetric, positive semi-definite
   blocks).
-- 256 sub-reconstructions of 10-300 cameras, mixed, one graph replay: the
-  smallest and the largest scenes against the oracle (1e-6)."""
+- 256 sub-reconstructions of 10-300 cameras, mixed, grouped launches replayed
+  as one graph: the smallest and the largest scenes against the oracle (1e-6),
+  and a few hundred kernels per replay."""
 import numpy as np
 import pytest
 
@@ -76,9 +77,13 @@ def test_256_subreconstructions_graph_against_oracle():
     outs = [torch.zeros((sc.n, 9, 9), dtype=torch.float64, device="cuda") for sc in scenes]
     try:
         with ccov.Batch(ctxs, outs) as b:
+            info = b.info()
             b.run()
             b.run()
             got = [o.cpu().numpy() for o in outs]
+        # the grouped form: one launch per step for all 256 scenes
+        assert info["form"] == ccov.CCOV_BATCH_GROUPED
+        assert info["launches"] < 1000
     finally:
         for c in ctxs:
             c.close()
