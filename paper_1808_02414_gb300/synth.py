@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
-           "subscene", "weak_camera_scene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
+           "subscene", "weak_camera_scene", "local_scene", "decomposition_orders", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
            "training_scene_specs", "training_scene"]
 
 
@@ -207,6 +207,39 @@ def shell_scene(n=1000, m=100_000, p_geom=1.0 / 7.0, radius=10.0, seed=1,
     ci, pi, u = _observe(rng, cams, Rs, pts, tracks, noise_px)
     return Scene(cams, pts, ci, pi, u, sigma, None,
                  {"kind": "shell", "seed": seed, "n": n, "m": m})
+
+
+def local_scene(n=200, m=20_000, p_geom=1.0 / 7.0, radius=10.0, seed=3, noise_px=1.0, sigma=1.0,
+                min_obs=5) -> Scene:
+    """A shell scene with visibility locality (as in real reconstructions,
+    where a point is seen from nearby viewpoints): n cameras with directions
+    uniform on the sphere at `radius`, looking at the origin; m points uniform
+    in the unit cube; each point's track is an anchor camera drawn uniformly
+    and the L - 1 cameras whose directions are closest to the anchor's,
+    L = 1 + Geometric(p) (min 2, mean 1/p + 1), capped at n."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    centers = radius * d
+    cams, Rs = _make_cameras(rng, centers)
+    dirs = centers / np.linalg.norm(centers, axis=1, keepdims=True)
+    near = np.argsort(-(dirs @ dirs.T), axis=1, kind="stable")     # row i: cameras by closeness to i
+    pts = rng.uniform(-0.5, 0.5, size=(m, 3))
+    lengths = np.minimum(1 + rng.geometric(p_geom, size=m), n)
+    anchors = rng.integers(0, n, size=m)
+    tracks = [near[a, :L].copy() for a, L in zip(anchors, lengths)]
+    tracks = _ensure_min_obs(rng, n, tracks, min_obs)
+    ci, pi, u = _observe(rng, cams, Rs, pts, tracks, noise_px)
+    return Scene(cams, pts, ci, pi, u, sigma, None,
+                 {"kind": "local", "seed": seed, "n": n, "m": m})
+
+
+def decomposition_orders(n: int, decompositions: int, seed=7) -> np.ndarray:
+    """Per decomposition of a scene into sub-reconstructions, the order in
+    which cameras are tried as seeds: `decompositions` seeded random
+    permutations of 0..n-1, (decompositions, n) int32."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.permutation(n) for _ in range(decompositions)]).astype(np.int32)
 
 
 def tiny_scene(n=4, m=14, track_len=3, seed=0, anisotropic=False) -> Scene:
