@@ -9,6 +9,13 @@ with X_c = R(r) X + t (the translation form of the same model), and
 Sec. 4 assumes the Jacobian J is "provided numerically"; this module obtains it
 by propagating dual numbers (value + 12 partial derivatives) through the
 projection, a derivation that does not use any hand-written derivative.
+
+The paper's own camera (Sec. 3, Sec. 4.1), model "centre8": 8 values
+{r (angle-axis), C (centre), c (focal length), k (radial)},
+    X_c = R(r) (X - C),  u_hat = c * (1 + k rho^2) * (X_c[0], X_c[1]) / X_c[2]
+(reading of Phi: divide by the third coordinate, then distort; multiplying by
+c before the division would cancel it).  The default model "rt9" is the one
+above.
 """
 from __future__ import annotations
 
@@ -16,6 +23,7 @@ import numpy as np
 
 N_CAM = 9
 N_PT = 3
+N_CAM_OF = {"rt9": 9, "centre8": 8}
 
 
 class Dual:
@@ -119,6 +127,16 @@ def project(cam, X):
     return [f * g * x, f * g * y]
 
 
+def project_centre(cam, X):
+    """u_hat of the 8-value centre camera on lists of Dual."""
+    r, C, c, k = cam[0:3], cam[3:6], cam[6], cam[7]
+    Xc = rotate(r, [X[q] - C[q] for q in range(3)])
+    x = Xc[0] / Xc[2]
+    y = Xc[1] / Xc[2]
+    g = 1.0 + k * (x * x + y * y)
+    return [c * g * x, c * g * y]
+
+
 def project_values(cams_t: np.ndarray, pts_t: np.ndarray) -> np.ndarray:
     """u_hat for paired rows of cameras (t, 9) and points (t, 3)."""
     t = cams_t.shape[0]
@@ -130,19 +148,21 @@ def project_values(cams_t: np.ndarray, pts_t: np.ndarray) -> np.ndarray:
 
 
 def jacobians(cams: np.ndarray, pts: np.ndarray, obs_cam: np.ndarray,
-              obs_pt: np.ndarray):
-    """Per observation (i, j) in S: J_c = d u_hat / d P_i (t, 2, 9) and
-    J_p = d u_hat / d X_j (t, 2, 3), by seeding 12 dual directions."""
+              obs_pt: np.ndarray, model: str = "rt9"):
+    """Per observation (i, j) in S: J_c = d u_hat / d P_i (t, 2, nc) and
+    J_p = d u_hat / d X_j (t, 2, 3), by seeding nc + 3 dual directions
+    (nc = 9 for "rt9", 8 for "centre8")."""
+    nc = N_CAM_OF[model]
     cams_t = cams[obs_cam]
     pts_t = pts[obs_pt]
     t = cams_t.shape[0]
-    k = N_CAM + N_PT
+    k = nc + N_PT
     eye = np.eye(k)
-    cam = [Dual(cams_t[:, c], np.broadcast_to(eye[c], (t, k))) for c in range(N_CAM)]
-    X = [Dual(pts_t[:, c], np.broadcast_to(eye[N_CAM + c], (t, k))) for c in range(N_PT)]
-    u = project(cam, X)
-    J = np.stack([u[0].d, u[1].d], axis=1)          # (t, 2, 12)
-    return J[:, :, :N_CAM].copy(), J[:, :, N_CAM:].copy()
+    cam = [Dual(cams_t[:, c], np.broadcast_to(eye[c], (t, k))) for c in range(nc)]
+    X = [Dual(pts_t[:, c], np.broadcast_to(eye[nc + c], (t, k))) for c in range(N_PT)]
+    u = (project_centre if model == "centre8" else project)(cam, X)
+    J = np.stack([u[0].d, u[1].d], axis=1)          # (t, 2, nc + 3)
+    return J[:, :, :nc].copy(), J[:, :, nc:].copy()
 
 
 def rotation_matrix(r: np.ndarray) -> np.ndarray:

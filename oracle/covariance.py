@@ -25,7 +25,7 @@ from . import camera, information, nullspace
 def _scales(U, A, HP, HX, mode):
     n, m = U.shape[0], A.shape[0]
     if mode == "none":
-        sP, sX, sb = np.ones((n, 9)), np.ones((m, 3)), np.ones(7)
+        sP, sX, sb = np.ones((n, U.shape[1])), np.ones((m, 3)), np.ones(7)
     elif mode == "jacobi":
         sP = 1.0 / np.sqrt(np.einsum("nii->ni", U))
         sX = 1.0 / np.sqrt(np.einsum("mii->mi", A))
@@ -48,7 +48,8 @@ def schur_system(scene, scaling="jacobi"):
 
 def _schur_from_blocks(scene, U, A, W, HP, HX, scaling):
     n, m, t = scene.n, scene.m, scene.t
-    N = 9 * n
+    nc = U.shape[1]
+    N = nc * n
     sP, sX, sb = _scales(U, A, HP, HX, scaling)
     # conditioned blocks: S_a M S_a and S_a H S_b
     Us = sP[:, :, None] * U * sP[:, None, :]
@@ -62,8 +63,8 @@ def _schur_from_blocks(scene, U, A, W, HP, HX, scaling):
     jj = (3 * np.arange(m)[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
     Ap_inv = sp.csr_matrix((Ainv.ravel(), (ii.ravel(), jj.ravel())), shape=(3 * m, 3 * m))
     # B_p = [M_XP, H_X]: rows of points, columns of cameras then the 7 of H
-    r = (3 * scene.obs_pt[:, None, None] + np.arange(3)[None, :, None]).repeat(9, 2)
-    c = (9 * scene.obs_cam[:, None, None] + np.arange(9)[None, None, :]).repeat(3, 1)
+    r = (3 * scene.obs_pt[:, None, None] + np.arange(3)[None, :, None]).repeat(nc, 2)
+    c = (nc * scene.obs_cam[:, None, None] + np.arange(nc)[None, None, :]).repeat(3, 1)
     rh = (np.arange(3 * m)[:, None]).repeat(7, 1)
     ch = (N + np.arange(7)[None, :]).repeat(3 * m, 0)
     Bp = sp.csr_matrix((np.concatenate([Ws.transpose(0, 2, 1).ravel(), HXs.reshape(-1, 7).ravel()]),
@@ -73,7 +74,7 @@ def _schur_from_blocks(scene, U, A, W, HP, HX, scaling):
     # D_p = [M_PP, H_P; H_P^T, 0]
     Dp = np.zeros((N + 7, N + 7))
     for i in range(n):
-        Dp[9 * i:9 * i + 9, 9 * i:9 * i + 9] = Us[i]
+        Dp[nc * i:nc * i + nc, nc * i:nc * i + nc] = Us[i]
     Dp[:N, N:] = HPs.reshape(N, 7)
     Dp[N:, :N] = HPs.reshape(N, 7).T
     Zp = Dp - (Bp.T @ (Ap_inv @ Bp)).toarray()
@@ -86,7 +87,7 @@ def schur_blocks_unscaled(scene):
     for the unconditioned system: Z = M_PP - M_PX A^-1 M_XP,
     G = H_P - M_PX A^-1 H_X, W7 = H_X^T A^-1 H_X."""
     Zp, _ = schur_system(scene, scaling="none")
-    N = 9 * scene.n
+    N = Zp.shape[0] - 7
     return Zp[:N, :N], Zp[:N, N:], -Zp[N:, N:]
 
 
@@ -142,10 +143,12 @@ def schur_rows_unscaled(scene, cams):
 
 
 def camera_covariance(scene, scaling="jacobi", full=False):
-    """Sigma_P = S_P Z_s S_P, Z_s the top-left 9n x 9n block of Z_p^-1.
-    Returns the diagonal 9x9 blocks (n, 9, 9), or the whole 9n x 9n matrix."""
+    """Sigma_P = S_P Z_s S_P, Z_s the top-left nc n x nc n block of Z_p^-1
+    (nc = 9, or 8 for the centre camera).  Returns the diagonal blocks
+    (n, nc, nc), or the whole nc n x nc n matrix."""
     Zp, scale = schur_system(scene, scaling)
-    N = 9 * scene.n
+    N = Zp.shape[0] - 7
+    nc = N // scene.n
     lu = sla.lu_factor(Zp, check_finite=True)
     E = np.zeros((N + 7, N))
     E[np.arange(N), np.arange(N)] = 1.0
@@ -156,4 +159,4 @@ def camera_covariance(scene, scaling="jacobi", full=False):
     if full:
         return Sigma
     n = scene.n
-    return np.stack([Sigma[9 * i:9 * i + 9, 9 * i:9 * i + 9] for i in range(n)])
+    return np.stack([Sigma[nc * i:nc * i + nc, nc * i:nc * i + nc] for i in range(n)])

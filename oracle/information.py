@@ -20,14 +20,20 @@ def obs_information(scene) -> np.ndarray:
     return np.linalg.inv(scene.obs_cov)
 
 
+def model(scene) -> str:
+    return getattr(scene, "model", "rt9")
+
+
 def blocks(scene, Jc=None, Jp=None):
-    """Returns U (n,9,9), A (m,3,3), W (t,9,3) and the Jacobians."""
+    """Returns U (n,nc,nc), A (m,3,3), W (t,nc,3) and the Jacobians (nc = 9, or
+    8 for the centre camera)."""
     if Jc is None:
-        Jc, Jp = camera.jacobians(scene.cams, scene.pts, scene.obs_cam, scene.obs_pt)
+        Jc, Jp = camera.jacobians(scene.cams, scene.pts, scene.obs_cam, scene.obs_pt, model(scene))
+    nc = Jc.shape[2]
     Wu = obs_information(scene)
-    JcW = np.einsum("tab,tbc->tac", Jc.transpose(0, 2, 1), Wu)   # (t, 9, 2)
+    JcW = np.einsum("tab,tbc->tac", Jc.transpose(0, 2, 1), Wu)   # (t, nc, 2)
     JpW = np.einsum("tab,tbc->tac", Jp.transpose(0, 2, 1), Wu)   # (t, 3, 2)
-    U = np.zeros((scene.n, 9, 9))
+    U = np.zeros((scene.n, nc, nc))
     np.add.at(U, scene.obs_cam, np.einsum("tab,tbc->tac", JcW, Jc))
     A = np.zeros((scene.m, 3, 3))
     np.add.at(A, scene.obs_pt, np.einsum("tab,tbc->tac", JpW, Jp))
@@ -36,15 +42,16 @@ def blocks(scene, Jc=None, Jp=None):
 
 
 def dense_jacobian(scene, Jc=None, Jp=None) -> np.ndarray:
-    """J as a dense (2t) x (9n + 3m) matrix, cameras first (tiny scenes only)."""
+    """J as a dense (2t) x (nc n + 3m) matrix, cameras first (tiny scenes only)."""
     if Jc is None:
-        Jc, Jp = camera.jacobians(scene.cams, scene.pts, scene.obs_cam, scene.obs_pt)
+        Jc, Jp = camera.jacobians(scene.cams, scene.pts, scene.obs_cam, scene.obs_pt, model(scene))
     n, m, t = scene.n, scene.m, scene.t
-    J = np.zeros((2 * t, 9 * n + 3 * m))
+    nc = Jc.shape[2]
+    J = np.zeros((2 * t, nc * n + 3 * m))
     for o in range(t):
         i, j = scene.obs_cam[o], scene.obs_pt[o]
-        J[2 * o:2 * o + 2, 9 * i:9 * i + 9] = Jc[o]
-        J[2 * o:2 * o + 2, 9 * n + 3 * j:9 * n + 3 * j + 3] = Jp[o]
+        J[2 * o:2 * o + 2, nc * i:nc * i + nc] = Jc[o]
+        J[2 * o:2 * o + 2, nc * n + 3 * j:nc * n + 3 * j + 3] = Jp[o]
     return J
 
 

@@ -10,6 +10,10 @@ the transformed parameters,
     X' = X + omega x X + dmu X + dT           ->  H_X = [I, -[X]_x, X]
     t' = (1 + dmu) t - R dT                   ->  H_t = [-R, 0, t]
     f, k1, k2 unchanged                       ->  zero rows.
+For the paper's centre camera (model "centre8", Sec. 4.1):
+    C' = C + omega x C + dmu C + dT           ->  H_C = [I, -[C]_x, C]
+(the paper's [I, [C]_x, C] up to the sign of the omega columns), c and k
+unchanged -> zero rows.
 The rotation rows H_r are not linear in s; as in Eq. rotation-nullspace-
 equation they are obtained from J H = 0: for camera i, J_r H_r = B with J_r
 the columns of J for r_i on the rows of camera i's observations and B minus
@@ -43,22 +47,30 @@ def point_rows(pts: np.ndarray) -> np.ndarray:
     return H
 
 
+def _position_rows(scene, i: int) -> np.ndarray:
+    """Rows of H for the position values of camera i (3, 7)."""
+    if getattr(scene, "model", "rt9") == "centre8":
+        C = scene.cams[i, 3:6]
+        return np.concatenate([np.eye(3), -skew(C), C[:, None]], 1)
+    R = camera.rotation_matrix(scene.cams[i, 0:3])
+    return np.concatenate([-R, np.zeros((3, 3)), scene.cams[i, 3:6, None]], 1)
+
+
 def camera_rows(scene, Jc: np.ndarray, Jp: np.ndarray) -> np.ndarray:
-    """H_P (n, 9, 7): translation rows in closed form, rotation rows from the
+    """H_P (n, nc, 7): position rows in closed form, rotation rows from the
     per-camera system J_r H_r = B (least squares over the camera's rows)."""
     n = scene.n
+    nc = Jc.shape[2]
     HX = point_rows(scene.pts)
-    H = np.zeros((n, 9, 7))
+    H = np.zeros((n, nc, 7))
     for i in range(n):
-        R = camera.rotation_matrix(scene.cams[i, 0:3])
-        H[i, 3:6, 0:3] = -R
-        H[i, 3:6, 6] = scene.cams[i, 3:6]
+        H[i, 3:6] = _position_rows(scene, i)
     obs = np.argsort(scene.obs_cam, kind="stable")
     starts = np.searchsorted(scene.obs_cam[obs], np.arange(n + 1))
     for i in range(n):
         rows = obs[starts[i]:starts[i + 1]]
         Jr = Jc[rows][:, :, 0:3].reshape(-1, 3)                     # (2 t_i, 3)
-        other = (np.einsum("tab,bc->tac", Jc[rows][:, :, 3:9], H[i, 3:9])
+        other = (np.einsum("tab,bc->tac", Jc[rows][:, :, 3:nc], H[i, 3:nc])
                  + np.einsum("tab,tbc->tac", Jp[rows], HX[scene.obs_pt[rows]]))
         B = -other.reshape(-1, 7)
         H[i, 0:3], *_ = np.linalg.lstsq(Jr, B, rcond=None)
@@ -82,15 +94,14 @@ def camera_rows_closed_form(scene) -> np.ndarray:
     solution of J_r H_r = B for the angle-axis parametrisation (a cross-check
     of the per-camera solve, not used by the oracle's covariance)."""
     n = scene.n
-    H = np.zeros((n, 9, 7))
+    nc = camera.N_CAM_OF[getattr(scene, "model", "rt9")]
+    H = np.zeros((n, nc, 7))
     for i in range(n):
-        R = camera.rotation_matrix(scene.cams[i, 0:3])
         H[i, 0:3, 3:6] = -right_jacobian_inverse(scene.cams[i, 0:3])
-        H[i, 3:6, 0:3] = -R
-        H[i, 3:6, 6] = scene.cams[i, 3:6]
+        H[i, 3:6] = _position_rows(scene, i)
     return H
 
 
 def dense_nullspace(scene, HP: np.ndarray) -> np.ndarray:
-    """H as a dense (9n + 3m) x 7 matrix, cameras first."""
+    """H as a dense (nc n + 3m) x 7 matrix, cameras first."""
     return np.concatenate([HP.reshape(-1, 7), point_rows(scene.pts).reshape(-1, 7)], 0)

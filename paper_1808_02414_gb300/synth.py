@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
-           "subscene", "weak_camera_scene", "local_scene", "decomposition_orders", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
+           "subscene", "weak_camera_scene", "local_scene", "decomposition_orders", "centre_scene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
            "training_scene_specs", "training_scene"]
 
 
@@ -33,6 +33,7 @@ class Scene:
     sigma: float = 1.0
     obs_cov: np.ndarray | None = None   # (t, 2, 2) float64 or None (sigma^2 I)
     meta: dict = field(default_factory=dict)
+    model: str = "rt9"        # "rt9": (r, t, f, k1, k2); "centre8": (r, C, c, k), cams (n, 8)
 
     @property
     def n(self) -> int:
@@ -232,6 +233,24 @@ def local_scene(n=200, m=20_000, p_geom=1.0 / 7.0, radius=10.0, seed=3, noise_px
     ci, pi, u = _observe(rng, cams, Rs, pts, tracks, noise_px)
     return Scene(cams, pts, ci, pi, u, sigma, None,
                  {"kind": "local", "seed": seed, "n": n, "m": m})
+
+
+def centre_scene(sc: Scene) -> Scene:
+    """The same cameras and points in the paper's 8-value parametrisation
+    {r, C, c, k} (Sec. 3): C = -R^T t, c = f, k = k1 (k2 dropped).  The
+    observations are kept: they do not enter the covariance."""
+    cams = np.zeros((sc.n, 8))
+    for i in range(sc.n):
+        th = np.linalg.norm(sc.cams[i, 0:3])
+        K = np.array([[0.0, -sc.cams[i, 2], sc.cams[i, 1]], [sc.cams[i, 2], 0.0, -sc.cams[i, 0]],
+                      [-sc.cams[i, 1], sc.cams[i, 0], 0.0]])
+        R = np.eye(3) + np.sin(th) / th * K + (1.0 - np.cos(th)) / th ** 2 * K @ K
+        cams[i, 0:3] = sc.cams[i, 0:3]
+        cams[i, 3:6] = -R.T @ sc.cams[i, 3:6]
+        cams[i, 6] = sc.cams[i, 6]
+        cams[i, 7] = sc.cams[i, 7]
+    return Scene(cams, sc.pts, sc.obs_cam, sc.obs_pt, sc.obs_u, sc.sigma, sc.obs_cov,
+                 dict(sc.meta, model="centre8"), "centre8")
 
 
 def decomposition_orders(n: int, decompositions: int, seed=7) -> np.ndarray:
