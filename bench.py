@@ -142,6 +142,26 @@ def traffic_for(kernel_tag: str, flops_per_launch: float):
     return rec["dram_bytes_per_flop"] * flops_per_launch
 
 
+def block_errors(S, R, cams=None):
+    """Per-block error measures of S against R ((n, 9, 9) arrays): relative
+    Frobenius of the block, of the block scaled by diag(R)^-1/2, of its 6x6
+    pose and 3x3 intrinsic sub-blocks, and (with `cams`) the paper's err
+    (Sec. 6: mean over the entries of sqrt(|S - R|) / O, O = sqrt(E|P| E|P|^T))."""
+    import numpy as np
+
+    def fro(a, b):
+        return np.linalg.norm(a - b, axis=(-2, -1)) / np.linalg.norm(b, axis=(-2, -1))
+
+    d = 1.0 / np.sqrt(np.abs(np.einsum("...ii->...i", R)))
+    Dd = d[..., :, None] * d[..., None, :]
+    out = {"rel_fro": fro(S, R), "norm_err": fro(S * Dd, R * Dd), "pose_err": fro(S[:, :6, :6], R[:, :6, :6]),
+           "intr_err": fro(S[:, 6:, 6:], R[:, 6:, 6:])}
+    if cams is not None:
+        e = np.abs(cams).mean(axis=0)
+        out["paper_err"] = (np.sqrt(np.abs(S - R)) / np.sqrt(np.outer(e, e))).mean(axis=(-2, -1))
+    return out
+
+
 def dist_init(n_gpus: int):
     import torch
     if n_gpus > 1 or "RANK" in os.environ:
@@ -386,8 +406,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms64 = g0.elapsed_time(g1)
         ref = ref.cpu().numpy()
-        from oracle import metrics
-        errs = metrics.all_errors(mixed, ref)
+        errs = block_errors(mixed, ref)
         line["vs_fp64_gpu"] = {"ms_per_step": ms64, "value": scene.n / (ms64 / 1e3), "unit": UNIT,
                                "speedup_of_mixed": ms64 / ms_step,
                                "max_rel_fro_per_block": float(errs["rel_fro"].max()),
@@ -635,14 +654,37 @@ def _solve_group(scenes, F, TG, ccov, surrogate, torch, LZ=None, SG=None):
             c.close()
 
 
-def _surrogate_accuracy(sm, f, L, truth, S):
+def _gaussian_kl(pred, true):
+    """KL(N(0, true) || N(0, pred)) per 9x9 block (unit-free error measure)."""
+    import numpy as np
+    Pi = np.linalg.inv(pred)
+    return 0.5 * (np.einsum("iab,iba->i", Pi, true) - true.shape[1] + np.linalg.slogdet(pred)[1]
+                  - np.linalg.slogdet(true)[1])
+
+
+def _cov_from_target(t, Lz):
+    """Sigma = L_z^-T L L^T L_z^-1 for network outputs t in the Cholesky
+    target form (9 log-diagonal entries, then the strict lower triangle row
+    by row), as the surrogate decodes them."""
+    import numpy as np
+    n = t.shape[0]
+    L = np.zeros((n, 9, 9))
+    k = np.arange(9)
+    L[:, k, k] = np.exp(t[:, :9])
+    il = np.tril_indices(9, -1)
+    L[:, il[0], il[1]] = t[:, 9:]
+    Li = np.linalg.inv(Lz)
+    return Li.transpose(0, 2, 1) @ (L @ L.transpose(0, 2, 1)) @ Li
+
+
+def _surrogate_accuracy(sm, f, L, truth):
     import numpy as np
     pred = sm.predict(f, __import__("torch").from_numpy(L).cuda()).cpu().numpy()
     mu_t = sm.normalization()[128:173].astype(np.float64)
     n = L.shape[0]
-    kl = {"surrogate": S.gaussian_kl(pred, truth),
-          "local_block_inverse": S.gaussian_kl(S.covariance_from_output(np.zeros((n, 45)), L), truth),
-          "constant_correction": S.gaussian_kl(S.covariance_from_output(np.tile(mu_t, (n, 1)), L), truth)}
+    kl = {"surrogate": _gaussian_kl(pred, truth),
+          "local_block_inverse": _gaussian_kl(_cov_from_target(np.zeros((n, 45)), L), truth),
+          "constant_correction": _gaussian_kl(_cov_from_target(np.tile(mu_t, (n, 1)), L), truth)}
     out = {k: {"median_kl": float(np.median(v)), "p90_kl": float(np.percentile(v, 90))} for k, v in kl.items()}
     out["surrogate"]["median_rel_fro"] = float(np.median(
         np.linalg.norm(pred - truth, axis=(1, 2)) / np.linalg.norm(truth, axis=(1, 2))))
@@ -654,7 +696,6 @@ def run_surrogate(args):
     import numpy as np
     import torch
 
-    from oracle import surrogate as S
     from paper_1808_02414_gb300 import ccov, surrogate, synth
 
     rank, world, local = dist_init(args.gpus)
@@ -678,7 +719,7 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
     ms_train_step = train_ms / steps
-    accuracy = {"heldout_scenes_50_500_cams": _surrogate_accuracy(sm, *held, S)}
+    accuracy = {"heldout_scenes_50_500_cams": _surrogate_accuracy(sm, *held)}
 
     # evaluation on the 4000-camera scene: exact blocks from the mixed path
     scene = synth.workload("shell4k")
@@ -727,7 +768,7 @@ def run_surrogate(args):
     ms_e2e = e0.elapsed_time(e1)
     ctx_h.close()
 
-    accuracy["shell4k_4000_cams"] = _surrogate_accuracy(sm, f, lz.cpu().numpy(), exact.cpu().numpy(), S)
+    accuracy["shell4k_4000_cams"] = _surrogate_accuracy(sm, f, lz.cpu().numpy(), exact.cpu().numpy())
     ctx.close()
 
     # executed tensor flops of one training step (padded widths 128/256/256/256/128)
@@ -758,6 +799,7 @@ def run_surrogate(args):
                          "loss_last": float(losses[-50:].mean())},
             "accuracy_vs_exact": accuracy}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import surrogate as S
         sub = synth.subscene(scene, np.arange(300))
         t0 = time.perf_counter()
         f_o, lz_o = S.features(sub)
@@ -771,12 +813,63 @@ def run_surrogate(args):
         print(json.dumps(line), flush=True)
 
 
+def run_subrecon(args):
+    """Sec. 5 pipeline on a 1000-camera scene with visibility locality: the
+    cameras' covariances from sub-reconstructions of k = 100 view-graph
+    neighbours, three decompositions, minimum-trace merge; error against the
+    full scene's covariances (mixed form)."""
+    import numpy as np
+    import torch
+
+    from paper_1808_02414_gb300 import ccov, synth
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    scene = synth.local_scene(n=1000, m=100_000, seed=3)
+    k, D = 100, 3
+    orders = synth.decomposition_orders(scene.n, D, seed=7)
+    for _ in range(args.warmup):
+        ccov.subrecon_covariances(scene, k, orders)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out, cover, nsub = ccov.subrecon_covariances(scene, k, orders)
+    torch.cuda.synchronize()
+    ms_step = barrier_max(1e3 * (time.perf_counter() - t0), world) / args.steps
+    clk = clocks.stop()
+    full = ccov.camera_covariances(scene, precision=ccov.CCOV_PREC_MIXED)
+    errs = block_errors(out, full, scene.cams)
+    value = scene.n * world / (ms_step / 1e3)
+    line = {"metric": "camera covariances/s (sub-reconstructions of a 1000-camera scene)", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "subrecon", "cameras": scene.n, "points": scene.m, "observations": scene.t,
+                       "cams_per_sub": k, "decompositions": D, "sub_reconstructions": int(nsub),
+                       "step": "ccov_subrecon_covariance from host inputs: plan, extraction, contexts, "
+                               "grouped batch, merge (host clock around the call)"},
+            "clocks": clk,
+            "e2e": {"value": value, "unit": UNIT,
+                    "h2d_bytes_per_step": scene.cams.nbytes + scene.pts.nbytes + scene.t * 24,
+                    "d2h_bytes_per_step": scene.n * 81 * 8, "ms_per_step": ms_step},
+            "gpu_launches": None,
+            "error_vs_full_scene": {k2: {"median": float(np.median(v)), "mean": float(np.mean(v)),
+                                         "p90": float(np.percentile(v, 90))} for k2, v in errs.items()},
+            "cover": {"min": int(cover.min()), "mean": float(cover.mean())}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "subrecon":
+        run_subrecon(args)
     elif args.workload == "surrogate":
         run_surrogate(args)
     else:

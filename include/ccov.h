@@ -71,10 +71,16 @@ typedef enum {
 enum { CCOV_PREC_FP64 = 0, CCOV_PREC_MIXED = 1 };
 enum { CCOV_MEM_HOST = 0, CCOV_MEM_DEVICE = 1 };
 enum { CCOV_NULL_PAPER = 0, CCOV_NULL_CLOSED = 1 };
+enum { CCOV_GAUGE_NATURAL = 0, CCOV_GAUGE_ZPINV = 1, CCOV_GAUGE_FIXED3 = 2 };
+enum { CCOV_CAMERA_RT9 = 0, CCOV_CAMERA_CENTRE8 = 1 };
 
 typedef struct {
     int precision;        /* CCOV_PREC_FP64 (default) or CCOV_PREC_MIXED */
-    int mixed_slices;     /* MIXED only: 8-bit digit slices per operand, 4..6; 0 = 5 */
+    int mixed_slices;     /* MIXED only: 8-bit digit slices per operand, 4..6; 0 = 5 for
+                             the natural gauge with the 9-value camera, 6 for
+                             CCOV_GAUGE_ZPINV / _FIXED3 and CCOV_CAMERA_CENTRE8, whose
+                             Jacobi-scaled matrices have condition numbers near 2e6
+                             (2e4 otherwise) */
     int nullspace_route;  /* CCOV_NULL_PAPER: rotation rows from J_r H_r = B (Sec. 4.1,
                              Eq. rotation-nullspace-equation), default;
                              CCOV_NULL_CLOSED: -J_r^-1(r) in closed form */
@@ -84,7 +90,28 @@ typedef struct {
                              events and report their time in ccov_stats */
     int est_cameras;      /* cameras sampled by the error estimate of ccov_covariance
                              (only when its est_rel_err is not NULL): 1..16, 0 = 4 */
-    int reserved[6];      /* set to zero */
+    int gauge;            /* CCOV_GAUGE_NATURAL (default): the method of the paper, the
+                             camera block of the natural covariance [M+]_PP;
+                             CCOV_GAUGE_ZPINV: Alg. 4 of Table 2, the Moore-Penrose
+                             inverse of the reduced camera matrix Z (projected onto the
+                             complement of the similarity nullspace, which leaves it
+                             unchanged); CCOV_GAUGE_FIXED3: Alg. 5 of Table 2, three
+                             points taken out of the parameters, the inverse of the
+                             full-rank Schur complement of the others (computed exactly) */
+    int fixed_points[3];  /* CCOV_GAUGE_FIXED3: the three point indices; all three -1 (or
+                             all 0): the point farthest from the centroid of the points,
+                             the point farthest from it, the point farthest from the line
+                             through those two (ties: the smaller index) */
+    int camera_model;     /* CCOV_CAMERA_RT9 (default): 9 values per camera, as above;
+                             CCOV_CAMERA_CENTRE8: the paper's camera of Sec. 3 and
+                             Sec. 4.1, 8 values {r, C, c, k} with X_c = R(r) (X - C),
+                             u = c (1 + k rho^2) (X_c[0], X_c[1]) / X_c[2]; `cameras` is
+                             then n x 8 (ccov_create, ccov_load), and each returned 9x9
+                             block holds the 8x8 covariance of (r, C, c, k) in its
+                             top-left corner, its 9th row and column those of an
+                             uncorrelated dummy value of variance 1 (a unit prior on a
+                             parameter that no observation sees) */
+    int reserved[1];      /* set to zero */
 } ccov_options;
 
 /* Per-context counters of the last calls (device times from CUDA events). */
@@ -254,7 +281,8 @@ CCOV_API void ccov_batch_destroy(ccov_batch* batch);
  *   CCOV_BATCH_PER_SCENE: every context's own steps, forked onto the
  *     contexts' streams and joined back (any precision, any options).
  *   CCOV_BATCH_AUTO: grouped when the contexts allow it, else per scene. */
-enum { CCOV_BATCH_AUTO = 0, CCOV_BATCH_PER_SCENE = 1, CCOV_BATCH_GROUPED = 2 };
+enum { CCOV_BATCH_AUTO = 0, CCOV_BATCH_PER_SCENE = 1, CCOV_BATCH_GROUPED = 2,
+       CCOV_BATCH_NO_TUNE = 8 /* or-ed into the form: keep the default launch shape, no tuning passes */ };
 CCOV_API ccov_status ccov_batch_create_ex(ccov_ctx* const* ctxs, int k, double* const* outs_device, int form,
                                           ccov_batch** out);
 
@@ -266,6 +294,50 @@ typedef struct {
     double tune_ms;         /* grouped: the batch time of the chosen shape while tuning */
 } ccov_batch_info;
 CCOV_API ccov_status ccov_batch_get_info(const ccov_batch* batch, ccov_batch_info* out);
+
+/* Uncertainty from sub-reconstructions, Sec. 5: a camera's uncertainty is
+ * evaluated from a sub-reconstruction of the cameras and points around it;
+ * each evaluation bounds it from above; the scene is decomposed several times
+ * and per camera the covariance with the smallest trace is kept (Sec. 6 uses
+ * the 100 neighbours of a camera in the view graph).
+ *   view graph  cameras i, k adjacent, weight = the number of points both see
+ *   neighbourhood of a seed camera: grown one camera at a time, adding the
+ *               camera with the largest total weight to those chosen (ties:
+ *               the smaller index), until cams_per_sub cameras or none left
+ *   decomposition d: cameras tried as seeds in the order seed_order[d][.];
+ *               a camera already in a neighbourhood of d is skipped, so each
+ *               decomposition covers every camera
+ *   sub-reconstruction: the neighbourhood's cameras, the points at least two
+ *               of them see and those observations, then cameras and points
+ *               with fewer than two observations dropped until none is left
+ *   merge:      per camera, the 9x9 block of smallest trace over the
+ *               sub-reconstructions that hold it */
+typedef struct {
+    int cams_per_sub;           /* cameras per neighbourhood, >= 2 */
+    int decompositions;         /* >= 1 */
+    const int32_t* seed_order;  /* host, decompositions x n: each row a permutation of 0..n-1 */
+} ccov_subrecon_options;
+
+/* The camera sets of the sub-reconstructions, in order (decomposition by
+ * decomposition), as CSR: sub s holds sub_cams[sub_ptr[s] .. sub_ptr[s+1]),
+ * ascending.  obs as for ccov_create (sorted by point).  *nsub and *total are
+ * always written; INVALID_ARG (nothing else written) if max_subs or max_total
+ * is too small (NULL buffers with 0 capacities: a size query). */
+CCOV_API ccov_status ccov_subrecon_plan(const ccov_obs* obs, int64_t t, int64_t n, int64_t m,
+                                        const ccov_subrecon_options* sopt, int64_t max_subs, int64_t max_total,
+                                        int32_t* sub_ptr, int32_t* sub_cams, int64_t* nsub, int64_t* total);
+
+/* The whole pipeline: plan, extraction, the covariances of all
+ * sub-reconstructions as one batch (grouped launches for precision MIXED),
+ * merge.  Inputs as for ccov_create, host memory; opt applies to every
+ * sub-reconstruction.  out: host n x 81, the merged blocks (NaN for a camera
+ * that no usable sub-reconstruction holds); cover: NULL or n int32, how many
+ * sub-reconstructions held each camera; nsub: NULL or the number solved.
+ * A degenerate sub-reconstruction is skipped. */
+CCOV_API ccov_status ccov_subrecon_covariance(const double* cameras, int64_t n, const double* points, int64_t m,
+                                              const ccov_obs* obs, int64_t t, double sigma, const double* obs_cov,
+                                              const ccov_options* opt, const ccov_subrecon_options* sopt,
+                                              double* out, int32_t* cover, int64_t* nsub);
 
 /* Allocation-free entry point (the paper has no counterpart).  For callers that
  * cannot call cudaMalloc: a real-time loop that must not allocate, or code in a

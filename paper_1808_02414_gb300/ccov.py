@@ -23,13 +23,16 @@ CCOV_ERR_TIMEOUT, CCOV_ERR_OOM, CCOV_ERR_CUDA = 4, 5, 6
 CCOV_PREC_FP64, CCOV_PREC_MIXED = 0, 1
 CCOV_MEM_HOST, CCOV_MEM_DEVICE = 0, 1
 CCOV_NULL_PAPER, CCOV_NULL_CLOSED = 0, 1
-CCOV_BATCH_AUTO, CCOV_BATCH_PER_SCENE, CCOV_BATCH_GROUPED = 0, 1, 2
+CCOV_BATCH_AUTO, CCOV_BATCH_PER_SCENE, CCOV_BATCH_GROUPED, CCOV_BATCH_NO_TUNE = 0, 1, 2, 8
+CCOV_GAUGE_NATURAL, CCOV_GAUGE_ZPINV, CCOV_GAUGE_FIXED3 = 0, 1, 2
+CCOV_CAMERA_RT9, CCOV_CAMERA_CENTRE8 = 0, 1
 
 EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_nullspace",
             "ccov_covariance", "ccov_get_blocks", "ccov_get_schur", "ccov_get_schur_blocks", "ccov_get_stats",
             "ccov_destroy", "ccov_status_string", "ccov_last_error",
             "ccov_spd_inverse_blocks_noalloc", "ccov_batch_covariance", "ccov_batch_create",
-            "ccov_batch_create_ex", "ccov_batch_get_info", "ccov_batch_run", "ccov_batch_destroy"]
+            "ccov_batch_create_ex", "ccov_batch_get_info", "ccov_batch_run", "ccov_batch_destroy",
+            "ccov_subrecon_plan", "ccov_subrecon_covariance"]
 
 
 class CcovError(RuntimeError):
@@ -41,7 +44,8 @@ class CcovError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("mixed_slices", C.c_int), ("nullspace_route", C.c_int),
                 ("input_memory", C.c_int), ("profile", C.c_int), ("est_cameras", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("gauge", C.c_int), ("fixed_points", C.c_int * 3), ("camera_model", C.c_int),
+                ("reserved", C.c_int * 1)]
 
 
 class Stats(C.Structure):
@@ -59,6 +63,10 @@ class Stats(C.Structure):
         for name in ("est_index", "est_rel", "est_norm"):
             d[name] = list(d[name])[:k]
         return d
+
+
+class SubreconOptions(C.Structure):
+    _fields_ = [("cams_per_sub", C.c_int), ("decompositions", C.c_int), ("seed_order", C.c_void_p)]
 
 
 class BatchInfo(C.Structure):
@@ -103,6 +111,10 @@ def load() -> C.CDLL:
         "ccov_batch_create": ([P, I, P, C.POINTER(C.c_void_p)], I),
         "ccov_batch_create_ex": ([P, I, P, I, C.POINTER(C.c_void_p)], I),
         "ccov_batch_get_info": ([P, C.POINTER(BatchInfo)], I),
+        "ccov_subrecon_plan": ([P, I64, I64, I64, C.POINTER(SubreconOptions), I64, I64, P, P,
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int64)], I),
+        "ccov_subrecon_covariance": ([P, I64, P, I64, P, I64, D, P, P, C.POINTER(SubreconOptions), P, P,
+                                      C.POINTER(C.c_int64)], I),
         "ccov_batch_run": ([P, P], I),
         "ccov_batch_destroy": ([P], None),
         "ccov_surrogate_features": ([P, P, P], I),
@@ -159,7 +171,8 @@ class Context:
     """One scene on the device (ccov_ctx).  Method names follow the C ABI."""
 
     def __init__(self, cameras, points, obs, sigma=1.0, obs_cov=None, precision=CCOV_PREC_FP64,
-                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None, profile=False, est_cameras=0):
+                 mixed_slices=0, nullspace_route=CCOV_NULL_PAPER, stream=None, profile=False, est_cameras=0,
+                 gauge=CCOV_GAUGE_NATURAL, fixed_points=(-1, -1, -1), camera_model=CCOV_CAMERA_RT9):
         L = load()
         dev = _is_device(cameras)
         if not dev:
@@ -170,7 +183,8 @@ class Context:
         n, m = int(cameras.shape[0]), int(points.shape[0])
         t = int(obs.shape[0]) if not dev else int(obs.numel() // 24)
         opt = Options(precision, mixed_slices, nullspace_route,
-                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST, 1 if profile else 0, est_cameras)
+                      CCOV_MEM_DEVICE if dev else CCOV_MEM_HOST, 1 if profile else 0, est_cameras, gauge,
+                      (C.c_int * 3)(*fixed_points), camera_model)
         h = C.c_void_p()
         s = L.ccov_create(_ptr(cameras), n, _ptr(points), m, _ptr(obs), t, float(sigma),
                           _ptr(obs_cov), C.byref(opt), stream, C.byref(h))
@@ -264,6 +278,8 @@ class Context:
 
 
 def from_scene(scene, **kw) -> Context:
+    if getattr(scene, "model", "rt9") == "centre8":
+        kw.setdefault("camera_model", CCOV_CAMERA_CENTRE8)
     return Context(scene.cams, scene.pts, scene.obs_records(), scene.sigma,
                    None if scene.obs_cov is None else scene.obs_cov.reshape(-1, 4), **kw)
 
@@ -338,3 +354,48 @@ def camera_covariances(scene, **kw) -> np.ndarray:
     """Per-camera 9x9 covariance blocks of a scene through the C ABI."""
     with from_scene(scene, **kw) as ctx:
         return ctx.run()
+
+
+def _subrecon_opts(k: int, orders: np.ndarray):
+    orders = np.ascontiguousarray(orders, dtype=np.int32)
+    return SubreconOptions(int(k), int(orders.shape[0]), orders.ctypes.data), orders
+
+
+def subrecon_plan(scene, k: int, orders) -> list[list[int]]:
+    """ccov_subrecon_plan: the camera sets of the sub-reconstructions (Sec. 5)."""
+    L = load()
+    so, keep = _subrecon_opts(k, orders)
+    rec = scene.obs_records()
+    nsub, total = C.c_int64(), C.c_int64()
+    s = L.ccov_subrecon_plan(rec.ctypes.data, scene.t, scene.n, scene.m, C.byref(so), 0, 0, None, None,
+                             C.byref(nsub), C.byref(total))
+    if s not in (CCOV_OK, CCOV_ERR_INVALID_ARG) or nsub.value == 0:
+        raise CcovError(s, "ccov_subrecon_plan")
+    ptr = np.empty(nsub.value + 1, np.int32)
+    cams = np.empty(max(total.value, 1), np.int32)
+    s = L.ccov_subrecon_plan(rec.ctypes.data, scene.t, scene.n, scene.m, C.byref(so), nsub.value, total.value,
+                             ptr.ctypes.data, cams.ctypes.data, C.byref(nsub), C.byref(total))
+    if s != CCOV_OK:
+        raise CcovError(s, "ccov_subrecon_plan")
+    return [cams[ptr[q]:ptr[q + 1]].tolist() for q in range(nsub.value)]
+
+
+def subrecon_covariances(scene, k: int, orders, precision=CCOV_PREC_MIXED, **kw):
+    """ccov_subrecon_covariance: merged (n, 9, 9) blocks, cover counts and the
+    number of sub-reconstructions solved."""
+    L = load()
+    so, keep = _subrecon_opts(k, orders)
+    opt = Options(precision, kw.get("mixed_slices", 0), kw.get("nullspace_route", CCOV_NULL_PAPER), CCOV_MEM_HOST,
+                  0, 0)
+    rec = scene.obs_records()
+    out = np.empty((scene.n, 9, 9))
+    cover = np.empty(scene.n, np.int32)
+    nsub = C.c_int64()
+    cov = None if scene.obs_cov is None else np.ascontiguousarray(scene.obs_cov.reshape(-1, 4))
+    s = L.ccov_subrecon_covariance(_ptr(np.ascontiguousarray(scene.cams)), scene.n,
+                                   _ptr(np.ascontiguousarray(scene.pts)), scene.m, rec.ctypes.data, scene.t,
+                                   float(scene.sigma), _ptr(cov), C.byref(opt), C.byref(so), out.ctypes.data,
+                                   cover.ctypes.data, C.byref(nsub))
+    if s != CCOV_OK:
+        raise CcovError(s, "ccov_subrecon_covariance")
+    return out, cover, nsub.value

@@ -129,16 +129,18 @@ ccov_status build_index(Ctx& c, const double* cams, const double* pts, const cco
 // counting sorts) and within a block by point, so the device sums every block
 // in a fixed order.  Depends on S only (ccov_load keeps it).
 void build_pairs(const ccov_obs* obs, int64_t n, int64_t m, const std::vector<int>& pt_ptr,
-                 std::vector<int4>& desc, std::vector<int2>& ent) {
+                 std::vector<int4>& desc, std::vector<int2>& ent, const std::vector<char>& fixed) {
     int64_t total = 0;
     for (int64_t j = 0; j < m; ++j) {
+        if (!fixed.empty() && fixed[j]) continue;
         const int64_t L = pt_ptr[j + 1] - pt_ptr[j];
         total += L * (L + 1) / 2;
     }
     std::vector<int> row(total), col(total);
     std::vector<int2> raw(total);
     int64_t e = 0;
-    for (int64_t j = 0; j < m; ++j)
+    for (int64_t j = 0; j < m; ++j) {
+        if (!fixed.empty() && fixed[j]) continue;   // a fixed point is not eliminated (Alg. 5)
         for (int a = pt_ptr[j]; a < pt_ptr[j + 1]; ++a)
             for (int b = a; b < pt_ptr[j + 1]; ++b) {
                 const int ca = obs[a].cam, cb = obs[b].cam;
@@ -148,6 +150,7 @@ void build_pairs(const ccov_obs* obs, int64_t n, int64_t m, const std::vector<in
                 raw[e] = make_int2(first ? a : b, first ? b : a);
                 ++e;
             }
+    }
     // stable counting sort by column, then by row: (row, col, point) order
     std::vector<int64_t> cnt(n + 1);
     std::vector<int64_t> by_col(total), order(total);
@@ -167,6 +170,42 @@ void build_pairs(const ccov_obs* obs, int64_t n, int64_t m, const std::vector<in
             desc.push_back(make_int4(row[src], col[src], (int)q, 0));
         desc.back().w++;
     }
+}
+
+// The three fixed points of Alg. 5 when the caller gives none: the point
+// farthest from the centroid, the point farthest from it, the point
+// farthest from the line through those two (ties: the smaller index).
+void three_far_points(const double* pts, int64_t m, int out[3]) {
+    double c[3] = {0, 0, 0};
+    for (int64_t j = 0; j < m; ++j)
+        for (int a = 0; a < 3; ++a) c[a] += pts[3 * j + a];
+    for (int a = 0; a < 3; ++a) c[a] /= (double)m;
+    auto far_from = [&](const double* q) {
+        int64_t best = 0;
+        double bd = -1.0;
+        for (int64_t j = 0; j < m; ++j) {
+            double d = 0.0;
+            for (int a = 0; a < 3; ++a) d += (pts[3 * j + a] - q[a]) * (pts[3 * j + a] - q[a]);
+            d = std::sqrt(d);
+            if (d > bd) { bd = d; best = j; }
+        }
+        return best;
+    };
+    const int64_t p1 = far_from(c), p2 = far_from(pts + 3 * p1);
+    double u[3], nu = 0.0;
+    for (int a = 0; a < 3; ++a) { u[a] = pts[3 * p2 + a] - pts[3 * p1 + a]; nu += u[a] * u[a]; }
+    nu = std::sqrt(nu);
+    for (int a = 0; a < 3; ++a) u[a] /= nu;
+    int64_t p3 = 0;
+    double bd = -1.0;
+    for (int64_t j = 0; j < m; ++j) {
+        double v[3], vu = 0.0, d = 0.0;
+        for (int a = 0; a < 3; ++a) { v[a] = pts[3 * j + a] - pts[3 * p1 + a]; vu += v[a] * u[a]; }
+        for (int a = 0; a < 3; ++a) d += (v[a] - vu * u[a]) * (v[a] - vu * u[a]);
+        d = std::sqrt(d);
+        if (d > bd) { bd = d; p3 = j; }
+    }
+    out[0] = (int)p1; out[1] = (int)p2; out[2] = (int)p3;
 }
 
 ccov_status check_device(Ctx& c, const char* where) {
@@ -206,10 +245,32 @@ float elapsed(Ctx& c, int a, int b) {
     return ms;
 }
 
+// The centre camera's n x 8 values {r, C, c, k} in the 9-slot layout the
+// kernels read (slot 8, no parameter, zero).  `memory` says where src lives.
+bool expand_centre(const double* src, int64_t n, int memory, std::vector<double>& out) {
+    std::vector<double> tmp(8 * n);
+    if (memory == CCOV_MEM_DEVICE) {
+        if (cudaMemcpy(tmp.data(), src, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    } else {
+        std::memcpy(tmp.data(), src, sizeof(double) * 8 * n);
+    }
+    out.assign(9 * n, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 8; ++k) out[9 * i + k] = tmp[8 * i + k];
+    return true;
+}
+
 ccov_status upload(Ctx& c, const double* cams, const double* pts, const ccov_obs* obs,
                    const double* cov, int memory) {
     cudaMemcpyKind kind = memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(c.d_cams, cams, sizeof(double) * 9 * c.n, kind, c.stream), "copy cameras");
+    if (c.opt.camera_model == CCOV_CAMERA_CENTRE8) {
+        std::vector<double> e;
+        if (!expand_centre(cams, c.n, memory, e)) return fail(&c, CCOV_ERR_INVALID_ARG, "cameras not readable");
+        // synchronous: the host vector goes out of scope
+        CK(cudaMemcpy(c.d_cams, e.data(), sizeof(double) * 9 * c.n, cudaMemcpyHostToDevice), "copy cameras");
+    } else {
+        CK(cudaMemcpyAsync(c.d_cams, cams, sizeof(double) * 9 * c.n, kind, c.stream), "copy cameras");
+    }
     CK(cudaMemcpyAsync(c.d_pts, pts, sizeof(double) * 3 * c.m, kind, c.stream), "copy points");
     CK(cudaMemcpyAsync(c.d_obs, obs, sizeof(ccov_obs) * c.t, kind, c.stream), "copy observations");
     if (cov) CK(cudaMemcpyAsync(c.d_obscov, cov, sizeof(double) * 4 * c.t, kind, c.stream), "copy obs_cov");
@@ -269,7 +330,11 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     Ctx& c = h->c;
     *out = h;
     if (opt) c.opt = *opt;
-    if (c.opt.mixed_slices == 0) c.opt.mixed_slices = 5;
+    // the comparison algorithms' matrices (Z restricted to its range, or with
+    // three points fixed) and the centre camera's are about 100x worse
+    // conditioned after Jacobi scaling (2e6 against 2e4): six digits
+    if (c.opt.mixed_slices == 0)
+        c.opt.mixed_slices = c.opt.gauge == CCOV_GAUGE_NATURAL && c.opt.camera_model == CCOV_CAMERA_RT9 ? 5 : 6;
     if (c.opt.precision != CCOV_PREC_FP64 && c.opt.precision != CCOV_PREC_MIXED)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown precision %d", c.opt.precision);
     if (c.opt.mixed_slices < 4 || c.opt.mixed_slices > 6)
@@ -279,6 +344,10 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
         return fail(&c, CCOV_ERR_INVALID_ARG, "est_cameras must be 1..%d", ccov::kEstMaxCams);
     if (c.opt.nullspace_route != CCOV_NULL_PAPER && c.opt.nullspace_route != CCOV_NULL_CLOSED)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown nullspace route");
+    if (c.opt.gauge != CCOV_GAUGE_NATURAL && c.opt.gauge != CCOV_GAUGE_ZPINV && c.opt.gauge != CCOV_GAUGE_FIXED3)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown gauge");
+    if (c.opt.camera_model != CCOV_CAMERA_RT9 && c.opt.camera_model != CCOV_CAMERA_CENTRE8)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown camera model");
     c.n = n; c.m = m; c.t = t; c.N = 9 * n;
     c.Np = (c.N + ccov::kNB - 1) / ccov::kNB * ccov::kNB;
     c.sigma = sigma;
@@ -291,13 +360,21 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     std::vector<ccov_obs> ho;
     const double* vc = cameras; const double* vp = points; const ccov_obs* vo = obs;
     const double* vcov = obs_cov;
+    std::vector<double> hc9;
+    if (c.opt.camera_model == CCOV_CAMERA_CENTRE8) {
+        if (!expand_centre(cameras, n, dev ? CCOV_MEM_DEVICE : CCOV_MEM_HOST, hc9))
+            return fail(&c, CCOV_ERR_INVALID_ARG, "cameras not readable");
+        vc = hc9.data();
+    }
     if (dev) {
         hc.resize(9 * n); hp.resize(3 * m); ho.resize(t);
-        if (cudaMemcpy(hc.data(), cameras, 8 * 9 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        if ((c.opt.camera_model != CCOV_CAMERA_CENTRE8 &&
+             cudaMemcpy(hc.data(), cameras, 8 * 9 * n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
             cudaMemcpy(hp.data(), points, 8 * 3 * m, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(ho.data(), obs, sizeof(ccov_obs) * t, cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(&c, CCOV_ERR_INVALID_ARG, "input_memory = device but the inputs are not readable device memory");
-        vc = hc.data(); vp = hp.data(); vo = ho.data();
+        if (c.opt.camera_model != CCOV_CAMERA_CENTRE8) vc = hc.data();
+        vp = hp.data(); vo = ho.data();
         if (obs_cov) {
             hcov.resize(4 * t);
             if (cudaMemcpy(hcov.data(), obs_cov, 8 * 4 * t, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -308,9 +385,21 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     std::vector<int> pt_ptr, cam_ptr, cam_perm;
     ccov_status s = build_index(c, vc, vp, vo, vcov, pt_ptr, cam_ptr, cam_perm);
     if (s != CCOV_OK) return s;
+    std::vector<char> fixed;
+    if (c.opt.gauge == CCOV_GAUGE_FIXED3) {
+        int* fp = c.opt.fixed_points;
+        const bool given = !(fp[0] == fp[1] && fp[1] == fp[2] && (fp[0] == -1 || fp[0] == 0));
+        if (!given) three_far_points(vp, m, fp);
+        fixed.assign(m, 0);
+        for (int q = 0; q < 3; ++q) {
+            if (fp[q] < 0 || fp[q] >= m || fixed[fp[q]])
+                return fail(&c, CCOV_ERR_INVALID_ARG, "fixed_points: three distinct point indices needed");
+            fixed[fp[q]] = 1;
+        }
+    }
     std::vector<int4> pair_desc;
     std::vector<int2> pair_ent;
-    build_pairs(vo, n, m, pt_ptr, pair_desc, pair_ent);
+    build_pairs(vo, n, m, pt_ptr, pair_desc, pair_ent, fixed);
     if ((int64_t)pair_ent.size() >= ((int64_t)1 << 31))
         return fail(&c, CCOV_ERR_INVALID_ARG, "too many camera pairs per point (%lld)", (long long)pair_ent.size());
     c.npairs = (int64_t)pair_desc.size();
@@ -383,7 +472,13 @@ ccov_status ccov_load(ccov_ctx* h, const double* cameras, const double* points, 
     if (memory == CCOV_MEM_HOST) {
         // the index set S must be the one the context was built for
         std::vector<int> pt_ptr, cam_ptr, cam_perm;
-        ccov_status s = build_index(c, cameras, points, obs, obs_cov, pt_ptr, cam_ptr, cam_perm);
+        std::vector<double> c9;
+        const double* vc = cameras;
+        if (c.opt.camera_model == CCOV_CAMERA_CENTRE8) {
+            expand_centre(cameras, c.n, CCOV_MEM_HOST, c9);
+            vc = c9.data();
+        }
+        ccov_status s = build_index(c, vc, points, obs, obs_cov, pt_ptr, cam_ptr, cam_perm);
         if (s != CCOV_OK) return s;
         std::vector<int> dptr(c.m + 1);
         CK(cudaMemcpy(dptr.data(), c.d_pt_ptr, sizeof(int) * (c.m + 1), cudaMemcpyDeviceToHost), "load");
@@ -684,7 +779,8 @@ static void batch_free(ccov_batch* b) {
 extern "C" {
 
 // The grouped form: plan, autotune, one direct pass, then capture.
-static ccov_status batch_create_grouped(ccov_ctx* const* ctxs, int k, double* const* outs_device, ccov_batch** out) {
+static ccov_status batch_create_grouped(ccov_ctx* const* ctxs, int k, double* const* outs_device, bool tune,
+                                        ccov_batch** out) {
     std::vector<Ctx*> cs(k);
     for (int i = 0; i < k; ++i) cs[i] = &ctxs[i]->c;
     ccov_batch* b = new (std::nothrow) ccov_batch();
@@ -707,7 +803,10 @@ static ccov_status batch_create_grouped(ccov_ctx* const* ctxs, int k, double* co
     ccov_status s = e == cudaSuccess ? ccov::group_status(*b->group, b->master, "ccov_batch_create") : CCOV_ERR_CUDA;
     if (s != CCOV_OK) { batch_free(b); return s; }
     float tune_ms = 0.f;
-    if (ccov::group_autotune(*b->group, b->master, 1, &tune_ms) != cudaSuccess) { batch_free(b); return CCOV_ERR_CUDA; }
+    if (tune && ccov::group_autotune(*b->group, b->master, 1, &tune_ms) != cudaSuccess) {
+        batch_free(b);
+        return CCOV_ERR_CUDA;
+    }
     s = ccov::group_status(*b->group, b->master, "ccov_batch_create");
     if (s != CCOV_OK) { batch_free(b); return s; }
     if (cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -734,6 +833,8 @@ ccov_status ccov_batch_create_ex(ccov_ctx* const* ctxs, int k, double* const* ou
                                  ccov_batch** out) {
     if (!out) return CCOV_ERR_INVALID_ARG;
     *out = nullptr;
+    const bool tune = !(form & CCOV_BATCH_NO_TUNE);
+    form &= ~CCOV_BATCH_NO_TUNE;
     if (form != CCOV_BATCH_AUTO && form != CCOV_BATCH_PER_SCENE && form != CCOV_BATCH_GROUPED)
         return CCOV_ERR_INVALID_ARG;
     {
@@ -743,7 +844,7 @@ ccov_status ccov_batch_create_ex(ccov_ctx* const* ctxs, int k, double* const* ou
     if (form != CCOV_BATCH_PER_SCENE) {
         std::vector<Ctx*> cs(k);
         for (int i = 0; i < k; ++i) cs[i] = &ctxs[i]->c;
-        if (ccov::group_eligible(cs.data(), k)) return batch_create_grouped(ctxs, k, outs_device, out);
+        if (ccov::group_eligible(cs.data(), k)) return batch_create_grouped(ctxs, k, outs_device, tune, out);
         if (form == CCOV_BATCH_GROUPED)
             return fail(&ctxs[0]->c, CCOV_ERR_INVALID_ARG,
                         "grouped batch: every context needs MIXED precision with the same digits, nullspace "

@@ -484,6 +484,7 @@ bool group_eligible(Ctx* const* ctxs, int k) {
         const Ctx& b = *ctxs[q];
         if (b.opt.precision != CCOV_PREC_MIXED || b.opt.mixed_slices != a.opt.mixed_slices ||
             b.opt.nullspace_route != a.opt.nullspace_route || b.has_cov != a.has_cov ||
+            b.opt.gauge != CCOV_GAUGE_NATURAL || b.opt.camera_model != a.opt.camera_model ||
             (!a.has_cov && b.sigma != a.sigma))
             return false;
     }
@@ -694,6 +695,12 @@ ccov_status group_status(GroupPlan& P, cudaStream_t st, const char* where) {
 }
 
 int64_t group_launches(const GroupPlan& P) { return P.launches; }
-void group_shape(const GroupPlan& P, int* cap, int* stages) { *cap = P.gemm_cap; *stages = P.gemm_stages; }
+void group_shape(const GroupPlan& P, int* cap, int* stages) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *cap = std::min(P.gemm_cap, sms);
+    *stages = P.gemm_stages;
+}
 
 }  // namespace ccov

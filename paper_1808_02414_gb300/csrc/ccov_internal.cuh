@@ -12,7 +12,7 @@
 namespace ccov {
 
 constexpr int kNB = 128;         // dense block size: panel width and K of every trailing update
-constexpr int kCamPrep = 24;     // doubles per prepared camera: R(9) t(3) f k1 k2 (3) J_l(9)
+constexpr int kCamPrep = 25;     // doubles per prepared camera: R(9) t(3) f k1 k2 (3) J_l(9) model(1)
 constexpr int kEstMaxCams = 16;  // sampled cameras of the a-posteriori error estimate, at most
 constexpr int kEstDefaultCams = 4;
 
@@ -172,6 +172,9 @@ void est_free(Ctx& c);
 void est_keep_fp64(Ctx& c);                  // after the FP64 scaling: keep Z_s
 void est_launch(Ctx& c, const long long* Xq);  // after the inverse, before the extraction
 void est_launch_final(Ctx& c);               // after the extraction
+// Y = X^T (X V) for g groups of nine columns (Np x 9g FP64, device), X the
+// inverse factor of the last step (d); s0..s2 scratch of 8 Np 9g bytes each
+void est_xtxv(Ctx& c, int g, const double* V, double* Y, void* s0, void* s1, void* s2);
 
 // ---- the batched form as grouped launches (ccov_group.cu) ----
 struct GroupPlan;

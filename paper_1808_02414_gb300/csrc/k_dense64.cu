@@ -53,11 +53,11 @@ __device__ bool inv7(const double* Ain, double* Aout) {
     return true;
 }
 
-// G = G_part + H_P (the border column block of Z_p).
+// G = G_part + H_P (the border column block of Z_p); Gp null: G = H_P.
 __global__ void g_kernel(int64_t N, const double* __restrict__ Gp, const double* __restrict__ HP,
                          double* __restrict__ G) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < 7 * N) G[e] = Gp[e] + HP[e];
+    if (e < 7 * N) G[e] = (Gp ? Gp[e] : 0.0) + HP[e];
 }
 
 // Gauge weight and the 7x7 matrices of the regularised route.  With span H =
@@ -70,9 +70,17 @@ __global__ void g_kernel(int64_t N, const double* __restrict__ Gp, const double*
 // One CTA of 256 threads.  Output (small): K = (Lambda^-1 + W7)^-1 at [0, 49),
 // C at [49, 98).  W7 (upper) at W7s[0, 49), H_X^T H_X (upper) at W7s[49, 98).
 constexpr double kGaugeAlpha = 1e-2;
+// gauge: CCOV_GAUGE_NATURAL as above; CCOV_GAUGE_ZPINV (Alg. 4) with G = H_P,
+// W7 = 0 and H^T H = H_P^T H_P, the same identity for Z, whose nullspace is
+// span(H_P): (Z + H_P Lambda H_P^T)^-1 = Z+ + H_P (H_P^T H_P)^-1 Lambda^-1
+// (H_P^T H_P)^-1 H_P^T; CCOV_GAUGE_FIXED3 (Alg. 5): Z is of full rank, K = C = 0.
 __device__ __forceinline__ void gauge_body(int64_t N, const double* __restrict__ G, const double* __restrict__ HP,
                                            const double* __restrict__ Z, int64_t ldz, const double* __restrict__ W7s,
-                                           double* __restrict__ small, int* flag) {
+                                           double* __restrict__ small, int* flag, int gauge) {
+    if (gauge == CCOV_GAUGE_FIXED3) {
+        for (int e = threadIdx.x; e < 98; e += blockDim.x) small[e] = 0.0;
+        return;
+    }
     __shared__ double red[35][33];
     double acc[35];
 #pragma unroll
@@ -109,9 +117,9 @@ __device__ __forceinline__ void gauge_body(int64_t N, const double* __restrict__
     int e = 7;
     for (int p = 0; p < 7; ++p)
         for (int q = p; q < 7; ++q, ++e) {
-            double hh = tot[e] + W7s[49 + 7 * p + q];
+            double hh = tot[e] + (gauge == CCOV_GAUGE_ZPINV ? 0.0 : W7s[49 + 7 * p + q]);
             HtH[7 * p + q] = hh; HtH[7 * q + p] = hh;
-            double w = W7s[7 * p + q];
+            double w = gauge == CCOV_GAUGE_ZPINV ? 0.0 : W7s[7 * p + q];
             M7[7 * p + q] = w; M7[7 * q + p] = w;
         }
     for (int q = 0; q < 7; ++q) M7[8 * q] += lam_inv[q];
@@ -128,8 +136,8 @@ __device__ __forceinline__ void gauge_body(int64_t N, const double* __restrict__
 __global__ void __launch_bounds__(256)
 gauge_kernel(int64_t N, const double* __restrict__ G, const double* __restrict__ HP,
              const double* __restrict__ Z, int64_t ldz, const double* __restrict__ W7s,
-             double* __restrict__ small, int* flag) {
-    gauge_body(N, G, HP, Z, ldz, W7s, small, flag);
+             double* __restrict__ small, int* flag, int gauge) {
+    gauge_body(N, G, HP, Z, ldz, W7s, small, flag, gauge);
 }
 
 // F = G K, D_r = (Z_rr + F_r . G_r)^-1/2 (row r of Z').
@@ -375,7 +383,7 @@ __global__ void extract_kernel(int64_t n, const double* __restrict__ D, const do
 // ---- grouped forms: the same step of many scenes in one launch ----
 __global__ void __launch_bounds__(256) gauge_grouped(const GaugeP* __restrict__ P, int* flag) {
     const GaugeP& a = P[blockIdx.x];
-    gauge_body(a.N, a.G, a.HP, a.Z, a.ldz, a.W7s, a.small, flag);
+    gauge_body(a.N, a.G, a.HP, a.Z, a.ldz, a.W7s, a.small, flag, CCOV_GAUGE_NATURAL);
 }
 
 __global__ void fd_grouped(const FdP* __restrict__ P, const int64_t* __restrict__ pre, int k, int* flag) {
@@ -406,8 +414,10 @@ void launch_g(Ctx& c) {
 }
 
 void launch_form_scaled(Ctx& c) {
-    g_kernel<<<(int)((7 * c.N + 255) / 256), 256, 0, c.stream>>>(c.N, c.d_Gp, c.d_HP, c.d_G);
-    gauge_kernel<<<1, 256, 0, c.stream>>>(c.N, c.d_G, c.d_HP, c.d_Z, c.Np, c.d_W7, c.d_small, c.d_flag);
+    g_kernel<<<(int)((7 * c.N + 255) / 256), 256, 0, c.stream>>>(
+        c.N, c.opt.gauge == CCOV_GAUGE_ZPINV ? nullptr : c.d_Gp, c.d_HP, c.d_G);
+    gauge_kernel<<<1, 256, 0, c.stream>>>(c.N, c.d_G, c.d_HP, c.d_Z, c.Np, c.d_W7, c.d_small, c.d_flag,
+                                          c.opt.gauge);
     fd_kernel<<<(int)((c.Np + 255) / 256), 256, 0, c.stream>>>(c.N, c.Np, c.d_small, c.d_Z, c.d_G, c.d_F,
                                                                 c.d_D, c.d_flag);
     c.launches += 3;

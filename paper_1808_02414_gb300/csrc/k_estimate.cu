@@ -157,7 +157,7 @@ lt_t_kernel(int64_t N, int64_t Np, const In* __restrict__ A, float scale, int st
 
 // out[r][9j + a] = sum over c <= r of A[r][c] V[c][9j + a] - [r = 9 idx_j + a]
 // (the lower triangle of a symmetric matrix times the camera's columns, minus
-// the unit columns).  Grid (N / 8, k), a warp per row.
+// the unit columns; idx null: no unit columns).  Grid (N / 8, k), a warp per row.
 template <class T, class In>
 __global__ void __launch_bounds__(256)
 lt_row_kernel(int64_t N, int64_t Np, const In* __restrict__ A, float scale, const T* __restrict__ V, int k,
@@ -185,7 +185,7 @@ lt_row_kernel(int64_t N, int64_t Np, const In* __restrict__ A, float scale, cons
 #pragma unroll
         for (int a = 1; a < 9; ++a)
             if (lane == a) s = acc[a];
-        if (r == 9 * (int64_t)idx[j] + lane) s = Ar<T>::add(s, Ar<T>::from_double(-1.0));
+        if (idx && r == 9 * (int64_t)idx[j] + lane) s = Ar<T>::add(s, Ar<T>::from_double(-1.0));
         out[r * ld + 9 * j + lane] = s;
     }
 }
@@ -258,7 +258,44 @@ void launch_est(Ctx& c, const XIn* X, float sx, const ZIn* Zs, float sz) {
     c.launches += 6;
 }
 
+template <class T>
+__global__ void to_arith_kernel(int64_t count, const double* __restrict__ in, T* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < count) out[e] = Ar<T>::from_double(in[e]);
+}
+
+template <class T>
+__global__ void from_arith_kernel(int64_t count, const T* __restrict__ in, double* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < count) out[e] = Ar<T>::to_double(in[e]);
+}
+
+// Y = X^T (X V) for g groups of nine columns (V, Y: Np x 9g FP64, device),
+// X the lower-triangular inverse factor of the last step (d); W, Y2 scratch
+// of the same size.  The arithmetic is the estimate's.
+template <class T, class XIn>
+void xtxv(Ctx& c, const XIn* X, float sx, int g, const double* V, double* Y, void* s0, void* s1, void* s2) {
+    const int64_t N = c.N, Np = c.Np, cnt = Np * 9 * (int64_t)g;
+    T* v = static_cast<T*>(s0);
+    T* w = static_cast<T*>(s1);
+    T* y = static_cast<T*>(s2);
+    const unsigned b = (unsigned)((cnt + 255) / 256);
+    to_arith_kernel<T><<<b, 256, 0, c.stream>>>(cnt, V, v);
+    const dim3 gt((unsigned)((Np + 31) / 32), (unsigned)g), gr((unsigned)((Np + 7) / 8), (unsigned)g);
+    lt_row_kernel<T, XIn><<<gr, 256, 0, c.stream>>>(N, Np, X, sx, v, g, nullptr, w);
+    lt_t_kernel<T, XIn><<<gt, 256, 0, c.stream>>>(N, Np, X, sx, 0, w, g, y, 0);
+    from_arith_kernel<T><<<b, 256, 0, c.stream>>>(cnt, y, Y);
+    c.launches += 4;
+}
+
 }  // namespace
+
+void est_xtxv(Ctx& c, int g, const double* V, double* Y, void* s0, void* s1, void* s2) {
+    if (c.opt.precision == CCOV_PREC_FP64)
+        xtxv<double, double>(c, c.d_R, 1.f, g, V, Y, s0, s1, s2);
+    else
+        xtxv<dsf, long long>(c, mixed_inverse_factor(c), 2.2737367544323206e-13f /* 2^-42 */, g, V, Y, s0, s1, s2);
+}
 
 cudaError_t est_alloc(Ctx& c, int k) {
     if (c.d_Zkeep && c.est_cap >= k) return cudaSuccess;

@@ -27,9 +27,10 @@ __device__ __forceinline__ void set_flag(int* flag, int code, int detail) {
 // R(r), t, f, k1, k2 and the left Jacobian J_l(r) of SO(3):
 // R = I + a [r]x + b [r]x^2, a = sin(th)/th, b = (1 - cos th)/th^2,
 // J_l = I + b [r]x + c [r]x^2, c = (th - sin th)/th^3, so that
-// d(R X)/dr = -[R X]x J_l.
+// d(R X)/dr = -[R X]x J_l.  The centre camera {r, C, c, k} (slots 3-5: C)
+// is stored as t = -R C, f = c, k1 = k, k2 = 0, with prep[24] = 1.
 __global__ void cam_prep_kernel(int64_t n, const double* __restrict__ cams,
-                                double* __restrict__ prep) {
+                                double* __restrict__ prep, int centre) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double* c = cams + 9 * i;
@@ -60,12 +61,20 @@ __global__ void cam_prep_kernel(int64_t n, const double* __restrict__ cams,
         o[e] = I + a * K[e] + b * K2[e];
         o[15 + e] = I + b * K[e] + cc * K2[e];
     }
-    o[9] = c[3]; o[10] = c[4]; o[11] = c[5];
-    o[12] = c[6]; o[13] = c[7]; o[14] = c[8];
+    if (centre) {
+        for (int p = 0; p < 3; ++p) o[9 + p] = -(o[3 * p] * c[3] + o[3 * p + 1] * c[4] + o[3 * p + 2] * c[5]);
+        o[12] = c[6]; o[13] = c[7]; o[14] = 0.0;
+    } else {
+        o[9] = c[3]; o[10] = c[4]; o[11] = c[5];
+        o[12] = c[6]; o[13] = c[7]; o[14] = c[8];
+    }
+    o[24] = centre ? 1.0 : 0.0;
 }
 
 // Analytic Jacobians of one observation (Sec. 4.1 projection with the
 // 9-parameter camera).  Jc: 2x9 row-major, Jp: 2x3.  Returns the depth.
+// Centre camera: p = R (X - C), so dp/dr = -[p]x J_l, dp/dC = -R, and slot
+// 8 (no parameter) has a zero column.
 __device__ __forceinline__ double obs_jacobian(const double* __restrict__ cp, double X0, double X1,
                                                double X2, double* Jc, double* Jp) {
     const double* R = cp;
@@ -85,9 +94,11 @@ __device__ __forceinline__ double obs_jacobian(const double* __restrict__ cp, do
     double D[6];
     D[0] = s * a00; D[1] = s * a01; D[2] = -s * (a00 * x + a01 * y);
     D[3] = s * a01; D[4] = s * a11; D[5] = -s * (a01 * x + a11 * y);
-    // Q = -[RX]x J_l  (d p / d r)
+    // Q = -[RX]x J_l  (d p / d r); centre camera: -[p]x J_l
     const double* Jl = cp + 15;
-    double S[9] = {0, RX2, -RX1, -RX2, 0, RX0, RX1, -RX0, 0};  // -[RX]x
+    const bool centre = cp[24] != 0.0;
+    const double q0 = centre ? p0 : RX0, q1 = centre ? p1 : RX1, q2 = centre ? p2 : RX2;
+    double S[9] = {0, q2, -q1, -q2, 0, q0, q1, -q0, 0};        // -[q]x
     double Q[9];
 #pragma unroll
     for (int pq = 0; pq < 9; ++pq) {
@@ -101,13 +112,14 @@ __device__ __forceinline__ double obs_jacobian(const double* __restrict__ cp, do
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             jc[q] = d[0] * Q[q] + d[1] * Q[3 + q] + d[2] * Q[6 + q];
-            jc[3 + q] = d[q];
             Jp[3 * row + q] = d[0] * R[q] + d[1] * R[3 + q] + d[2] * R[6 + q];
+            jc[3 + q] = centre ? -Jp[3 * row + q] : d[q];
         }
     }
     Jc[6] = g * x;          Jc[15] = g * y;
     Jc[7] = f * r2 * x;     Jc[16] = f * r2 * y;
-    Jc[8] = f * r2 * r2 * x; Jc[17] = f * r2 * r2 * y;
+    Jc[8] = centre ? 0.0 : f * r2 * r2 * x;
+    Jc[17] = centre ? 0.0 : f * r2 * r2 * y;
     return p2;
 }
 
@@ -223,6 +235,8 @@ cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restric
 #pragma unroll
         for (int e = 0; e < 45; ++e) {
             double v = warp_sum(u[e]);
+            // centre camera: a unit prior on the value that no observation sees (slot 8)
+            if (e == 44 && cp[24] != 0.0) v += 1.0;
             if (lane == 0) U[45 * i + e] = v;
         }
     }
@@ -436,6 +450,8 @@ cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
 // ---------------------------------------------------------------------------
 // Step (c): H_P per camera.  Paper route: accumulate J_r^T J_r and J_r^T B over
 // the camera's observations, B = -(J_t H_t + J_X H_X), and solve (3x3 SPD).
+// Position rows: H_t = [-R, 0, t] (translation form), H_C = [I, -[C]x, C]
+// (centre camera, C in slots 3-5 of the camera).
 __global__ void __launch_bounds__(32 * kWarps)
 nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
                  const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
@@ -447,7 +463,20 @@ nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
     for (int64_t i = warp; i < n; i += nwarp) {
         const double* cp = prep + (int64_t)kCamPrep * i;
         const double* R = cp;
-        const double t0 = cp[9], t1 = cp[10], t2 = cp[11];
+        const bool centre = cp[24] != 0.0;
+        // position values: t (translation form) or C (centre camera)
+        const double t0 = centre ? cams[9 * i + 3] : cp[9], t1 = centre ? cams[9 * i + 4] : cp[10],
+                     t2 = centre ? cams[9 * i + 5] : cp[11];
+        // rows of H for the position values, 3 x 7
+        double Hpos[21];
+        for (int p = 0; p < 3; ++p) {
+            for (int q = 0; q < 3; ++q) Hpos[7 * p + q] = centre ? (p == q ? 1.0 : 0.0) : -R[3 * p + q];
+            Hpos[7 * p + 6] = p == 0 ? t0 : (p == 1 ? t1 : t2);
+        }
+        // -[C]x for the centre camera, 0 for the translation form
+        Hpos[3] = 0.0;                 Hpos[4] = centre ? t2 : 0.0;  Hpos[5] = centre ? -t1 : 0.0;
+        Hpos[10] = centre ? -t2 : 0.0; Hpos[11] = 0.0;               Hpos[12] = centre ? t0 : 0.0;
+        Hpos[17] = centre ? t1 : 0.0;  Hpos[18] = centre ? -t0 : 0.0; Hpos[19] = 0.0;
         double Hr[21];
         if (route == CCOV_NULL_CLOSED) {
             // H_r = [0, -J_r^-1(r), 0], J_r^-1 = I + 1/2 K + c K^2
@@ -479,15 +508,15 @@ nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
                     const double* jr = Jc + 9 * row;       // d/dr (3)
                     const double* jt = Jc + 9 * row + 3;   // d/dt (3)
                     const double* jx = Jp + 3 * row;
-                    // B row = -(J_t H_t + J_X H_X); H_t = [-R, 0, t], H_X = [I, -[X]x, X]
+                    // B row = -(J_pos H_pos + J_X H_X), H_X = [I, -[X]x, X]
                     double b[7];
-                    for (int q = 0; q < 3; ++q)
-                        b[q] = -(-(jt[0] * R[q] + jt[1] * R[3 + q] + jt[2] * R[6 + q]) + jx[q]);
+                    for (int q = 0; q < 7; ++q) b[q] = -(jt[0] * Hpos[q] + jt[1] * Hpos[7 + q] + jt[2] * Hpos[14 + q]);
+                    for (int q = 0; q < 3; ++q) b[q] -= jx[q];
                     // J_X (-[X]x): columns of -[X]x = [[0,X2,-X1],[-X2,0,X0],[X1,-X0,0]]
-                    b[3] = -(jx[1] * (-X2) + jx[2] * X1);
-                    b[4] = -(jx[0] * X2 + jx[2] * (-X0));
-                    b[5] = -(jx[0] * (-X1) + jx[1] * X0);
-                    b[6] = -(jt[0] * t0 + jt[1] * t1 + jt[2] * t2 + jx[0] * X0 + jx[1] * X1 + jx[2] * X2);
+                    b[3] -= jx[1] * (-X2) + jx[2] * X1;
+                    b[4] -= jx[0] * X2 + jx[2] * (-X0);
+                    b[5] -= jx[0] * (-X1) + jx[1] * X0;
+                    b[6] -= jx[0] * X0 + jx[1] * X1 + jx[2] * X2;
                     jj[0] += jr[0] * jr[0]; jj[1] += jr[0] * jr[1]; jj[2] += jr[0] * jr[2];
                     jj[3] += jr[1] * jr[1]; jj[4] += jr[1] * jr[2]; jj[5] += jr[2] * jr[2];
 #pragma unroll
@@ -524,11 +553,7 @@ nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
         if (lane == 0) {
             double* h = HP + 63 * i;
             for (int e = 0; e < 21; ++e) h[e] = Hr[e];
-            for (int p = 0; p < 3; ++p) {
-                for (int q = 0; q < 3; ++q) h[21 + 7 * p + q] = -R[3 * p + q];
-                h[21 + 7 * p + 3] = 0.0; h[21 + 7 * p + 4] = 0.0; h[21 + 7 * p + 5] = 0.0;
-            }
-            h[21 + 6] = t0; h[28 + 6] = t1; h[35 + 6] = t2;
+            for (int e = 0; e < 21; ++e) h[21 + e] = Hpos[e];
             for (int e = 42; e < 63; ++e) h[e] = 0.0;
         }
     }
@@ -543,7 +568,8 @@ int grid_for(int64_t items, int per_cta) {
 }  // namespace
 
 void launch_cam_prep(Ctx& c) {
-    cam_prep_kernel<<<(int)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_cams, c.d_camprep);
+    cam_prep_kernel<<<(int)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_cams, c.d_camprep,
+                                                                  c.opt.camera_model == CCOV_CAMERA_CENTRE8);
     CCOV_LAUNCH_CHECK(c);
 }
 

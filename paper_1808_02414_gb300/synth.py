@@ -19,7 +19,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Scene", "ring_scene", "shell_scene", "batch_scenes", "tiny_scene",
-           "subscene", "weak_camera_scene", "local_scene", "decomposition_orders", "centre_scene", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
+           "subscene", "weak_camera_scene", "local_scene", "decomposition_orders", "centre_scene",
+           "added_observations", "WORKLOADS", "workload", "surrogate_init", "minibatch_indices",
            "training_scene_specs", "training_scene"]
 
 
@@ -251,6 +252,45 @@ def centre_scene(sc: Scene) -> Scene:
         cams[i, 7] = sc.cams[i, 7]
     return Scene(cams, sc.pts, sc.obs_cam, sc.obs_pt, sc.obs_u, sc.sigma, sc.obs_cov,
                  dict(sc.meta, model="centre8"), "centre8")
+
+
+def added_observations(sc: Scene, k: int, cams=None, seed=11):
+    """k new observations (camera, point) of existing points by existing
+    cameras, none already in S: from the cameras `cams` (default: any),
+    points drawn uniformly; u = projection + N(0, 1 px^2).  Returns (the
+    scene with them merged, sorted by point; the added records, sorted by
+    point)."""
+    rng = np.random.default_rng(seed)
+    have = set(zip(sc.obs_cam.tolist(), sc.obs_pt.tolist()))
+    pool = np.arange(sc.n) if cams is None else np.asarray(cams)
+    add = set()
+    while len(add) < k:
+        c, j = int(rng.choice(pool)), int(rng.integers(0, sc.m))
+        if (c, j) not in have and (c, j) not in add:
+            add.add((c, j))
+    add = sorted(add, key=lambda cj: (cj[1], cj[0]))
+    ac = np.array([c for c, _ in add], np.int32)
+    ap = np.array([j for _, j in add], np.int32)
+    Rs = np.stack([_rotation(sc.cams[c, 0:3]) for c in ac])
+    Xc = np.einsum("tij,tj->ti", Rs, sc.pts[ap]) + sc.cams[ac, 3:6]
+    x = Xc[:, :2] / Xc[:, 2:3]
+    rho2 = (x * x).sum(1)
+    g = 1.0 + sc.cams[ac, 7] * rho2 + sc.cams[ac, 8] * rho2 * rho2
+    au = sc.cams[ac, 6:7] * g[:, None] * x + rng.normal(0.0, 1.0, size=x.shape)
+    cam = np.concatenate([sc.obs_cam, ac])
+    pt = np.concatenate([sc.obs_pt, ap])
+    u = np.concatenate([sc.obs_u, au])
+    order = np.lexsort((cam, pt))
+    merged = Scene(sc.cams, sc.pts, cam[order].astype(np.int32), pt[order].astype(np.int32), u[order],
+                   sc.sigma, None, dict(sc.meta, added=k))
+    added = Scene(sc.cams, sc.pts, ac, ap, au, sc.sigma, None, {"kind": "added"})
+    return merged, added
+
+
+def _rotation(r: np.ndarray) -> np.ndarray:
+    th = np.linalg.norm(r)
+    K = np.array([[0.0, -r[2], r[1]], [r[2], 0.0, -r[0]], [-r[1], r[0], 0.0]])
+    return np.eye(3) + np.sin(th) / th * K + (1.0 - np.cos(th)) / th ** 2 * K @ K
 
 
 def decomposition_orders(n: int, decompositions: int, seed=7) -> np.ndarray:
