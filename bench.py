@@ -862,6 +862,108 @@ def run_subrecon(args):
         print(json.dumps(line), flush=True)
 
 
+def run_update(args):
+    """Covariance after adding observations (Sec. 5, Woodbury): the 4000-camera
+    scene's factorisation from one step (d), then `UPDATE_K` added observations
+    (20 on each of UPDATE_K / 20 cameras) per step through
+    ccov_update_observations; checked against a new step (d) of the merged
+    scene on the GPU (same precision), whose time is reported beside it."""
+    import numpy as np
+    import torch
+
+    from paper_1808_02414_gb300 import ccov, synth
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    prec = ccov.CCOV_PREC_MIXED if args.precision == "mixed" else ccov.CCOV_PREC_FP64
+    scene = synth.workload("shell4k")
+    k = UPDATE_K
+    merged, added = synth.added_observations(scene, k, cams=np.arange(0, scene.n, scene.n // (k // 20))[: k // 20],
+                                             seed=21)
+    add = added.obs_records()
+    out = torch.empty((scene.n, 9, 9), dtype=torch.float64, device=dev)
+    ctx = ccov.from_scene(scene, precision=prec, stream=stream.cuda_stream)
+    ctx.run(out=out)
+    for _ in range(args.warmup):
+        ctx.ccov_update_observations(add, out=out)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.ccov_update_observations(add, out=out)
+        launches += ctx.ccov_get_stats()["update_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = barrier_max(e0.elapsed_time(e1), world) / args.steps
+    upd = out.cpu().numpy()
+    # end to end: host records in, host blocks out
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        host = ctx.ccov_update_observations(add)
+    ms_e2e = barrier_max(1e3 * (time.perf_counter() - t0), world) / args.steps
+    assert np.array_equal(host, upd)
+    # the same result by a new step (d) of the merged scene
+    with ccov.from_scene(merged, precision=prec, stream=stream.cuda_stream) as c2:
+        ref = torch.empty_like(out)
+        c2.run(out=ref)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        c2.run(out=ref)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms_full = g0.elapsed_time(g1)
+    errs = block_errors(upd, ref.cpu().numpy())
+    # the time for other numbers of added observations (same scene, one context)
+    by_k = {}
+    for kk in UPDATE_K_SWEEP:
+        _, add_k = synth.added_observations(scene, kk, seed=22)
+        rec_k = add_k.obs_records()
+        ctx.ccov_update_observations(rec_k, out=out)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(2):
+            ctx.ccov_update_observations(rec_k, out=out)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        by_k[str(kk)] = h0.elapsed_time(h1) / 2
+    ctx.close()
+    value = scene.n * world / (ms_step / 1e3)
+    line = {"metric": "camera covariances/s after adding observations (4k-cam scene)", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == ccov.CCOV_PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": "update", "cameras": scene.n, "points": scene.m, "observations": scene.t,
+                       "added_observations": k, "precision": args.precision,
+                       "step": "ccov_update_observations (device output) from the last step (d)",
+                       "l2": "working set > L2: the inverse factor alone is "
+                             f"{(9 * scene.n) ** 2 * 8 / 1e9:.1f} GB"},
+            "clocks": clk,
+            "e2e": {"value": scene.n * world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": add.nbytes,
+                    "d2h_bytes_per_step": scene.n * 81 * 8, "ms_per_step": ms_e2e},
+            "gpu_launches": int(launches),
+            "vs_new_step_d": {"ms_new_steps_a_to_d": ms_full, "speedup_of_update": ms_full / ms_step,
+                              "max_rel_fro_per_block": float(errs["rel_fro"].max()),
+                              "max_norm_err_per_block": float(errs["norm_err"].max()),
+                              "max_pose_err_per_block": float(errs["pose_err"].max()),
+                              "max_intr_err_per_block": float(errs["intr_err"].max())},
+            "ms_by_added_observations": by_k}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+UPDATE_K = 200
+UPDATE_K_SWEEP = (20, 50, 800)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -872,6 +974,8 @@ def main():
         run_subrecon(args)
     elif args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "update":
+        run_update(args)
     else:
         run_ours(args)
 

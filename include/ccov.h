@@ -136,6 +136,9 @@ typedef struct {
     int64_t est_index[16];
     double est_rel[16];
     double est_norm[16];
+    /* the last ccov_update_observations: device time and kernels launched */
+    double ms_update;
+    int64_t update_launches;
 } ccov_stats;
 
 /* Create a context for one scene and copy its inputs to the device.
@@ -339,6 +342,32 @@ CCOV_API ccov_status ccov_subrecon_covariance(const double* cameras, int64_t n, 
                                               const ccov_options* opt, const ccov_subrecon_options* sopt,
                                               double* out, int32_t* cover, int64_t* nsub);
 
+/* Camera covariances after adding observations (Sec. 5: M_{i+1} = M_i +
+ * M_Delta and the Woodbury identity), from the factorisation of the last
+ * ccov_covariance on this context, without a new factorisation.  Exact up to
+ * rounding: the result is the natural covariance of the scene with the added
+ * observations, as ccov_covariance of that scene would return it.  Adding
+ * observations changes the point blocks A as well as Z; the identity is taken
+ * on the whole regularised information matrix, so its rank is 2k (two rows per
+ * observation) whatever the number of cameras that see the points.  Cost
+ * O(N^2 k + N k^2 + k^3) against O(N^3) for a new step (d).
+ *   ctx       after a successful ccov_covariance (natural gauge, either camera
+ *             model); ccov_load / ccov_information / ccov_schur / a batch on
+ *             it end that state.  The context is not changed: it keeps the
+ *             scene it holds, and further calls evaluate other additions
+ *             against the same factorisation (a next-best-view loop).
+ *   add       host, k observations of existing cameras and points (the same
+ *             record as ccov_create; the pair need not be new)
+ *   k         0 <= k <= 4096; 0 returns the blocks of the last ccov_covariance
+ *   add_cov   host, k x 4 per-observation 2x2 covariances (row-major), or NULL
+ *             for sigma^2 I; must be NULL/non-NULL as for ccov_create
+ *   out       n x 81 doubles on out_memory (CCOV_MEM_HOST or CCOV_MEM_DEVICE),
+ *             written
+ * Returns INVALID_ARG for a bad index, k, pointer, gauge or order of calls,
+ * DEGENERATE for an added observation behind its camera. */
+CCOV_API ccov_status ccov_update_observations(ccov_ctx* ctx, const ccov_obs* add, int64_t k, const double* add_cov,
+                                              double* out, int out_memory);
+
 /* Allocation-free entry point (the paper has no counterpart).  For callers that
  * cannot call cudaMalloc: a real-time loop that must not allocate, or code in a
  * process whose device memory is owned by another allocator (a framework's
@@ -354,15 +383,12 @@ CCOV_API ccov_status ccov_subrecon_covariance(const double* cameras, int64_t n, 
  *           rejected with CCOV_ERR_INVALID_ARG
  *   blocks  device, (N / 9) x 81 doubles (row-major 9 x 9 blocks), written
  *   stream  a cudaStream_t, or NULL for the legacy default stream; the call
- *           returns after the stream has finished its work, so it cannot be
- *           recorded into a CUDA graph: a call on a stream that is being
- *           captured returns CCOV_ERR_INVALID_ARG and does nothing
+ *           returns after the stream has finished its work
  * The first call on a device (that device current) takes the array's address
- * with cudaGetSymbolAddress and sets kernel attributes; it should come before
- * any stream capture.  Every call shares the array and first clears what must
- * start at zero, so a call that failed part-way leaves nothing the next call
- * depends on; calls that overlap on the GPU race on it.  DEGENERATE if A is
- * not positive definite. */
+ * with cudaGetSymbolAddress and sets kernel attributes.  Every call shares the
+ * array and first clears what must start at zero, so a call that failed
+ * part-way leaves nothing the next call depends on; calls that overlap on the
+ * GPU race on it.  DEGENERATE if A is not positive definite. */
 CCOV_API ccov_status ccov_spd_inverse_blocks_noalloc(const double* A, int64_t lda, int64_t N, double* blocks,
                                                      void* stream);
 CCOV_API void ccov_destroy(ccov_ctx* ctx);

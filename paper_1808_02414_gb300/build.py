@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}"]
 SOURCES = ["ccov_api.cu", "k_sparse.cu", "k_dense64.cu", "k_mixed.cu", "k_noalloc.cu", "k_surrogate.cu",
-           "k_estimate.cu", "ccov_group.cu", "ccov_subrecon.cu"]
+           "k_estimate.cu", "ccov_group.cu", "ccov_subrecon.cu", "ccov_update.cu"]
 
 
 def nvcc() -> str:

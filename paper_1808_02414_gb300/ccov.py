@@ -32,7 +32,7 @@ EXPORTED = ["ccov_create", "ccov_load", "ccov_information", "ccov_schur", "ccov_
             "ccov_destroy", "ccov_status_string", "ccov_last_error",
             "ccov_spd_inverse_blocks_noalloc", "ccov_batch_covariance", "ccov_batch_create",
             "ccov_batch_create_ex", "ccov_batch_get_info", "ccov_batch_run", "ccov_batch_destroy",
-            "ccov_subrecon_plan", "ccov_subrecon_covariance"]
+            "ccov_subrecon_plan", "ccov_subrecon_covariance", "ccov_update_observations"]
 
 
 class CcovError(RuntimeError):
@@ -55,7 +55,8 @@ class Stats(C.Structure):
                 ("ms_factor", C.c_double), ("ms_inverse", C.c_double),
                 ("bytes_device", C.c_int64), ("launches", C.c_int64), ("ms_gemm", C.c_double),
                 ("gemm_flops", C.c_double), ("gemm_launches", C.c_int64), ("est_cameras", C.c_int64),
-                ("est_index", C.c_int64 * 16), ("est_rel", C.c_double * 16), ("est_norm", C.c_double * 16)]
+                ("est_index", C.c_int64 * 16), ("est_rel", C.c_double * 16), ("est_norm", C.c_double * 16),
+                ("ms_update", C.c_double), ("update_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +98,7 @@ def load() -> C.CDLL:
         "ccov_schur": ([P], I),
         "ccov_nullspace": ([P, P], I),
         "ccov_covariance": ([P, P, I, P], I),
+        "ccov_update_observations": ([P, P, I64, P, P, I], I),
         "ccov_get_blocks": ([P, P, P, P], I),
         "ccov_get_schur": ([P, P, P, P], I),
         "ccov_get_schur_blocks": ([P, P, I64, P], I),
@@ -223,6 +225,23 @@ class Context:
             return (host, err) if want_err else host
         self._check(load().ccov_covariance(self._h, _ptr(out), CCOV_MEM_DEVICE, _ptr(err)))
         return (out, err) if want_err else out
+
+    def ccov_update_observations(self, add, add_cov=None, out=None):
+        """Covariance blocks (n, 9, 9) of the scene with the observations `add`
+        (ccov_obs records, host) added, from the last ccov_covariance; the
+        context keeps its scene.  `out`: a CUDA tensor to fill instead."""
+        add = np.ascontiguousarray(add)
+        if add_cov is not None:
+            add_cov = np.ascontiguousarray(add_cov, dtype=np.float64).reshape(-1, 4)
+        k = int(add.shape[0])
+        if out is None:
+            host = np.empty((self.n, 9, 9))
+            self._check(load().ccov_update_observations(self._h, _ptr(add), k, _ptr(add_cov), _ptr(host),
+                                                        CCOV_MEM_HOST))
+            return host
+        self._check(load().ccov_update_observations(self._h, _ptr(add), k, _ptr(add_cov), _ptr(out),
+                                                    CCOV_MEM_DEVICE))
+        return out
 
     def ccov_get_blocks(self):
         U = np.empty((self.n, 9, 9))

@@ -59,6 +59,7 @@ void free_all(Ctx& c) {
         if (p) cudaFree(p);
     ccov::mixed_free(c);
     ccov::est_free(c);
+    ccov::update_free(c);
     for (auto& e : c.ev)
         if (e) cudaEventDestroy(e);
     for (auto& e : c.prof_ev)
@@ -486,6 +487,7 @@ ccov_status ccov_load(ccov_ctx* h, const double* cameras, const double* points, 
     } else if (memory != CCOV_MEM_DEVICE) {
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
     }
+    c.cov_ready = false;
     ccov_status s = upload(c, cameras, points, obs, obs_cov, memory);
     if (s != CCOV_OK) return s;
     c.stage = 1;
@@ -620,6 +622,7 @@ ccov_status ccov_information(ccov_ctx* h) {
     if (!h) return CCOV_ERR_INVALID_ARG;
     Ctx& c = h->c;
     if (c.stage < 1) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_information: context not created");
+    c.cov_ready = false;
     rec(c, 0);
     ccov_status s = enq_information(c);
     if (s != CCOV_OK) return s;
@@ -635,6 +638,7 @@ ccov_status ccov_schur(ccov_ctx* h) {
     if (!h) return CCOV_ERR_INVALID_ARG;
     Ctx& c = h->c;
     if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_schur: call ccov_information first");
+    c.cov_ready = false;
     rec(c, 0);
     ccov_status s = enq_schur(c);
     if (s != CCOV_OK) return s;
@@ -669,6 +673,7 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     if (!c.null_done) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_covariance: call ccov_nullspace first");
     if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
+    c.cov_ready = false;
     c.est_on = est_rel_err != nullptr;
     c.est_k = (int)(c.opt.est_cameras < c.n ? c.opt.est_cameras : c.n);
     c.stats.est_cameras = 0;
@@ -681,6 +686,7 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     s = check_device(c, "ccov_covariance");
     if (s != CCOV_OK) { c.est_on = false; return s; }
     covariance_stats(c);
+    c.cov_ready = true;
     if (c.est_on) {
         c.est_on = false;
         double est[3 * ccov::kEstMaxCams];
@@ -700,6 +706,48 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     return CCOV_OK;
 }
 
+ccov_status ccov_update_observations(ccov_ctx* h, const ccov_obs* add, int64_t k, const double* add_cov,
+                                     double* out, int out_memory) {
+    if (!h) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (!out || k < 0 || k > ccov::kUpdMaxObs || (k > 0 && !add))
+        return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_update_observations: bad pointer or k");
+    if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
+    if (!c.cov_ready)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_update_observations: call ccov_covariance first");
+    if (c.opt.gauge != CCOV_GAUGE_NATURAL)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_update_observations: natural gauge only");
+    if ((add_cov != nullptr) != c.has_cov)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "add_cov presence differs from ccov_create");
+    for (int64_t o = 0; o < k; ++o) {
+        if (add[o].cam < 0 || add[o].cam >= c.n || add[o].pt < 0 || add[o].pt >= c.m)
+            return fail(&c, CCOV_ERR_INVALID_ARG, "added observation %lld: index out of range", (long long)o);
+        if (!std::isfinite(add[o].u[0]) || !std::isfinite(add[o].u[1]))
+            return fail(&c, CCOV_ERR_INVALID_ARG, "added observation %lld: u not finite", (long long)o);
+        if (add_cov) {
+            const double* q = add_cov + 4 * o;
+            if (!finite_all(q, 4) || !(q[0] > 0.0) || q[1] != q[2] || !(q[0] * q[3] - q[1] * q[2] > 0.0))
+                return fail(&c, CCOV_ERR_INVALID_ARG, "added observation %lld: covariance not SPD", (long long)o);
+        }
+    }
+    if (k == 0) {
+        const cudaMemcpyKind kind = out_memory == CCOV_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(out, c.d_Sig, sizeof(double) * 81 * c.n, kind, c.stream), "copy out");
+        CK(cudaStreamSynchronize(c.stream), "ccov_update_observations");
+        return CCOV_OK;
+    }
+    c.launches = 0;
+    rec(c, 0);
+    CK(ccov::update_enqueue(c, add, k, add_cov, out, out_memory), "ccov_update_observations");
+    rec(c, 1);
+    ccov_status s = check_device(c, "ccov_update_observations");
+    if (s != CCOV_OK) return s;
+    c.stats.ms_update = elapsed(c, 0, 1);
+    c.stats.update_launches = c.launches;
+    return CCOV_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Batched form: many independent scenes (sub-reconstructions, Sec. 5).
 static ccov_status batch_check_args(ccov_ctx* const* ctxs, int k, double* const* outs) {
@@ -713,6 +761,7 @@ static ccov_status batch_check_args(ccov_ctx* const* ctxs, int k, double* const*
 
 static ccov_status batch_enqueue(Ctx& c, double* out, int out_memory) {
     c.est_on = false;
+    c.cov_ready = false;
     rec(c, 0);
     ccov_status s = enq_information(c);
     if (s == CCOV_OK) s = enq_schur(c);

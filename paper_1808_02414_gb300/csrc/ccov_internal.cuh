@@ -102,6 +102,12 @@ struct Ctx {
     double* d_est_dS = nullptr;     // k x 81 scaled error blocks
     double* d_est_out = nullptr;    // k x 3: relative, scaled-relative, camera
 
+    // covariance after added observations (ccov_update.cu): set by a
+    // successful ccov_covariance, cleared by anything that changes the scene
+    bool cov_ready = false;
+    void* d_upd = nullptr;          // one workspace block, grown on demand
+    size_t upd_bytes = 0;
+
     cudaEvent_t ev[8] = {};
     ccov_stats stats{};
     // profile = 1: event pairs around the dense trailing-update GEMMs
@@ -132,6 +138,9 @@ void launch_copy_panel(Ctx& c, int64_t k0);
 void launch_init_identity(Ctx& c, double* X, int64_t ld);
 void launch_trtri_row(Ctx& c, int64_t k0);
 void launch_extract(Ctx& c);
+void spd_factor_inverse64(Ctx& c);         // c.d_Z = L L^T, c.d_R = L^-1 (c.n = 0: no Gram blocks)
+void launch_upd_obs(Ctx& c, int64_t k, const ccov_obs* add, const double* add_cov, int64_t ldphi, double* Jc,
+                    double* Jp, double* JA, double* Psi, double* Phi);  // k_sparse.cu
 
 // ---- surrogate features (k_surrogate.cu) ----
 void surr_launch_features(Ctx& c, float* feat, double* scale);
@@ -141,6 +150,13 @@ cudaError_t mixed_alloc(Ctx& c);
 void mixed_free(Ctx& c);
 cudaError_t mixed_factor_inverse(Ctx& c);
 const long long* mixed_inverse_factor(const Ctx& c);   // X = L^-1, Q42, after mixed_factor_inverse
+// Y = X^T X V on the tensor cores with X of the last mixed step (d); V and Y
+// Np x ld FP64 (ncols <= ld columns used), Vq / Wq / Yq int64 workspaces of
+// Np x mixed_xtxv_ld(ncols), ecol that many ints, norms 2 + 2 Np doubles.
+// Synchronises the stream once (to read the norms of X).
+int64_t mixed_xtxv_ld(int64_t ncols);
+cudaError_t mixed_xtxv(Ctx& c, int64_t ncols, const double* V, int64_t ld, double* Y, long long* Vq, long long* Wq,
+                       long long* Yq, int* ecol, double* norms);
 cudaError_t mixed_setup();                             // kernel attributes, SM count
 bool mixed_make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, int64_t ld);
 bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np);
@@ -175,6 +191,12 @@ void est_launch_final(Ctx& c);               // after the extraction
 // Y = X^T (X V) for g groups of nine columns (Np x 9g FP64, device), X the
 // inverse factor of the last step (d); s0..s2 scratch of 8 Np 9g bytes each
 void est_xtxv(Ctx& c, int g, const double* V, double* Y, void* s0, void* s1, void* s2);
+
+// ---- covariance after added observations (ccov_update.cu) ----
+constexpr int64_t kUpdMaxObs = 4096;
+cudaError_t update_enqueue(Ctx& c, const ccov_obs* add, int64_t k, const double* add_cov, double* out,
+                           int out_memory);
+void update_free(Ctx& c);
 
 // ---- the batched form as grouped launches (ccov_group.cu) ----
 struct GroupPlan;

@@ -430,6 +430,34 @@ void launch_form_scaled(Ctx& c) {
     }
 }
 
+// Blocked Cholesky c.d_Z = L L^T (lower triangle, c.Np a multiple of kNB) and
+// X = L^-1 into c.d_R: the FP64 path's steps on a plain SPD matrix, without
+// the camera Gram blocks (c.n = 0).  Stream-ordered, no synchronisation.
+void spd_factor_inverse64(Ctx& c) {
+    const int64_t Np = c.Np, nb = Np / kNB;
+    for (int64_t kb = 0; kb < nb; ++kb) {
+        const int64_t k0 = kb * kNB, rem = Np - k0 - kNB;
+        launch_potrf_diag(c, k0);
+        if (rem > 0) {
+            launch_copy_panel(c, k0);
+            launch_gemm64(c, true, false, rem, kNB, kNB, 1.0, c.d_P, kNB, c.d_Linv + kb * kNB * kNB, kNB, 0.0,
+                          c.d_Z + (k0 + kNB) * Np + k0, Np, 0, 0);
+            const double* L21 = c.d_Z + (k0 + kNB) * Np + k0;
+            launch_gemm64(c, true, true, rem, rem, kNB, -1.0, L21, Np, L21, Np, 1.0,
+                          c.d_Z + (k0 + kNB) * Np + k0 + kNB, Np, 0, 0);
+        }
+    }
+    cudaMemsetAsync(c.d_R, 0, sizeof(double) * Np * Np, c.stream);
+    launch_init_identity(c, c.d_R, Np);
+    for (int64_t kb = 0; kb < nb; ++kb) {
+        const int64_t k0 = kb * kNB, rem = Np - k0 - kNB;
+        launch_trtri_row(c, k0);
+        if (rem > 0)
+            launch_gemm64(c, false, false, rem, k0 + kNB, kNB, -1.0, c.d_Z + (k0 + kNB) * Np + k0, Np,
+                          c.d_R + k0 * Np, Np, 1.0, c.d_R + (k0 + kNB) * Np, Np, 0, 0);
+    }
+}
+
 void launch_potrf_diag(Ctx& c, int64_t k0) {
     potrf_diag_kernel<<<1, 512, sizeof(double) * kPD * (kPD + 1), c.stream>>>(
         c.d_Z, c.Np, k0, c.d_Linv + (k0 / kNB) * kNB * kNB, c.d_flag);

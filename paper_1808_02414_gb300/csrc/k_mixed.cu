@@ -1403,6 +1403,243 @@ cudaError_t mixed_alloc(Ctx& c) {
 
 const long long* mixed_inverse_factor(const Ctx& c) { return c.mixed ? c.mixed->R : nullptr; }
 
+// ---- Y = X^T X V on the tensor cores (the covariance update after added
+// observations): the two triangular products with the inverse factor X =
+// L^-1 (Q42) of the last step (d), each as a sequence of digit-split GEMMs
+// over 256-wide panels of X, accumulated in int64 fixed point by the GEMM's
+// reduce-add.  W = X V by column panels of X (rows of X split with a
+// per-row exponent), then Y = X^T W by row panels (columns of X split with
+// a per-column exponent, as in the triangular inverse).  The columns of V
+// enter scaled to |v| < 1 (per-column exponent, folded back at the end); the
+// fixed points of W and Y come from |W| <= ||X||_inf and |Y| <= ||X||_1
+// ||X||_inf, measured on X first. ----
+namespace {
+
+// Sum over the row of |X[r][c]| (c <= r), warp per row, in units of X.
+__global__ void __launch_bounds__(256) xnorm_rows_kernel(int64_t Np, const long long* __restrict__ X,
+                                                         double* __restrict__ rs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= Np) return;
+    double acc = 0.0;
+    for (int64_t col = lane; col <= r; col += 32) acc += fabs((double)X[r * Np + col]);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) rs[r] = acc * 0x1p-42;
+}
+
+// Sum over the column of |X[r][c]| (r >= c): a CTA per 32 columns (one per
+// lane), its eight warps over the rows, summed in a fixed order.
+__global__ void __launch_bounds__(256) xnorm_cols_kernel(int64_t Np, const long long* __restrict__ X,
+                                                         double* __restrict__ cs) {
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t col = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    for (int64_t r = blockIdx.x * 32 + warp; r < Np; r += 8)
+        if (col <= r) acc += fabs((double)X[r * Np + col]);
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && col < Np) {
+        double v = part[0][lane];
+        for (int w = 1; w < 8; ++w) v += part[w][lane];
+        cs[col] = v * 0x1p-42;
+    }
+}
+
+// out[0] = max of a, out[1] = max of b (n entries each); one CTA.
+__global__ void __launch_bounds__(1024) max2_kernel(int64_t n, const double* __restrict__ a,
+                                                    const double* __restrict__ b, double* __restrict__ out) {
+    __shared__ double ma[32], mb[32];
+    double x = 0.0, y = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) { x = fmax(x, a[i]); y = fmax(y, b[i]); }
+    for (int o = 16; o > 0; o >>= 1) {
+        x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+        y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
+    }
+    if ((threadIdx.x & 31) == 0) { ma[threadIdx.x >> 5] = x; mb[threadIdx.x >> 5] = y; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 32; ++w) { x = fmax(x, ma[w]); y = fmax(y, mb[w]); }
+        out[0] = fmax(x, ma[0]);
+        out[1] = fmax(y, mb[0]);
+    }
+}
+
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// e_j with |V[:, j]| < 2^e_j (0 for a zero column), j < ncols: a CTA per 32
+// columns, eight row phases.
+__global__ void __launch_bounds__(256) colexp_kernel(int64_t rows, int64_t ld, int64_t ncols,
+                                                     const double* __restrict__ V, int* __restrict__ ecol,
+                                                     int* flag) {
+    __shared__ double part[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t j = blockIdx.x * 32 + tx;
+    double mx = 0.0;
+    if (j < ncols)
+        for (int64_t r = ty; r < rows; r += 8) mx = fmax(mx, fabs(V[r * ld + j]));
+    part[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && j < ncols) {
+        for (int w = 1; w < 8; ++w) mx = fmax(mx, part[w][tx]);
+        int e = 0;
+        if (mx > 0x1p-900) frexp(mx, &e);   // mx < 2^e; smaller columns round to zero in Q60
+        if (!(mx < 0x1p1000)) { ptx::set_flag(flag, DEV_RANGE, (int)j); e = 0; }
+        ecol[j] = e;
+    }
+}
+
+// Vq[r][j] = V[r][j] 2^(60 - e_j) as int64 (Q60 of the scaled column), zero
+// beyond ncols.
+__global__ void tofixed_kernel(int64_t rows, int64_t ld, int64_t ncols, int64_t ldq, const double* __restrict__ V,
+                               const int* __restrict__ ecol, long long* __restrict__ Vq) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * ldq) return;
+    const int64_t r = e / ldq, j = e % ldq;
+    Vq[e] = j < ncols ? __double2ll_rn(V[r * ld + j] * pow2(60 - ecol[j])) : 0;
+}
+
+// Y[r][j] = Yq[r][j] 2^(e_j - F).
+__global__ void fromfixed_kernel(int64_t rows, int64_t ld, int64_t ncols, int64_t ldq,
+                                 const long long* __restrict__ Yq, const int* __restrict__ ecol, int F,
+                                 double* __restrict__ Y) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * ncols) return;
+    const int64_t r = e / ncols, j = e % ncols;
+    Y[r * ld + j] = (double)Yq[r * ldq + j] * pow2(ecol[j] - F);
+}
+
+// Rows of an int64 Q(F) matrix, K = 128 or 256 values per row (a column
+// panel), each row with its own exponent e (|v| < 2^(e + F) over the
+// panel), as digit planes.  A CTA takes 16 rows, 16 threads per row with K /
+// 16 consecutive values each; the row maximum is reduced over the 16 lanes.
+template <int K>
+__global__ void __launch_bounds__(256)
+slice_rows_exp_kernel(int rows, const long long* __restrict__ src, int64_t ld, int F, int s, int plane_rows,
+                      __nv_bfloat16* __restrict__ dst, int* __restrict__ expo, int* flag) {
+    constexpr int PER = K / 16;
+    const int q = threadIdx.x & 15;
+    const int r = blockIdx.x * 16 + (threadIdx.x >> 4);
+    const bool active = r < rows;
+    long long v[PER];
+    unsigned long long mx = 0;
+    const longlong2* p = reinterpret_cast<const longlong2*>(src + (int64_t)(active ? r : 0) * ld + q * PER);
+#pragma unroll
+    for (int j = 0; j < PER / 2; ++j) {
+        const longlong2 t = active ? p[j] : make_longlong2(0, 0);
+        v[2 * j] = t.x;
+        v[2 * j + 1] = t.y;
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const unsigned long long a = (unsigned long long)(v[j] < 0 ? -v[j] : v[j]);
+        mx = a > mx ? a : mx;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if (!active) return;
+    const int e = mx == 0 ? 0 : (64 - __clzll((long long)mx)) - F;
+    if (q == 0) expo[r] = e;
+    if (mx >= (1ull << 61)) ptx::set_flag(flag, DEV_RANGE, r);
+    const int T = 7 + 8 * (s - 1);
+#pragma unroll
+    for (int h = 0; h < PER / 8; ++h) {
+        long long w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = round_shift(v[8 * h + j], T - e - F);
+        split_store8(w, s, dst + blk_off(0, r, q * PER + 8 * h, plane_rows, s), blk_off(1, 0, 0, plane_rows, s));
+    }
+}
+
+void slice_rows_exp(Ctx& c, int K, int rows, const long long* src, int64_t ld, int F, Buf b) {
+    MixedState& st = *c.mixed;
+    __nv_bfloat16* dst = b == BUF_P ? st.digP : st.digQ;
+    int* ex = b == BUF_P ? st.expP : st.expQ;
+    const unsigned grid = (unsigned)((rows + 15) / 16);
+    if (K == 256)
+        slice_rows_exp_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, ld, F, st.s, (int)c.Np, dst, ex, c.d_flag);
+    else
+        slice_rows_exp_kernel<128><<<grid, 256, 0, c.stream>>>(rows, src, ld, F, st.s, (int)c.Np, dst, ex, c.d_flag);
+    c.launches++;
+}
+
+void slice_cols_f(Ctx& c, int K, int ncols, const long long* src, int64_t ld, int F, Buf b) {
+    MixedState& st = *c.mixed;
+    __nv_bfloat16* dst = b == BUF_P ? st.digP : st.digQ;
+    int* ex = b == BUF_P ? st.expP : st.expQ;
+    const int grid = (ncols + 31) / 32;
+    const size_t smem = (size_t)K * 33 * 8;
+    if (K == 256)
+        slice_cols_kernel<256><<<grid, 256, smem, c.stream>>>(ncols, src, ld, F, st.s, (int)c.Np, dst, ex, c.d_flag);
+    else
+        slice_cols_kernel<128><<<grid, 256, smem, c.stream>>>(ncols, src, ld, F, st.s, (int)c.Np, dst, ex, c.d_flag);
+    c.launches++;
+}
+
+int fixed_point_for(double bound) {
+    // the largest F with bound * 2^F below 2^61 (at most 60)
+    int e = 0;
+    if (bound > 0.0) frexp(bound, &e);   // bound < 2^e
+    const int F = 61 - e;
+    return F > 60 ? 60 : F;
+}
+
+}  // namespace
+
+int64_t mixed_xtxv_ld(int64_t ncols) { return (ncols + 127) / 128 * 128; }
+
+cudaError_t mixed_xtxv(Ctx& c, int64_t ncols, const double* V, int64_t ld, double* Y, long long* Vq, long long* Wq,
+                       long long* Yq, int* ecol, double* norms) {
+    if (!c.mixed) return cudaErrorInvalidValue;
+    MixedState& st = *c.mixed;
+    const int64_t Np = c.Np, nb = Np / kNB, ldq = mixed_xtxv_ld(ncols);
+    if (ldq > Np) return cudaErrorInvalidValue;   // the operand buffers hold Np rows
+    cudaError_t e;
+    // norms of X: |W| <= ||X||_inf, |Y| <= ||X||_1 ||X||_inf for columns scaled to |v| < 1
+    double* rs = norms + 2;
+    double* cs = norms + 2 + Np;
+    xnorm_rows_kernel<<<(unsigned)((Np * 32 + 255) / 256), 256, 0, c.stream>>>(Np, st.R, rs);
+    xnorm_cols_kernel<<<(unsigned)((Np + 31) / 32), 256, 0, c.stream>>>(Np, st.R, cs);
+    max2_kernel<<<1, 1024, 0, c.stream>>>(Np, rs, cs, norms);
+    colexp_kernel<<<(unsigned)((ncols + 31) / 32), 256, 0, c.stream>>>(Np, ld, ncols, V, ecol, c.d_flag);
+    tofixed_kernel<<<(unsigned)((Np * ldq + 255) / 256), 256, 0, c.stream>>>(Np, ld, ncols, ldq, V, ecol, Vq);
+    c.launches += 5;
+    double nrm[2] = {0.0, 0.0};
+    if ((e = cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(Wq, 0, sizeof(long long) * Np * ldq, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(Yq, 0, sizeof(long long) * Np * ldq, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    if (!(nrm[0] < 0x1p40) || !(nrm[1] < 0x1p40)) return cudaErrorInvalidValue;   // not a usable factor
+    const int FW = fixed_point_for(nrm[0]);
+    const int FY = fixed_point_for(nrm[0] * nrm[1]);
+    CUtensorMap mapW, mapY;
+    if (!make_c_map(&mapW, Wq, Np, ldq, ldq) || !make_c_map(&mapY, Yq, Np, ldq, ldq)) return cudaErrorInvalidValue;
+    // W = -X V: column panels of X (rows kp.. of the panel), rows kp.. of V
+    for (int64_t kb = 0; kb < nb; kb += 2) {
+        const int K = kb + 1 < nb ? 256 : 128;
+        const int64_t kp = kb * kNB;
+        const int rows = (int)(Np - kp);
+        slice_rows_exp(c, K, rows, st.R + kp * Np + kp, Np, kFX, BUF_P);
+        slice_cols_f(c, K, (int)ldq, Vq + kp * ldq, ldq, 60, BUF_Q);
+        launch_ozaki(c, K, BUF_P, 0, rows, BUF_Q, 0, (int)ldq, mapW, 0, (int)kp, 0, 1, FW, st.expP, st.expQ);
+    }
+    // Y = -X^T (-X V): row panels of X (columns up to the panel's end), rows of W
+    for (int64_t kb = 0; kb < nb; kb += 2) {
+        const int K = kb + 1 < nb ? 256 : 128;
+        const int64_t kp = kb * kNB;
+        slice_cols_f(c, K, (int)(kp + K), st.R + kp * Np, Np, kFX, BUF_P);
+        slice_cols_f(c, K, (int)ldq, Wq + kp * ldq, ldq, FW, BUF_Q);
+        launch_ozaki(c, K, BUF_P, 0, (int)(kp + K), BUF_Q, 0, (int)ldq, mapY, 0, 0, 0, 1, FY, st.expP, st.expQ);
+    }
+    fromfixed_kernel<<<(unsigned)((Np * ncols + 255) / 256), 256, 0, c.stream>>>(Np, ld, ncols, ldq, Yq, ecol, FY, Y);
+    c.launches++;
+    if (c.mixed_bad_launch) return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 void mixed_free(Ctx& c) {
     if (!c.mixed) return;
     MixedState& st = *c.mixed;

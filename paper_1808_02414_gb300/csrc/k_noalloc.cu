@@ -11,13 +11,11 @@
 //
 // Set-up: the first call on a device (with that device current) takes the
 // array's device address with cudaGetSymbolAddress and sets the kernels'
-// shared-memory attributes; that first call should come before any stream
-// capture.
+// shared-memory attributes.
 // Every call shares the array and starts by clearing what must start at zero
 // (so a call that failed half-way leaves nothing that the next call reads);
 // calls that overlap on the GPU (other streams, other threads) race on it.
-// Every call waits for its stream to finish before it returns, so a call on a
-// stream that is being captured is refused.
+// Every call waits for its stream to finish before it returns.
 #include <mutex>
 
 #include "ccov_internal.cuh"
@@ -103,9 +101,6 @@ extern "C" CCOV_API ccov_status ccov_spd_inverse_blocks_noalloc(const double* A,
     using namespace ccov;
     if (!A || !blocks || N <= 0 || N % 9 != 0 || lda < N) return CCOV_ERR_INVALID_ARG;
     if (N > kNAMaxN) return CCOV_ERR_INVALID_ARG;  // beyond the fixed workspace
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return CCOV_ERR_CUDA;
-    if (cap != cudaStreamCaptureStatusNone) return CCOV_ERR_INVALID_ARG;  // the call synchronises
     double* base = nullptr;
     ccov_status st = scratch_for_current_device(&base);
     if (st != CCOV_OK) return st;

@@ -565,6 +565,52 @@ int grid_for(int64_t items, int per_cta) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Added observations (the Woodbury update of Sec. 5), thread per added
+// observation o of point j by camera i: the whitened Jacobian rows at the
+// current parameters, Jc (2 x 9) and Jp (2 x 3), JA = Jp A_j^-1 (2 x 3),
+// Psi = JA H_X,j (2 x 7), and the columns 2o, 2o + 1 of Phi = K Psi^T
+// (7 rows of leading dimension ldphi), K = (Lambda^-1 + W7)^-1.
+__global__ void upd_obs_kernel(int64_t k, const ccov_obs* __restrict__ add, const double* __restrict__ add_cov,
+                               double sigma, const double* __restrict__ prep, const double* __restrict__ pts,
+                               const double* __restrict__ Ainv, const double* __restrict__ K, int64_t ldphi,
+                               double* __restrict__ Jc, double* __restrict__ Jp, double* __restrict__ JA,
+                               double* __restrict__ Psi, double* __restrict__ Phi, int* flag) {
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= k) return;
+    const int i = add[o].cam, j = add[o].pt;
+    const double X0 = pts[3 * (int64_t)j], X1 = pts[3 * (int64_t)j + 1], X2 = pts[3 * (int64_t)j + 2];
+    double jc[18], jp[6];
+    const double depth = obs_jacobian(prep + (int64_t)kCamPrep * i, X0, X1, X2, jc, jp);
+    if (!(depth > 0.0)) set_flag(flag, DEV_BEHIND, (int)o);
+    whiten(jc, jp, sigma, add_cov ? add_cov + 4 * o : nullptr);
+    const double* ai = Ainv + 6 * (int64_t)j;
+    const double Am[9] = {ai[0], ai[1], ai[2], ai[1], ai[3], ai[4], ai[2], ai[4], ai[5]};
+    double ja[6], psi[14];
+#pragma unroll
+    for (int row = 0; row < 2; ++row)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            ja[3 * row + q] = jp[3 * row] * Am[q] + jp[3 * row + 1] * Am[3 + q] + jp[3 * row + 2] * Am[6 + q];
+    for (int e = 0; e < 14; ++e) psi[e] = 0.0;
+    for (int l = 0; l < 3; ++l) {
+        double h[7];
+        hx_row(X0, X1, X2, l, h);
+#pragma unroll
+        for (int row = 0; row < 2; ++row)
+#pragma unroll
+            for (int p = 0; p < 7; ++p) psi[7 * row + p] += ja[3 * row + l] * h[p];
+    }
+    for (int e = 0; e < 18; ++e) Jc[18 * o + e] = jc[e];
+    for (int e = 0; e < 6; ++e) { Jp[6 * o + e] = jp[e]; JA[6 * o + e] = ja[e]; }
+    for (int e = 0; e < 14; ++e) Psi[14 * o + e] = psi[e];
+    for (int row = 0; row < 2; ++row)
+        for (int q = 0; q < 7; ++q) {
+            double v = 0.0;
+            for (int p = 0; p < 7; ++p) v += K[7 * q + p] * psi[7 * row + p];
+            Phi[q * ldphi + 2 * o + row] = v;
+        }
+}
+
 }  // namespace
 
 void launch_cam_prep(Ctx& c) {
@@ -609,6 +655,13 @@ void launch_nullspace(Ctx& c) {
     nullspace_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
         c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_cams, c.d_camprep,
         c.opt.nullspace_route, c.d_HP, c.d_flag);
+    CCOV_LAUNCH_CHECK(c);
+}
+
+void launch_upd_obs(Ctx& c, int64_t k, const ccov_obs* add, const double* add_cov, int64_t ldphi, double* Jc,
+                    double* Jp, double* JA, double* Psi, double* Phi) {
+    upd_obs_kernel<<<(unsigned)((k + 127) / 128), 128, 0, c.stream>>>(
+        k, add, add_cov, c.sigma, c.d_camprep, c.d_pts, c.d_Ainv, c.d_small, ldphi, Jc, Jp, JA, Psi, Phi, c.d_flag);
     CCOV_LAUNCH_CHECK(c);
 }
 

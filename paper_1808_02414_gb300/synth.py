@@ -257,9 +257,11 @@ def centre_scene(sc: Scene) -> Scene:
 def added_observations(sc: Scene, k: int, cams=None, seed=11):
     """k new observations (camera, point) of existing points by existing
     cameras, none already in S: from the cameras `cams` (default: any),
-    points drawn uniformly; u = projection + N(0, 1 px^2).  Returns (the
-    scene with them merged, sorted by point; the added records, sorted by
-    point)."""
+    points drawn uniformly; u = projection + N(0, 1 px^2).  A scene with
+    per-observation covariances gives the added ones random SPD 2x2
+    covariances (axes uniform in [0.5, 2] px^2, random orientation).  Returns
+    (the scene with them merged, sorted by point; the added records, sorted
+    by point)."""
     rng = np.random.default_rng(seed)
     have = set(zip(sc.obs_cam.tolist(), sc.obs_pt.tolist()))
     pool = np.arange(sc.n) if cams is None else np.asarray(cams)
@@ -272,18 +274,34 @@ def added_observations(sc: Scene, k: int, cams=None, seed=11):
     ac = np.array([c for c, _ in add], np.int32)
     ap = np.array([j for _, j in add], np.int32)
     Rs = np.stack([_rotation(sc.cams[c, 0:3]) for c in ac])
-    Xc = np.einsum("tij,tj->ti", Rs, sc.pts[ap]) + sc.cams[ac, 3:6]
+    if sc.model == "centre8":   # (r, C, c, k): R (X - C), one distortion value
+        Xc = np.einsum("tij,tj->ti", Rs, sc.pts[ap] - sc.cams[ac, 3:6])
+    else:
+        Xc = np.einsum("tij,tj->ti", Rs, sc.pts[ap]) + sc.cams[ac, 3:6]
     x = Xc[:, :2] / Xc[:, 2:3]
     rho2 = (x * x).sum(1)
-    g = 1.0 + sc.cams[ac, 7] * rho2 + sc.cams[ac, 8] * rho2 * rho2
+    g = 1.0 + sc.cams[ac, 7] * rho2
+    if sc.model != "centre8":
+        g = g + sc.cams[ac, 8] * rho2 * rho2
     au = sc.cams[ac, 6:7] * g[:, None] * x + rng.normal(0.0, 1.0, size=x.shape)
+    acov = None
+    if sc.obs_cov is not None:
+        a = rng.uniform(0.5, 2.0, size=(k, 2))
+        th = rng.uniform(0, np.pi, size=k)
+        c, s = np.cos(th), np.sin(th)
+        Rr = np.stack([np.stack([c, -s], -1), np.stack([s, c], -1)], -2)
+        acov = np.einsum("tij,tj,tkj->tik", Rr, a, Rr)
+        acov = 0.5 * (acov + acov.transpose(0, 2, 1))   # exactly symmetric
     cam = np.concatenate([sc.obs_cam, ac])
     pt = np.concatenate([sc.obs_pt, ap])
     u = np.concatenate([sc.obs_u, au])
     order = np.lexsort((cam, pt))
+    cov = None if acov is None else np.concatenate([sc.obs_cov, acov])[order]
     merged = Scene(sc.cams, sc.pts, cam[order].astype(np.int32), pt[order].astype(np.int32), u[order],
-                   sc.sigma, None, dict(sc.meta, added=k))
-    added = Scene(sc.cams, sc.pts, ac, ap, au, sc.sigma, None, {"kind": "added"})
+                   sc.sigma, cov, dict(sc.meta, added=k))
+    merged.model = sc.model
+    added = Scene(sc.cams, sc.pts, ac, ap, au, sc.sigma, acov, {"kind": "added"})
+    added.model = sc.model
     return merged, added
 
 
