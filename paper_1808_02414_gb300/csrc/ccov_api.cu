@@ -674,6 +674,7 @@ ccov_status ccov_covariance(ccov_ctx* h, double* out, int out_memory, double* es
     if (out_memory != CCOV_MEM_HOST && out_memory != CCOV_MEM_DEVICE)
         return fail(&c, CCOV_ERR_INVALID_ARG, "unknown memory kind");
     c.cov_ready = false;
+    c.upd_norm_ok = false;
     c.est_on = est_rel_err != nullptr;
     c.est_k = (int)(c.opt.est_cameras < c.n ? c.opt.est_cameras : c.n);
     c.stats.est_cameras = 0;

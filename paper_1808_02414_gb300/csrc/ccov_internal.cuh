@@ -105,6 +105,8 @@ struct Ctx {
     // covariance after added observations (ccov_update.cu): set by a
     // successful ccov_covariance, cleared by anything that changes the scene
     bool cov_ready = false;
+    bool upd_norm_ok = false;       // ||X||_inf and ||X||_1 of the current factor measured
+    double upd_norm[2] = {0.0, 0.0};
     void* d_upd = nullptr;          // one workspace block, grown on demand
     size_t upd_bytes = 0;
 
@@ -151,12 +153,19 @@ void mixed_free(Ctx& c);
 cudaError_t mixed_factor_inverse(Ctx& c);
 const long long* mixed_inverse_factor(const Ctx& c);   // X = L^-1, Q42, after mixed_factor_inverse
 // Y = X^T X V on the tensor cores with X of the last mixed step (d); V and Y
-// Np x ld FP64 (ncols <= ld columns used), Vq / Wq / Yq int64 workspaces of
-// Np x mixed_xtxv_ld(ncols), ecol that many ints, norms 2 + 2 Np doubles.
-// Synchronises the stream once (to read the norms of X).
+// Np x ld FP64 (ncols <= ld columns used).  With q = mixed_xtxv_ld(ncols):
+// Vq / Wq / Yq int64 workspaces of Np x q, Sq q x q, ecol q ints, cmax q
+// 64-bit words, norms 2 + 2 Np doubles.  Also Sq = -V'^T X^T X V' in Q(*FS)
+// for the columns scaled to V' = V diag(2^-ecol).  The first call after a
+// step (d) measures the norms of X and synchronises the stream once.
 int64_t mixed_xtxv_ld(int64_t ncols);
 cudaError_t mixed_xtxv(Ctx& c, int64_t ncols, const double* V, int64_t ld, double* Y, long long* Vq, long long* Wq,
-                       long long* Yq, int* ecol, double* norms);
+                       long long* Yq, long long* Sq, int* ecol, unsigned long long* cmax, double* norms, int* FS);
+// P = Y_s X_S^T for the update (after mixed_xtxv on the same columns): Yq and
+// ecol from mixed_xtxv, X_S ldq x ldq FP64 with |X_S| <= 1; emax one int,
+// XSq ldq x ldq and Pq Np x ldq int64 workspaces; P: N x ld FP64.
+cudaError_t mixed_update_p(Ctx& c, int64_t ncols, const long long* Yq, const double* XS, const int* ecol,
+                           int* emax, long long* XSq, long long* Pq, double* P, int64_t ld);
 cudaError_t mixed_setup();                             // kernel attributes, SM count
 bool mixed_make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, int64_t ld);
 bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np);

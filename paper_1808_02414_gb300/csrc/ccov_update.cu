@@ -117,9 +117,12 @@ upd_atb_kernel(int64_t rows, int64_t ld, int64_t chunk, const double* __restrict
 }
 
 // S (rp x rp): I + J_X A^-1 J_X^T (observations of one point) - Psi K Psi^T
-// + Vt^T Y (the split-K partials summed in order) on the 2k x 2k block, the
-// identity elsewhere.  Column a is row a & 1 of added observation a >> 1.
+// + Vt^T Y on the 2k x 2k block, the identity elsewhere.  Vt^T Y is either
+// the split-K partials summed in order, or (Sq not null, the tensor-core
+// form) -Sq[a][b] 2^(e_a + e_b - FS).  Column a is row a & 1 of added
+// observation a >> 1.
 __global__ void upd_s_kernel(int64_t r, int64_t ld, int64_t rp, int nsplit, const double* __restrict__ part,
+                             const long long* __restrict__ Sq, int64_t ldq, const int* __restrict__ ecol, int FS,
                              const ccov_obs* __restrict__ add, const double* __restrict__ JA,
                              const double* __restrict__ Jp, const double* __restrict__ Psi,
                              const double* __restrict__ K, double* __restrict__ S) {
@@ -128,7 +131,10 @@ __global__ void upd_s_kernel(int64_t r, int64_t ld, int64_t rp, int nsplit, cons
     const int64_t a = e / rp, b = e % rp;
     if (a >= r || b >= r) { S[e] = (a == b) ? 1.0 : 0.0; return; }
     double v = 0.0;
-    for (int z = 0; z < nsplit; ++z) v += part[((int64_t)z * ld + a) * ld + b];
+    if (Sq)
+        v = -ldexp((double)Sq[a * ldq + b], ecol[a] + ecol[b] - FS);
+    else
+        for (int z = 0; z < nsplit; ++z) v += part[((int64_t)z * ld + a) * ld + b];
     if (a == b) v += 1.0;
     const int64_t oa = a >> 1, ob = b >> 1;
     const int ra = (int)(a & 1), rb = (int)(b & 1);
@@ -173,7 +179,8 @@ struct Layout {
     int64_t r = 0, g = 0, ld = 0, rp = 0, nsplit = 1, chunk = 0;
     int64_t ldq = 0;   // columns of the scratch blocks (the tensor-core products pad to 128)
     size_t add = 0, cov = 0, Jc = 0, Jp = 0, JA = 0, Psi = 0, Phi = 0, Vt = 0, Ys = 0, s0 = 0, s1 = 0, s2 = 0,
-           S = 0, RS = 0, PS = 0, LS = 0, part = 0, out = 0, ecol = 0, norms = 0, total = 0;
+           S = 0, RS = 0, PS = 0, LS = 0, part = 0, out = 0, ecol = 0, norms = 0, Sq = 0, cmax = 0, emax = 0,
+           total = 0;
 };
 
 Layout layout(const Ctx& c, int64_t k) {
@@ -209,6 +216,9 @@ Layout layout(const Ctx& c, int64_t k) {
     L.out = take(d * 81 * c.n);
     L.ecol = take(sizeof(int) * L.ldq);
     L.norms = take(d * (2 + 2 * (size_t)c.Np));
+    L.Sq = take(sizeof(long long) * (size_t)L.ldq * L.ldq);
+    L.cmax = take(sizeof(unsigned long long) * (size_t)L.ldq);
+    L.emax = take(sizeof(int));
     L.total = off;
     return L;
 }
@@ -251,21 +261,29 @@ cudaError_t update_enqueue(Ctx& c, const ccov_obs* add, int64_t k, const double*
     // Y_s = X^T X (D Vt): on the tensor cores for the mixed form (digit-split
     // GEMMs over panels of X), else in FP64 (or where the operand buffers of
     // the mixed form are too short for the columns)
-    if (c.opt.precision == CCOV_PREC_MIXED && L.ldq <= Np) {
+    const bool tensor = c.opt.precision == CCOV_PREC_MIXED && L.ldq <= Np;
+    long long* Sq = tensor ? reinterpret_cast<long long*>(base + L.Sq) : nullptr;
+    int* ecol = reinterpret_cast<int*>(base + L.ecol);
+    int FS = 0;
+    if (tensor) {
         if ((e = mixed_xtxv(c, L.ld, Vt, ld, Ys, reinterpret_cast<long long*>(base + L.s0),
-                            reinterpret_cast<long long*>(base + L.s1), reinterpret_cast<long long*>(base + L.s2),
-                            reinterpret_cast<int*>(base + L.ecol), at(L.norms))) != cudaSuccess)
+                            reinterpret_cast<long long*>(base + L.s1), reinterpret_cast<long long*>(base + L.s2), Sq,
+                            ecol, reinterpret_cast<unsigned long long*>(base + L.cmax), at(L.norms), &FS)) !=
+            cudaSuccess)
             return e;
     } else {
         est_xtxv(c, (int)L.g, Vt, Ys, base + L.s0, base + L.s1, base + L.s2);
     }
     // S = I + ... + (D Vt)^T Y_s
     {
-        const unsigned t = (unsigned)((ld + 31) / 32);
-        upd_atb_kernel<<<dim3(t, t, (unsigned)L.nsplit), 256, 0, c.stream>>>(N, ld, L.chunk, Vt, Ys, part);
+        if (!tensor) {
+            const unsigned t = (unsigned)((ld + 31) / 32);
+            upd_atb_kernel<<<dim3(t, t, (unsigned)L.nsplit), 256, 0, c.stream>>>(N, ld, L.chunk, Vt, Ys, part);
+            c.launches++;
+        }
         upd_s_kernel<<<(unsigned)((L.rp * L.rp + 255) / 256), 256, 0, c.stream>>>(
-            L.r, ld, L.rp, (int)L.nsplit, part, d_add, JA, Jp, Psi, c.d_small, S);
-        c.launches += 2;
+            L.r, ld, L.rp, (int)L.nsplit, part, Sq, L.ldq, ecol, FS, d_add, JA, Jp, Psi, c.d_small, S);
+        c.launches++;
     }
     // S = L_S L_S^T, X_S = L_S^-1 (the FP64 blocked path on the small matrix)
     {
@@ -281,9 +299,19 @@ cudaError_t update_enqueue(Ctx& c, const ccov_obs* add, int64_t k, const double*
         spd_factor_inverse64(s);
         c.launches += s.launches;
     }
-    // P = Y_s X_S^T (into s2), then the camera blocks
+    // P = Y_s X_S^T, then the camera blocks.  Tensor-core form: from the
+    // fixed-point Y of mixed_xtxv (s2), with X_S in Q60 (s0) and P in int64
+    // (s1), P itself into Vt (no longer needed)
     double* P = at(L.s2);
-    launch_gemm64(c, true, false, N, ld, ld, 1.0, Ys, ld, RS, L.rp, 0.0, P, ld, 0, 0);
+    if (tensor) {
+        P = Vt;
+        if ((e = mixed_update_p(c, ld, reinterpret_cast<const long long*>(base + L.s2), RS, ecol,
+                                reinterpret_cast<int*>(base + L.emax), reinterpret_cast<long long*>(base + L.s0),
+                                reinterpret_cast<long long*>(base + L.s1), P, ld)) != cudaSuccess)
+            return e;
+    } else {
+        launch_gemm64(c, true, false, N, ld, ld, 1.0, Ys, ld, RS, L.rp, 0.0, P, ld, 0, 0);
+    }
     upd_diag_kernel<<<(unsigned)c.n, 128, 0, c.stream>>>(ld, ld, P, c.d_D, c.d_Sig, res);
     c.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <utility>
 #include <vector>
@@ -1467,36 +1468,55 @@ __global__ void __launch_bounds__(1024) max2_kernel(int64_t n, const double* __r
 
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
-// e_j with |V[:, j]| < 2^e_j (0 for a zero column), j < ncols: a CTA per 32
-// columns, eight row phases.
-__global__ void __launch_bounds__(256) colexp_kernel(int64_t rows, int64_t ld, int64_t ncols,
-                                                     const double* __restrict__ V, int* __restrict__ ecol,
-                                                     int* flag) {
+// Column maxima of |V| (j < ncols) as the bit patterns of non-negative
+// doubles, whose integer order is their order: a CTA per 32 columns and row
+// chunk, eight row phases, one atomicMax per column (cmax starts at 0).
+__global__ void __launch_bounds__(256) colmax_kernel(int64_t rows, int64_t ld, int64_t ncols, int64_t chunk,
+                                                     const double* __restrict__ V,
+                                                     unsigned long long* __restrict__ cmax) {
     __shared__ double part[8][32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t j = blockIdx.x * 32 + tx;
+    const int64_t j = blockIdx.x * 32 + tx, r0 = blockIdx.y * chunk, r1 = r0 + chunk < rows ? r0 + chunk : rows;
     double mx = 0.0;
     if (j < ncols)
-        for (int64_t r = ty; r < rows; r += 8) mx = fmax(mx, fabs(V[r * ld + j]));
+        for (int64_t r = r0 + ty; r < r1; r += 8) mx = fmax(mx, fabs(V[r * ld + j]));
     part[ty][tx] = mx;
     __syncthreads();
     if (ty == 0 && j < ncols) {
         for (int w = 1; w < 8; ++w) mx = fmax(mx, part[w][tx]);
-        int e = 0;
-        if (mx > 0x1p-900) frexp(mx, &e);   // mx < 2^e; smaller columns round to zero in Q60
-        if (!(mx < 0x1p1000)) { ptx::set_flag(flag, DEV_RANGE, (int)j); e = 0; }
-        ecol[j] = e;
+        atomicMax(cmax + j, (unsigned long long)__double_as_longlong(mx));
     }
 }
 
+// e_j with |V[:, j]| < 2^e_j (0 for a zero column, or one below 2^-900 that
+// rounds to zero in Q60 anyway).
+__device__ __forceinline__ int col_exponent(unsigned long long bits) {
+    const double mx = __longlong_as_double((long long)bits);
+    int e = 0;
+    if (mx > 0x1p-900) frexp(mx, &e);
+    return e;
+}
+
 // Vq[r][j] = V[r][j] 2^(60 - e_j) as int64 (Q60 of the scaled column), zero
-// beyond ncols.
+// beyond ncols; row 0 also writes e_j.
 __global__ void tofixed_kernel(int64_t rows, int64_t ld, int64_t ncols, int64_t ldq, const double* __restrict__ V,
-                               const int* __restrict__ ecol, long long* __restrict__ Vq) {
+                               const unsigned long long* __restrict__ cmax, int* __restrict__ ecol,
+                               long long* __restrict__ Vq, int* flag) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= rows * ldq) return;
     const int64_t r = e / ldq, j = e % ldq;
-    Vq[e] = j < ncols ? __double2ll_rn(V[r * ld + j] * pow2(60 - ecol[j])) : 0;
+    long long q = 0;
+    if (j < ncols) {
+        const unsigned long long b = cmax[j];
+        if (!(__longlong_as_double((long long)b) < 0x1p1000)) {   // not finite or far too large
+            if (r == 0) { ptx::set_flag(flag, DEV_RANGE, (int)j); ecol[j] = 0; }
+        } else {
+            const int ej = col_exponent(b);
+            if (r == 0) ecol[j] = ej;
+            q = __double2ll_rn(V[r * ld + j] * pow2(60 - ej));
+        }
+    }
+    Vq[e] = q;
 }
 
 // Y[r][j] = Yq[r][j] 2^(e_j - F).
@@ -1507,6 +1527,35 @@ __global__ void fromfixed_kernel(int64_t rows, int64_t ld, int64_t ncols, int64_
     if (e >= rows * ncols) return;
     const int64_t r = e / ncols, j = e % ncols;
     Y[r * ld + j] = (double)Yq[r * ldq + j] * pow2(ecol[j] - F);
+}
+
+// emax[0] = the largest e_j (j < ncols); one warp.
+__global__ void emax_kernel(int64_t ncols, const int* __restrict__ ecol, int* __restrict__ emax) {
+    int m = -100000;
+    for (int64_t j = threadIdx.x; j < ncols; j += 32) m = max(m, ecol[j]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) emax[0] = m;
+}
+
+// XSq[a][j] = X_S[a][j] 2^(e_j - emax + 60) for j < ncols (|X_S| <= 1: S >= I),
+// zero beyond; ldq x ldq, X_S with leading dimension ldq.
+__global__ void xs_tofixed_kernel(int64_t ldq, int64_t ncols, const double* __restrict__ XS,
+                                  const int* __restrict__ ecol, const int* __restrict__ emax,
+                                  long long* __restrict__ XSq) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ldq * ldq) return;
+    const int64_t j = e % ldq;
+    XSq[e] = j < ncols ? __double2ll_rn(ldexp(XS[e], ecol[j] - emax[0] + 60)) : 0;
+}
+
+// P[i][a] = -Pq[i][a] 2^(emax - F) for a < ncols (P: rows x ld FP64).
+__global__ void p_fromfixed_kernel(int64_t rows, int64_t ncols, int64_t ld, int64_t ldq,
+                                   const long long* __restrict__ Pq, const int* __restrict__ emax, int F,
+                                   double* __restrict__ P) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * ncols) return;
+    const int64_t i = e / ncols, a = e % ncols;
+    P[i * ld + a] = -ldexp((double)Pq[i * ldq + a], emax[0] - F);
 }
 
 // Rows of an int64 Q(F) matrix, K = 128 or 256 values per row (a column
@@ -1592,31 +1641,51 @@ int fixed_point_for(double bound) {
 int64_t mixed_xtxv_ld(int64_t ncols) { return (ncols + 127) / 128 * 128; }
 
 cudaError_t mixed_xtxv(Ctx& c, int64_t ncols, const double* V, int64_t ld, double* Y, long long* Vq, long long* Wq,
-                       long long* Yq, int* ecol, double* norms) {
+                       long long* Yq, long long* Sq, int* ecol, unsigned long long* cmax, double* norms, int* FS) {
     if (!c.mixed) return cudaErrorInvalidValue;
     MixedState& st = *c.mixed;
     const int64_t Np = c.Np, nb = Np / kNB, ldq = mixed_xtxv_ld(ncols);
     if (ldq > Np) return cudaErrorInvalidValue;   // the operand buffers hold Np rows
     cudaError_t e;
-    // norms of X: |W| <= ||X||_inf, |Y| <= ||X||_1 ||X||_inf for columns scaled to |v| < 1
-    double* rs = norms + 2;
-    double* cs = norms + 2 + Np;
-    xnorm_rows_kernel<<<(unsigned)((Np * 32 + 255) / 256), 256, 0, c.stream>>>(Np, st.R, rs);
-    xnorm_cols_kernel<<<(unsigned)((Np + 31) / 32), 256, 0, c.stream>>>(Np, st.R, cs);
-    max2_kernel<<<1, 1024, 0, c.stream>>>(Np, rs, cs, norms);
-    colexp_kernel<<<(unsigned)((ncols + 31) / 32), 256, 0, c.stream>>>(Np, ld, ncols, V, ecol, c.d_flag);
-    tofixed_kernel<<<(unsigned)((Np * ldq + 255) / 256), 256, 0, c.stream>>>(Np, ld, ncols, ldq, V, ecol, Vq);
-    c.launches += 5;
-    double nrm[2] = {0.0, 0.0};
-    if ((e = cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess) return e;
+    // norms of X, once per factorisation: |W| <= ||X||_inf, |Y| <= ||X||_1
+    // ||X||_inf for columns scaled to |v| < 1
+    if (!c.upd_norm_ok) {
+        double* rs = norms + 2;
+        double* cs = norms + 2 + Np;
+        xnorm_rows_kernel<<<(unsigned)((Np * 32 + 255) / 256), 256, 0, c.stream>>>(Np, st.R, rs);
+        xnorm_cols_kernel<<<(unsigned)((Np + 31) / 32), 256, 0, c.stream>>>(Np, st.R, cs);
+        max2_kernel<<<1, 1024, 0, c.stream>>>(Np, rs, cs, norms);
+        c.launches += 3;
+        double nrm[2] = {0.0, 0.0};
+        if ((e = cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+        if (!(nrm[0] < 0x1p40) || !(nrm[1] < 0x1p40)) return cudaErrorInvalidValue;   // not a usable factor
+        c.upd_norm[0] = nrm[0];
+        c.upd_norm[1] = nrm[1];
+        c.upd_norm_ok = true;
+    }
+    const double ninf = c.upd_norm[0], n1 = c.upd_norm[1];
+    const int FW = fixed_point_for(ninf);
+    const int FY = fixed_point_for(ninf * n1);
+    *FS = fixed_point_for((double)c.N * ninf * ninf);
+    // columns scaled to |v| < 1, as Q60
+    if ((e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * ldq, c.stream)) != cudaSuccess) return e;
+    {
+        const int64_t cb = (ncols + 31) / 32;
+        const int64_t nch = std::max<int64_t>(1, std::min<int64_t>(64, (4 * 152 + cb - 1) / cb));
+        const int64_t chunk = (Np + nch - 1) / nch;
+        colmax_kernel<<<dim3((unsigned)cb, (unsigned)nch), 256, 0, c.stream>>>(Np, ld, ncols, chunk, V, cmax);
+    }
+    tofixed_kernel<<<(unsigned)((Np * ldq + 255) / 256), 256, 0, c.stream>>>(Np, ld, ncols, ldq, V, cmax, ecol, Vq,
+                                                                             c.d_flag);
+    c.launches += 2;
     if ((e = cudaMemsetAsync(Wq, 0, sizeof(long long) * Np * ldq, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Yq, 0, sizeof(long long) * Np * ldq, c.stream)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
-    if (!(nrm[0] < 0x1p40) || !(nrm[1] < 0x1p40)) return cudaErrorInvalidValue;   // not a usable factor
-    const int FW = fixed_point_for(nrm[0]);
-    const int FY = fixed_point_for(nrm[0] * nrm[1]);
-    CUtensorMap mapW, mapY;
-    if (!make_c_map(&mapW, Wq, Np, ldq, ldq) || !make_c_map(&mapY, Yq, Np, ldq, ldq)) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(Sq, 0, sizeof(long long) * ldq * ldq, c.stream)) != cudaSuccess) return e;
+    CUtensorMap mapW, mapY, mapS;
+    if (!make_c_map(&mapW, Wq, Np, ldq, ldq) || !make_c_map(&mapY, Yq, Np, ldq, ldq) ||
+        !make_c_map(&mapS, Sq, ldq, ldq, ldq))
+        return cudaErrorInvalidValue;
     // W = -X V: column panels of X (rows kp.. of the panel), rows kp.. of V
     for (int64_t kb = 0; kb < nb; kb += 2) {
         const int K = kb + 1 < nb ? 256 : 128;
@@ -1626,15 +1695,49 @@ cudaError_t mixed_xtxv(Ctx& c, int64_t ncols, const double* V, int64_t ld, doubl
         slice_cols_f(c, K, (int)ldq, Vq + kp * ldq, ldq, 60, BUF_Q);
         launch_ozaki(c, K, BUF_P, 0, rows, BUF_Q, 0, (int)ldq, mapW, 0, (int)kp, 0, 1, FW, st.expP, st.expQ);
     }
-    // Y = -X^T (-X V): row panels of X (columns up to the panel's end), rows of W
+    // Y = -X^T (-X V) by row panels of X (columns up to the panel's end) and
+    // rows of W; with the same digits of W, S = -W^T W (= -V^T X^T X V)
     for (int64_t kb = 0; kb < nb; kb += 2) {
         const int K = kb + 1 < nb ? 256 : 128;
         const int64_t kp = kb * kNB;
         slice_cols_f(c, K, (int)(kp + K), st.R + kp * Np, Np, kFX, BUF_P);
         slice_cols_f(c, K, (int)ldq, Wq + kp * ldq, ldq, FW, BUF_Q);
         launch_ozaki(c, K, BUF_P, 0, (int)(kp + K), BUF_Q, 0, (int)ldq, mapY, 0, 0, 0, 1, FY, st.expP, st.expQ);
+        launch_ozaki(c, K, BUF_Q, 0, (int)ldq, BUF_Q, 0, (int)ldq, mapS, 0, 0, 0, 1, *FS, st.expQ, st.expQ);
     }
     fromfixed_kernel<<<(unsigned)((Np * ncols + 255) / 256), 256, 0, c.stream>>>(Np, ld, ncols, ldq, Yq, ecol, FY, Y);
+    c.launches++;
+    if (c.mixed_bad_launch) return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// P = Y_s X_S^T for the covariance update, on the tensor cores: Y_s from the
+// normalised fixed-point Yq of mixed_xtxv (Y_s = Y' 2^e_j by column), X_S =
+// L_S^-1 (FP64, ldq x ldq, |X_S| <= 1) with its columns scaled by 2^(e_j -
+// emax) into Q60; P = Y' (X_S E)^T over 256-wide panels of the ncols
+// columns.  XSq ldq x ldq and Pq Np x ldq int64 workspaces; P rows x ld FP64.
+cudaError_t mixed_update_p(Ctx& c, int64_t ncols, const long long* Yq, const double* XS, const int* ecol,
+                           int* emax, long long* XSq, long long* Pq, double* P, int64_t ld) {
+    MixedState& st = *c.mixed;
+    const int64_t Np = c.Np, ldq = mixed_xtxv_ld(ncols);
+    const double ninf = c.upd_norm[0], n1 = c.upd_norm[1];
+    const int FY = fixed_point_for(ninf * n1);
+    const int FP = fixed_point_for((double)ldq * ninf * n1);
+    cudaError_t e;
+    emax_kernel<<<1, 32, 0, c.stream>>>(ncols, ecol, emax);
+    xs_tofixed_kernel<<<(unsigned)((ldq * ldq + 255) / 256), 256, 0, c.stream>>>(ldq, ncols, XS, ecol, emax, XSq);
+    c.launches += 2;
+    if ((e = cudaMemsetAsync(Pq, 0, sizeof(long long) * Np * ldq, c.stream)) != cudaSuccess) return e;
+    CUtensorMap mapP;
+    if (!make_c_map(&mapP, Pq, Np, ldq, ldq)) return cudaErrorInvalidValue;
+    for (int64_t kp = 0; kp < ldq; kp += 256) {
+        const int K = kp + 256 <= ldq ? 256 : 128;
+        slice_rows_exp(c, K, (int)Np, Yq + kp, ldq, FY, BUF_P);
+        slice_rows_exp(c, K, (int)ldq, XSq + kp, ldq, 60, BUF_Q);
+        launch_ozaki(c, K, BUF_P, 0, (int)Np, BUF_Q, 0, (int)ldq, mapP, 0, 0, 0, 1, FP, st.expP, st.expQ);
+    }
+    p_fromfixed_kernel<<<(unsigned)((c.N * ncols + 255) / 256), 256, 0, c.stream>>>(c.N, ncols, ld, ldq, Pq, emax,
+                                                                                    FP, P);
     c.launches++;
     if (c.mixed_bad_launch) return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -11,6 +11,8 @@ form as one replayed graph).
   step (d) of the mixed path against the FP64 GPU path (1e-6) together with
   properties that hold at any size (symmetric, positive semi-definite
   blocks).
+- the same scene with 200 observations added by the Woodbury update (mixed)
+  against the FP64 GPU path on the merged scene (1e-6).
 - 256 sub-reconstructions of 10-300 cameras, mixed, grouped launches replayed
   as one graph: the smallest and the largest scenes against the oracle (1e-6),
   and a few hundred kernels per replay."""
@@ -68,6 +70,20 @@ def test_4000_cameras_sampled_steps_and_mixed_against_fp64():
     _psd_symmetric(mixed)
     _psd_symmetric(fp64)
     assert_blocks_close(mixed, fp64, 1e-6)
+
+
+def test_4000_cameras_update_against_fp64_of_the_merged_scene():
+    """The Woodbury update (Sec. 5) at the bench's size: 200 observations
+    added to the mixed factorisation of the 4000-camera scene, against the
+    FP64 GPU form of the merged scene computed from scratch (1e-6)."""
+    sc = synth.workload("shell4k")
+    merged, added = synth.added_observations(sc, 200, cams=np.arange(0, sc.n, sc.n // 10)[:10], seed=21)
+    with ccov.from_scene(sc, precision=ccov.CCOV_PREC_MIXED) as ctx:
+        ctx.run()
+        upd = ctx.ccov_update_observations(added.obs_records())
+    want = ccov.camera_covariances(merged)
+    _psd_symmetric(upd)
+    assert_blocks_close(upd, want, 1e-6)
 
 
 def test_256_subreconstructions_graph_against_oracle():
