@@ -75,7 +75,11 @@ enum { CCOV_GAUGE_NATURAL = 0, CCOV_GAUGE_ZPINV = 1, CCOV_GAUGE_FIXED3 = 2 };
 enum { CCOV_CAMERA_RT9 = 0, CCOV_CAMERA_CENTRE8 = 1 };
 
 typedef struct {
-    int precision;        /* CCOV_PREC_FP64 (default) or CCOV_PREC_MIXED */
+    int precision;        /* CCOV_PREC_FP64 (default): every sum in FP64;
+                             CCOV_PREC_MIXED: step (d) as exact digit products on the
+                             tensor cores (int64 fixed point, mixed_slices digits) and the
+                             Schur sums of step (b) in double-single arithmetic (about 44
+                             bits, above the digits' 39) */
     int mixed_slices;     /* MIXED only: 8-bit digit slices per operand, 4..6; 0 = 5 for
                              the natural gauge with the 9-value camera, 6 for
                              CCOV_GAUGE_ZPINV / _FIXED3 and CCOV_CAMERA_CENTRE8, whose

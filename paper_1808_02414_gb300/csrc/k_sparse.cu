@@ -8,6 +8,7 @@
 // equation) gives the nullspace H.  Layout: observations sorted by point
 // (CSR by point, pt_ptr) plus a permutation grouping them by camera.
 #include "ccov_internal.cuh"
+#include "ds_arith.cuh"
 
 namespace ccov {
 namespace {
@@ -152,58 +153,62 @@ __device__ __forceinline__ void whiten(double* Jc, double* Jp, double sigma,
     }
 }
 
-// Step (a), point part: warp per point.  A_j = sum Jp^T Jp, its inverse, and
-// W_ij = Jc^T Jp per observation.
-__global__ void __launch_bounds__(32 * kWarps)
-point_info_kernel(int64_t m, const int* __restrict__ pt_ptr, const ccov_obs* __restrict__ obs,
-                  const double* __restrict__ pts, const double* __restrict__ prep, double sigma,
-                  const double* __restrict__ cov, double* __restrict__ W,
+// Step (a), point part in two passes (the same quantities as
+// point_info_kernel, whose warp per point leaves most lanes idle on tracks of
+// a few observations): a thread per observation computes the whitened
+// Jacobian, W_ij = Jc^T Jp and the observation's share Jp^T Jp of A_j (six
+// values into `share`); a thread per point then sums the shares of its
+// observations in order and inverts A_j.
+__global__ void __launch_bounds__(128)
+obs_info_kernel(int64_t t, const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
+                const double* __restrict__ prep, double sigma, const double* __restrict__ cov,
+                double* __restrict__ W, double* __restrict__ share, int* flag) {
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= t) return;
+    const int i = obs[o].cam;
+    const int64_t j = obs[o].pt;
+    double Jc[18], Jp[6];
+    const double depth = obs_jacobian(prep + (int64_t)kCamPrep * i, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], Jc, Jp);
+    if (!(depth > 0.0)) set_flag(flag, DEV_BEHIND, (int)o);
+    whiten(Jc, Jp, sigma, cov ? cov + 4 * o : nullptr);
+    double* a = share + 6 * o;
+    a[0] = Jp[0] * Jp[0] + Jp[3] * Jp[3];
+    a[1] = Jp[0] * Jp[1] + Jp[3] * Jp[4];
+    a[2] = Jp[0] * Jp[2] + Jp[3] * Jp[5];
+    a[3] = Jp[1] * Jp[1] + Jp[4] * Jp[4];
+    a[4] = Jp[1] * Jp[2] + Jp[4] * Jp[5];
+    a[5] = Jp[2] * Jp[2] + Jp[5] * Jp[5];
+    double* w = W + 27 * o;
+#pragma unroll
+    for (int p = 0; p < 9; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) w[3 * p + q] = Jc[p] * Jp[q] + Jc[9 + p] * Jp[3 + q];
+}
+
+__global__ void __launch_bounds__(128)
+point_ainv_kernel(int64_t m, const int* __restrict__ pt_ptr, const double* __restrict__ share,
                   double* __restrict__ Ainv, int* flag) {
-    const int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < m; j += nwarp) {
-        int o0 = pt_ptr[j], o1 = pt_ptr[j + 1];
-        double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
-        double a[6] = {0, 0, 0, 0, 0, 0};
-        for (int o = o0 + lane; o < o1; o += 32) {
-            int i = obs[o].cam;
-            double Jc[18], Jp[6];
-            double depth = obs_jacobian(prep + (int64_t)kCamPrep * i, X0, X1, X2, Jc, Jp);
-            if (!(depth > 0.0)) set_flag(flag, DEV_BEHIND, o);
-            whiten(Jc, Jp, sigma, cov ? cov + 4 * (int64_t)o : nullptr);
-            a[0] += Jp[0] * Jp[0] + Jp[3] * Jp[3];
-            a[1] += Jp[0] * Jp[1] + Jp[3] * Jp[4];
-            a[2] += Jp[0] * Jp[2] + Jp[3] * Jp[5];
-            a[3] += Jp[1] * Jp[1] + Jp[4] * Jp[4];
-            a[4] += Jp[1] * Jp[2] + Jp[4] * Jp[5];
-            a[5] += Jp[2] * Jp[2] + Jp[5] * Jp[5];
-            double* w = W + 27 * (int64_t)o;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    for (int o = pt_ptr[j]; o < pt_ptr[j + 1]; ++o)
 #pragma unroll
-            for (int p = 0; p < 9; ++p)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) w[3 * p + q] = Jc[p] * Jp[q] + Jc[9 + p] * Jp[3 + q];
-        }
-#pragma unroll
-        for (int e = 0; e < 6; ++e) a[e] = warp_sum(a[e]);
-        if (lane == 0) {
-            // inverse of the symmetric 3x3 block by cofactors
-            double c00 = a[3] * a[5] - a[4] * a[4];
-            double c01 = a[2] * a[4] - a[1] * a[5];
-            double c02 = a[1] * a[4] - a[2] * a[3];
-            double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-            double scale = a[0] * a[3] * a[5];
-            if (!(det > 1e-14 * scale) || !(a[0] > 0.0)) set_flag(flag, DEV_SINGULAR_A, (int)j);
-            double id = 1.0 / det;
-            double* ai = Ainv + 6 * j;
-            ai[0] = c00 * id;
-            ai[1] = c01 * id;
-            ai[2] = c02 * id;
-            ai[3] = (a[0] * a[5] - a[2] * a[2]) * id;
-            ai[4] = (a[1] * a[2] - a[0] * a[4]) * id;
-            ai[5] = (a[0] * a[3] - a[1] * a[1]) * id;
-        }
-    }
+        for (int e = 0; e < 6; ++e) a[e] += share[6 * (int64_t)o + e];
+    // inverse of the symmetric 3x3 block by cofactors
+    const double c00 = a[3] * a[5] - a[4] * a[4];
+    const double c01 = a[2] * a[4] - a[1] * a[5];
+    const double c02 = a[1] * a[4] - a[2] * a[3];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    const double scale = a[0] * a[3] * a[5];
+    if (!(det > 1e-14 * scale) || !(a[0] > 0.0)) set_flag(flag, DEV_SINGULAR_A, (int)j);
+    const double id = 1.0 / det;
+    double* ai = Ainv + 6 * j;
+    ai[0] = c00 * id;
+    ai[1] = c01 * id;
+    ai[2] = c02 * id;
+    ai[3] = (a[0] * a[5] - a[2] * a[2]) * id;
+    ai[4] = (a[1] * a[2] - a[0] * a[4]) * id;
+    ai[5] = (a[0] * a[3] - a[1] * a[1]) * id;
 }
 
 // Step (a), camera part: warp per camera, U_i = sum Jc^T Jc (lower, 45).
@@ -284,35 +289,86 @@ __global__ void vmat_kernel(int64_t t, const ccov_obs* __restrict__ obs, const d
 // Several scenes at once (cam_scene not null): camera i belongs to scene
 // cam_scene[i], whose matrix starts at Z + scene_zo[s] with leading
 // dimension scene_ld[s] and whose first camera is scene_co[s].
+// The sums run in FP64 (the FP64 form) or in double-single arithmetic on the
+// FP32 pipes (the mixed form, whose digits keep 39 bits of Z anyway; GB300
+// issues FP64 FMAs at a small fraction of the FP32 rate).
+template <class T>
+struct SchurAr;
+
+template <>
+struct SchurAr<double> {
+    typedef double V;
+    static __device__ __forceinline__ double load(double x) { return x; }
+    static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ double dot3(double acc, const double* v, const double* w) {
+        return acc + (v[0] * w[0] + v[1] * w[1] + v[2] * w[2]);
+    }
+    static __device__ __forceinline__ double value(double a) { return a; }
+};
+
+template <>
+struct SchurAr<dsf> {
+    typedef dsf V;
+    static __device__ __forceinline__ dsf load(double x) { return ds_from_double(x); }
+    static __device__ __forceinline__ dsf zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ dsf dot3(dsf acc, const dsf* v, const dsf* w) {
+        acc = ds_fma(acc, v[0], w[0]);
+        acc = ds_fma(acc, v[1], w[1]);
+        return ds_fma(acc, v[2], w[2]);
+    }
+    static __device__ __forceinline__ double value(dsf a) { return (double)a.h + (double)a.l; }
+};
+
+template <class T>
 __global__ void __launch_bounds__(32 * kWarps)
 schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __restrict__ ent,
                    const double* __restrict__ V, const double* __restrict__ W, const double* __restrict__ U,
                    double* __restrict__ Z, int64_t ldz, const int* __restrict__ cam_scene,
                    const int64_t* __restrict__ scene_zo, const int64_t* __restrict__ scene_ld,
                    const int* __restrict__ scene_co) {
-    __shared__ double sv[kWarps][2][28];
+    typedef SchurAr<T> Ar;
+    typedef typename Ar::V E;
+    // four entries (observation pairs) staged at a time, so that each lane has
+    // eight loads in flight; the sums still run over the entries in order
+    constexpr int kU = 4;
+    __shared__ E sv[kWarps][kU][2][28];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    double* vs = sv[wi][0];
-    double* ws = sv[wi][1];
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int e0 = lane, e1 = lane + 32, e2 = lane + 64;
     const int r0 = e0 / 9, c0 = e0 % 9, r1 = e1 / 9, c1 = e1 % 9, r2 = e2 / 9, c2 = e2 % 9;
     for (int64_t p = warp; p < npairs; p += nwarp) {
         const int4 d = desc[p];
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        for (int q = d.z; q < d.z + d.w; ++q) {
-            const int2 oo = ent[q];
-            __syncwarp();
-            if (lane < 27) {
-                vs[lane] = V[27 * (int64_t)oo.x + lane];
-                ws[lane] = W[27 * (int64_t)oo.y + lane];
+        E a0 = Ar::zero(), a1 = Ar::zero(), a2 = Ar::zero();
+        const int qend = d.z + d.w;
+        for (int q = d.z; q < qend; q += kU) {
+            const int nq = qend - q < kU ? qend - q : kU;
+            double rv[kU], rw[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                rv[u] = 0.0;
+                rw[u] = 0.0;
+                if (u < nq && lane < 27) {
+                    const int2 oo = ent[q + u];
+                    rv[u] = V[27 * (int64_t)oo.x + lane];
+                    rw[u] = W[27 * (int64_t)oo.y + lane];
+                }
             }
             __syncwarp();
-            a0 += vs[3 * r0] * ws[3 * c0] + vs[3 * r0 + 1] * ws[3 * c0 + 1] + vs[3 * r0 + 2] * ws[3 * c0 + 2];
-            a1 += vs[3 * r1] * ws[3 * c1] + vs[3 * r1 + 1] * ws[3 * c1 + 1] + vs[3 * r1 + 2] * ws[3 * c1 + 2];
-            if (e2 < 81)
-                a2 += vs[3 * r2] * ws[3 * c2] + vs[3 * r2 + 1] * ws[3 * c2 + 1] + vs[3 * r2 + 2] * ws[3 * c2 + 2];
+            if (lane < 27)
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    sv[wi][u][0][lane] = Ar::load(rv[u]);
+                    sv[wi][u][1][lane] = Ar::load(rw[u]);
+                }
+            __syncwarp();
+            for (int u = 0; u < nq; ++u) {
+                const E* vs = sv[wi][u][0];
+                const E* ws = sv[wi][u][1];
+                a0 = Ar::dot3(a0, vs + 3 * r0, ws + 3 * c0);
+                a1 = Ar::dot3(a1, vs + 3 * r1, ws + 3 * c1);
+                if (e2 < 81) a2 = Ar::dot3(a2, vs + 3 * r2, ws + 3 * c2);
+            }
         }
         const bool diag = d.x == d.y;
         double* zs = Z;
@@ -327,9 +383,10 @@ schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __
         double* zb = zs + 9 * li * ld + 9 * lk;
         const double* u = U + 45 * (int64_t)d.x;
         // a diagonal block keeps its lower triangle, plus U_i (lower, row by row)
-        if (!diag || c0 <= r0) zb[r0 * ld + c0] = (diag ? u[r0 * (r0 + 1) / 2 + c0] : 0.0) - a0;
-        if (!diag || c1 <= r1) zb[r1 * ld + c1] = (diag ? u[r1 * (r1 + 1) / 2 + c1] : 0.0) - a1;
-        if (e2 < 81 && (!diag || c2 <= r2)) zb[r2 * ld + c2] = (diag ? u[r2 * (r2 + 1) / 2 + c2] : 0.0) - a2;
+        const double s0 = Ar::value(a0), s1 = Ar::value(a1), s2 = Ar::value(a2);
+        if (!diag || c0 <= r0) zb[r0 * ld + c0] = (diag ? u[r0 * (r0 + 1) / 2 + c0] : 0.0) - s0;
+        if (!diag || c1 <= r1) zb[r1 * ld + c1] = (diag ? u[r1 * (r1 + 1) / 2 + c1] : 0.0) - s1;
+        if (e2 < 81 && (!diag || c2 <= r2)) zb[r2 * ld + c2] = (diag ? u[r2 * (r2 + 1) / 2 + c2] : 0.0) - s2;
     }
 }
 
@@ -620,9 +677,13 @@ void launch_cam_prep(Ctx& c) {
 }
 
 void launch_point_info(Ctx& c) {
-    point_info_kernel<<<grid_for(c.m, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.m, c.d_pt_ptr, c.d_obs, c.d_pts, c.d_camprep, c.sigma, c.d_obscov, c.d_W, c.d_Ainv,
-        c.d_flag);
+    // the observations' shares of A go into V (t x 27), which step (b) fills later
+    obs_info_kernel<<<(unsigned)((c.t + 127) / 128), 128, 0, c.stream>>>(c.t, c.d_obs, c.d_pts, c.d_camprep,
+                                                                         c.sigma, c.d_obscov, c.d_W, c.d_V,
+                                                                         c.d_flag);
+    CCOV_LAUNCH_CHECK(c);
+    point_ainv_kernel<<<(unsigned)((c.m + 127) / 128), 128, 0, c.stream>>>(c.m, c.d_pt_ptr, c.d_V, c.d_Ainv,
+                                                                           c.d_flag);
     CCOV_LAUNCH_CHECK(c);
 }
 
@@ -635,9 +696,14 @@ void launch_cam_info(Ctx& c) {
 void launch_schur(Ctx& c) {
     vmat_kernel<<<(int)((c.t + 255) / 256), 256, 0, c.stream>>>(c.t, c.d_obs, c.d_W, c.d_Ainv, c.d_V);
     CCOV_LAUNCH_CHECK(c);
-    schur_pairs_kernel<<<grid_for(c.npairs, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np, c.d_cam_scene, c.d_scene_zo,
-        c.d_scene_ld, c.d_scene_co);
+    if (c.opt.precision == CCOV_PREC_MIXED)
+        schur_pairs_kernel<dsf><<<grid_for(c.npairs, kWarps), 32 * kWarps, 0, c.stream>>>(
+            c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np, c.d_cam_scene, c.d_scene_zo,
+            c.d_scene_ld, c.d_scene_co);
+    else
+        schur_pairs_kernel<double><<<grid_for(c.npairs, kWarps), 32 * kWarps, 0, c.stream>>>(
+            c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np, c.d_cam_scene, c.d_scene_zo,
+            c.d_scene_ld, c.d_scene_co);
     CCOV_LAUNCH_CHECK(c);
     const int wps = kW7Warps;
     w7_partial_kernel<<<(unsigned)(c.nscenes * wps / kWarps), 32 * kWarps, 0, c.stream>>>(
