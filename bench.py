@@ -937,6 +937,30 @@ def run_update(args):
         by_k[str(kk)] = h0.elapsed_time(h1) / 2
     ctx.close()
     value = scene.n * world / (ms_step / 1e3)
+    # roofline of the tensor-core products of one update: the algorithmic work
+    # (X V and X^T W, N^2 r flop each with X triangular; W^T W and Y X_S^T, N r^2
+    # each, r = 2k) and the executed digit products (every 128 x 64 tile of
+    # the K = 256 panel GEMMs x 15 products for S = 5), both over the whole
+    # update time (a lower bound of the GEMMs' rate)
+    N, r = 9 * scene.n, 2 * k
+    Np = (N + 127) // 128 * 128
+    ldq = (9 * ((r + 8) // 9) + 127) // 128 * 128
+    rb, cb, panels = Np // 128, ldq // 64, (Np // 128 + 1) // 2
+    tiles = sum((rb - 2 * p) * cb for p in range(panels)) + sum(min(2 * p + 2, rb) * cb for p in range(panels))
+    tiles += panels * (ldq // 128) * cb + ((ldq + 255) // 256) * rb * cb
+    alg = 2.0 * N * N * r + 2.0 * N * r * r
+    exe = tiles * 2.0 * 128 * 64 * 256 * 15
+    pk, src = peaks()
+    peak = pk["bf16_tflops_sustained"]
+    roof = {"bound": "tensor", "achieved": alg / (ms_step / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": alg / (ms_step / 1e3) / 1e12 / peak, "traffic": None,
+            "kernel": "ozaki_gemm (digit-split products with the inverse factor)",
+            "peak_source": f"bf16 sustained ({src})",
+            "work": f"2 N^2 r + 2 N r^2 = {alg:.3e} flop per update, N = {N}, r = 2k = {r}",
+            "executed": {"flops_per_step": exe, "tflops": exe / (ms_step / 1e3) / 1e12,
+                         "frac": exe / (ms_step / 1e3) / 1e12 / peak,
+                         "what": "every 128x64 tile of the panel GEMMs x 15 digit products"},
+            "timing": "work / whole update time (a lower bound of the GEMMs' rate)"}
     line = {"metric": "camera covariances/s after adding observations (4k-cam scene)", "value": value,
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -950,6 +974,7 @@ def run_update(args):
             "e2e": {"value": scene.n * world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": add.nbytes,
                     "d2h_bytes_per_step": scene.n * 81 * 8, "ms_per_step": ms_e2e},
             "gpu_launches": int(launches),
+            "roofline": roof,
             "vs_new_step_d": {"ms_new_steps_a_to_d": ms_full, "speedup_of_update": ms_full / ms_step,
                               "max_rel_fro_per_block": float(errs["rel_fro"].max()),
                               "max_norm_err_per_block": float(errs["norm_err"].max()),

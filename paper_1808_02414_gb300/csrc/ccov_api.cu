@@ -54,7 +54,7 @@ void free_all(Ctx& c) {
     void* ptrs[] = {c.d_cams, c.d_pts, c.d_obs, c.d_obscov, c.d_pt_ptr, c.d_cam_ptr, c.d_cam_perm,
                     c.d_camprep, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.d_Gp, c.d_W7, c.d_HP, c.d_R,
                     c.d_P, c.d_Linv, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag,
-                    c.d_V, c.d_pair_desc, c.d_pair_ent, c.d_w7part};
+                    c.d_V, c.d_J, c.d_pair_desc, c.d_pair_ent, c.d_w7part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ccov::mixed_free(c);
@@ -428,6 +428,7 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     CK(dalloc(c, &c.d_U, 45 * n), "alloc");
     CK(dalloc(c, &c.d_Z, Np * Np), "alloc Z");
     CK(dalloc(c, &c.d_V, 27 * t), "alloc");
+    CK(dalloc(c, &c.d_J, 24 * t), "alloc");
     CK(dalloc(c, &c.d_pair_desc, c.npairs), "alloc");
     CK(dalloc(c, &c.d_pair_ent, c.nent), "alloc");
     CK(dalloc(c, &c.d_w7part, 56 * 2048), "alloc");
@@ -527,7 +528,7 @@ ccov_status enq_schur(Ctx& c) {
 
 ccov_status enq_nullspace(Ctx& c, bool prep) {
     if (prep) ccov::launch_cam_prep(c);
-    ccov::launch_nullspace(c);
+    ccov::launch_nullspace(c, !prep);   // after step (a) on these inputs: its kept Jacobians
     CK(cudaGetLastError(), "ccov_nullspace launch");
     return CCOV_OK;
 }

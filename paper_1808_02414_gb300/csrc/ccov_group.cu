@@ -427,7 +427,7 @@ cudaError_t group_enqueue(GroupPlan& P, cudaStream_t main) {
     if ((e = cudaMemsetAsync(c.d_Z, 0, sizeof(double) * zsum, main)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c.d_W7, 0, sizeof(double) * 128 * P.k, main)) != cudaSuccess) return e;
     launch_schur(c);
-    launch_nullspace(c);
+    launch_nullspace(c, true);
     launch_g(c);
     grp_gauge(main, P.at<GaugeP>(P.gauge_rec), P.k, c.d_flag);
     grp_fd(main, P.at<FdP>(P.fd_rec), P.at<int64_t>(P.fd_pre), P.k, P.fd_blocks, c.d_flag);
@@ -455,7 +455,7 @@ void group_free(GroupPlan* P) {
     if (P->hi) cudaStreamSynchronize(P->hi);
     if (P->side) cudaStreamSynchronize(P->side);
     void* ptrs[] = {c.d_cams, c.d_pts, c.d_obs, c.d_obscov, c.d_pt_ptr, c.d_cam_ptr, c.d_cam_perm, c.d_camprep,
-                    c.d_W, c.d_Ainv, c.d_U, c.d_V, c.d_pair_desc, c.d_pair_ent, c.d_w7part, c.d_Z, c.d_Gp, c.d_W7,
+                    c.d_W, c.d_Ainv, c.d_U, c.d_V, c.d_J, c.d_pair_desc, c.d_pair_ent, c.d_w7part, c.d_Z, c.d_Gp, c.d_W7,
                     c.d_HP, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag, P->R, P->d_blob,
                     const_cast<int*>(c.d_cam_scene), const_cast<int64_t*>(c.d_scene_zo),
                     const_cast<int64_t*>(c.d_scene_ld), const_cast<int*>(c.d_scene_co),
@@ -559,7 +559,7 @@ cudaError_t group_create(Ctx* const* ctxs, double* const* outs, int k, GroupPlan
     if (c.has_cov) GCK(galloc(c, &c.d_obscov, 4 * ts));
     GCK(galloc(c, &c.d_pt_ptr, ms + 1)); GCK(galloc(c, &c.d_cam_ptr, ns + 1)); GCK(galloc(c, &c.d_cam_perm, ts));
     GCK(galloc(c, &c.d_camprep, kCamPrep * ns)); GCK(galloc(c, &c.d_W, 27 * ts)); GCK(galloc(c, &c.d_Ainv, 6 * ms));
-    GCK(galloc(c, &c.d_U, 45 * ns)); GCK(galloc(c, &c.d_V, 27 * ts));
+    GCK(galloc(c, &c.d_U, 45 * ns)); GCK(galloc(c, &c.d_V, 27 * ts)); GCK(galloc(c, &c.d_J, 24 * ts));
     GCK(galloc(c, &c.d_pair_desc, np)); GCK(galloc(c, &c.d_pair_ent, ne));
     GCK(galloc(c, &c.d_w7part, (size_t)56 * k * c.w7_wps));
     GCK(galloc(c, &c.d_Z, zs)); GCK(galloc(c, &c.d_Gp, 7 * 9 * ns)); GCK(galloc(c, &c.d_W7, 128 * k));

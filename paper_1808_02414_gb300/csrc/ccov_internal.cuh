@@ -57,7 +57,8 @@ struct Ctx {
     double* d_Ainv = nullptr;     // m x 6 (xx xy xz yy yz zz)
     double* d_U = nullptr;        // n x 45 (lower triangle, row by row)
     // step (b), (c)
-    double* d_V = nullptr;        // t x 27: W A^-1 per observation
+    double* d_V = nullptr;        // t x 27: W A^-1 per observation (step (a): scratch)
+    double* d_J = nullptr;        // t x 24: unwhitened Jc (2 x 9), Jp (2 x 3) per observation, from step (a)
     int4* d_pair_desc = nullptr;  // blocks Z_ik with shared points: (i, k, first entry, entries)
     int2* d_pair_ent = nullptr;   // per block, the observation pairs (o_i, o_k) in point order
     int64_t npairs = 0, nent = 0;
@@ -127,7 +128,7 @@ void launch_cam_prep(Ctx& c);
 void launch_point_info(Ctx& c);
 void launch_cam_info(Ctx& c);
 void launch_schur(Ctx& c);
-void launch_nullspace(Ctx& c);
+void launch_nullspace(Ctx& c, bool kept_jacobians);   // kept: step (a) ran on the current inputs
 
 // ---- launchers (k_dense64.cu) ----
 void launch_form_scaled(Ctx& c);           // G, W7^-1, F, D, Z_s = D (Z + F G^T) D

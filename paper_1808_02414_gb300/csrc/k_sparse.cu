@@ -153,16 +153,17 @@ __device__ __forceinline__ void whiten(double* Jc, double* Jp, double sigma,
     }
 }
 
-// Step (a), point part in two passes (the same quantities as
-// point_info_kernel, whose warp per point leaves most lanes idle on tracks of
-// a few observations): a thread per observation computes the whitened
-// Jacobian, W_ij = Jc^T Jp and the observation's share Jp^T Jp of A_j (six
-// values into `share`); a thread per point then sums the shares of its
-// observations in order and inverts A_j.
+// Step (a), point part in two passes (a warp per point leaves most lanes
+// idle on tracks of a few observations): a thread per observation computes
+// the Jacobian, keeps it unwhitened in J (Jc 2 x 9, then Jp 2 x 3: 24 values,
+// read again by the camera blocks and the nullspace), whitens it and writes
+// W_ij = Jc^T Jp and the observation's share Jp^T Jp of A_j (six values into
+// `share`); a thread per point then sums the shares of its observations in
+// order and inverts A_j.
 __global__ void __launch_bounds__(128)
 obs_info_kernel(int64_t t, const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
                 const double* __restrict__ prep, double sigma, const double* __restrict__ cov,
-                double* __restrict__ W, double* __restrict__ share, int* flag) {
+                double* __restrict__ W, double* __restrict__ share, double* __restrict__ J, int* flag) {
     const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (o >= t) return;
     const int i = obs[o].cam;
@@ -170,6 +171,11 @@ obs_info_kernel(int64_t t, const ccov_obs* __restrict__ obs, const double* __res
     double Jc[18], Jp[6];
     const double depth = obs_jacobian(prep + (int64_t)kCamPrep * i, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], Jc, Jp);
     if (!(depth > 0.0)) set_flag(flag, DEV_BEHIND, (int)o);
+    double* jo = J + 24 * o;
+#pragma unroll
+    for (int e = 0; e < 18; ++e) jo[e] = Jc[e];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) jo[18 + e] = Jp[e];
     whiten(Jc, Jp, sigma, cov ? cov + 4 * o : nullptr);
     double* a = share + 6 * o;
     a[0] = Jp[0] * Jp[0] + Jp[3] * Jp[3];
@@ -211,12 +217,12 @@ point_ainv_kernel(int64_t m, const int* __restrict__ pt_ptr, const double* __res
     ai[5] = (a[0] * a[3] - a[1] * a[1]) * id;
 }
 
-// Step (a), camera part: warp per camera, U_i = sum Jc^T Jc (lower, 45).
+// Step (a), camera part: warp per camera, U_i = sum Jc^T Jc (lower, 45),
+// from the Jacobians that obs_info_kernel kept (J, unwhitened).
 __global__ void __launch_bounds__(32 * kWarps)
 cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
-                const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
-                const double* __restrict__ prep, double sigma, const double* __restrict__ cov,
-                double* __restrict__ U) {
+                const double* __restrict__ J, const double* __restrict__ prep, double sigma,
+                const double* __restrict__ cov, double* __restrict__ U) {
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -226,10 +232,13 @@ cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restric
         for (int e = 0; e < 45; ++e) u[e] = 0.0;
         const double* cp = prep + (int64_t)kCamPrep * i;
         for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
-            int o = cam_perm[k];
-            int j = obs[o].pt;
+            const int o = cam_perm[k];
+            const double* jo = J + 24 * (int64_t)o;
             double Jc[18], Jp[6];
-            obs_jacobian(cp, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], Jc, Jp);
+#pragma unroll
+            for (int e = 0; e < 18; ++e) Jc[e] = jo[e];
+#pragma unroll
+            for (int e = 0; e < 6; ++e) Jp[e] = jo[18 + e];
             whiten(Jc, Jp, sigma, cov ? cov + 4 * (int64_t)o : nullptr);
             int e = 0;
 #pragma unroll
@@ -391,10 +400,16 @@ schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __
 }
 
 // W7 = sum_j H_Xj^T A_j^-1 H_Xj and sum_j H_Xj^T H_Xj (for H^T H of the gauge
-// term), per scene: wps warps per scene, warp q of scene s summing its points
-// po[s] + q, + 2 wps, ... (po null: one scene of m points); lane e < 28 owns
-// entry (p, q), p <= q.  Partial sums part[w][56], w = s wps + q.
+// term), per scene: wps warps per scene; warp q of scene s takes the points
+// po[s] + q + wps (32 u + l) on its lane l (po null: one scene of m points),
+// each lane forming all 28 upper entries of both sums for its points (a
+// column B_q = A_j^-1 H_Xj e_q at a time, H_X = [I, -[X]x, X]); the warp then
+// sums its lanes by a fixed butterfly.  Partial sums part[w][56], w = s wps +
+// q: W7 entries (p, q), p <= q, row by row, then those of H_X^T H_X.
+__device__ __forceinline__ constexpr int upper_index(int p, int q) { return p * 7 - p * (p - 1) / 2 + (q - p); }
+
 constexpr int kW7Warps = 2048;
+
 __global__ void __launch_bounds__(32 * kWarps)
 w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __restrict__ pts,
                   double* __restrict__ part, const int* __restrict__ po, int wps) {
@@ -402,34 +417,38 @@ w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __re
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t sc = warp / wps, q0 = warp % wps;
     const int64_t j0 = po ? po[sc] : 0, j1 = po ? po[sc + 1] : m;
-    int w7p = 0, w7q = 0;
-    {
-        int e = lane, p = 0;
-        while (p < 7 && e >= 7 - p) { e -= 7 - p; ++p; }
-        w7p = p; w7q = p + e;
-    }
-    double w7acc = 0.0, hhacc = 0.0;
-    if (lane < 28) {
-        for (int64_t j = j0 + q0; j < j1; j += wps) {
-            const double* ai = Ainv + 6 * j;
-            const double Am[9] = {ai[0], ai[1], ai[2], ai[1], ai[3], ai[4], ai[2], ai[4], ai[5]};
-            const double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
-            double hp[7], hq[7], v = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                hx_row(X0, X1, X2, k, hp);
-                hhacc += hp[w7p] * hp[w7q];
+    double w7[28], hh[28];
+#pragma unroll
+    for (int e = 0; e < 28; ++e) { w7[e] = 0.0; hh[e] = 0.0; }
+    for (int64_t j = j0 + q0 + (int64_t)wps * lane; j < j1; j += (int64_t)wps * 32) {
+        const double* ai = Ainv + 6 * j;
+        const double A00 = ai[0], A01 = ai[1], A02 = ai[2], A11 = ai[3], A12 = ai[4], A22 = ai[5];
+        const double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
+        double H[3][7];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) hx_row(X0, X1, X2, k, H[k]);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const double b0 = A00 * H[0][q] + A01 * H[1][q] + A02 * H[2][q];
+            const double b1 = A01 * H[0][q] + A11 * H[1][q] + A12 * H[2][q];
+            const double b2 = A02 * H[0][q] + A12 * H[1][q] + A22 * H[2][q];
+#pragma unroll
+            for (int p = 0; p <= q; ++p) {
+                const int e = upper_index(p, q);
+                w7[e] += H[0][p] * b0 + H[1][p] * b1 + H[2][p] * b2;
+                hh[e] += H[0][p] * H[0][q] + H[1][p] * H[1][q] + H[2][p] * H[2][q];
             }
-            for (int k = 0; k < 3; ++k) {
-                hx_row(X0, X1, X2, k, hp);
-                for (int l = 0; l < 3; ++l) {
-                    hx_row(X0, X1, X2, l, hq);
-                    v += hp[w7p] * Am[3 * k + l] * hq[w7q];
-                }
-            }
-            w7acc += v;
         }
-        part[56 * warp + lane] = w7acc;
-        part[56 * warp + 28 + lane] = hhacc;
+    }
+#pragma unroll
+    for (int e = 0; e < 28; ++e) {
+        w7[e] = warp_sum(w7[e]);
+        hh[e] = warp_sum(hh[e]);
+    }
+    if (lane == 0) {
+        double* pw = part + 56 * warp;
+#pragma unroll
+        for (int e = 0; e < 28; ++e) { pw[e] = w7[e]; pw[28 + e] = hh[e]; }
     }
 }
 
@@ -455,9 +474,7 @@ __global__ void w7_reduce_kernel(const double* __restrict__ part, double* __rest
 __global__ void __launch_bounds__(32 * kWarps)
 cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
                  const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
-                 const double* __restrict__ W, const double* __restrict__ Ainv,
-                 const double* __restrict__ U, double* __restrict__ Z, int64_t ldz,
-                 double* __restrict__ Gp) {
+                 const double* __restrict__ V, double* __restrict__ Gp) {
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -471,16 +488,11 @@ cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
         for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
             int o = cam_perm[k];
             int j = obs[o].pt;
-            const double* ai = Ainv + 6 * (int64_t)j;
-            double Am[9] = {ai[0], ai[1], ai[2], ai[1], ai[3], ai[4], ai[2], ai[4], ai[5]};
             double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
-            const double* w = W + 27 * (int64_t)o;
+            const double* vo = V + 27 * (int64_t)o;   // V = W A^-1 of this observation (vmat_kernel)
 #pragma unroll
             for (int p = 0; p < 9; ++p) {
-                double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
-                double v0 = w0 * Am[0] + w1 * Am[3] + w2 * Am[6];
-                double v1 = w0 * Am[1] + w1 * Am[4] + w2 * Am[7];
-                double v2 = w0 * Am[2] + w1 * Am[5] + w2 * Am[8];
+                const double v0 = vo[3 * p], v1 = vo[3 * p + 1], v2 = vo[3 * p + 2];
                 sV[3 * p] += v0; sV[3 * p + 1] += v1; sV[3 * p + 2] += v2;
                 sVX[p] += v0 * X0 + v1 * X1 + v2 * X2;
                 // V [X]x, [X]x = [[0,-X2,X1],[X2,0,-X0],[-X1,X0,0]]
@@ -513,7 +525,7 @@ __global__ void __launch_bounds__(32 * kWarps)
 nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
                  const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
                  const double* __restrict__ cams, const double* __restrict__ prep, int route,
-                 double* __restrict__ HP, int* flag) {
+                 const double* __restrict__ J, double* __restrict__ HP, int* flag) {
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -559,7 +571,15 @@ nullspace_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
                 int j = obs[o].pt;
                 double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
                 double Jc[18], Jp[6];
-                obs_jacobian(cp, X0, X1, X2, Jc, Jp);
+                if (J) {   // kept by step (a) (unwhitened)
+                    const double* jo = J + 24 * (int64_t)o;
+#pragma unroll
+                    for (int e = 0; e < 18; ++e) Jc[e] = jo[e];
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) Jp[e] = jo[18 + e];
+                } else {
+                    obs_jacobian(cp, X0, X1, X2, Jc, Jp);
+                }
 #pragma unroll
                 for (int row = 0; row < 2; ++row) {
                     const double* jr = Jc + 9 * row;       // d/dr (3)
@@ -680,7 +700,7 @@ void launch_point_info(Ctx& c) {
     // the observations' shares of A go into V (t x 27), which step (b) fills later
     obs_info_kernel<<<(unsigned)((c.t + 127) / 128), 128, 0, c.stream>>>(c.t, c.d_obs, c.d_pts, c.d_camprep,
                                                                          c.sigma, c.d_obscov, c.d_W, c.d_V,
-                                                                         c.d_flag);
+                                                                         c.d_J, c.d_flag);
     CCOV_LAUNCH_CHECK(c);
     point_ainv_kernel<<<(unsigned)((c.m + 127) / 128), 128, 0, c.stream>>>(c.m, c.d_pt_ptr, c.d_V, c.d_Ainv,
                                                                            c.d_flag);
@@ -689,7 +709,7 @@ void launch_point_info(Ctx& c) {
 
 void launch_cam_info(Ctx& c) {
     cam_info_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_camprep, c.sigma, c.d_obscov, c.d_U);
+        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_J, c.d_camprep, c.sigma, c.d_obscov, c.d_U);
     CCOV_LAUNCH_CHECK(c);
 }
 
@@ -712,15 +732,14 @@ void launch_schur(Ctx& c) {
     w7_reduce_kernel<<<c.nscenes, 64, 0, c.stream>>>(c.d_w7part, c.d_W7, wps);
     CCOV_LAUNCH_CHECK(c);
     cam_schur_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.Np,
-        c.d_Gp);
+        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_V, c.d_Gp);
     CCOV_LAUNCH_CHECK(c);
 }
 
-void launch_nullspace(Ctx& c) {
+void launch_nullspace(Ctx& c, bool kept_jacobians) {
     nullspace_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
         c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_cams, c.d_camprep,
-        c.opt.nullspace_route, c.d_HP, c.d_flag);
+        c.opt.nullspace_route, kept_jacobians ? c.d_J : nullptr, c.d_HP, c.d_flag);
     CCOV_LAUNCH_CHECK(c);
 }
 
