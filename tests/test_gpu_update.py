@@ -81,6 +81,33 @@ def test_update_centre_camera_against_the_oracle():
     np.testing.assert_allclose(got[:, 8, 8], 1.0, rtol=1e-12)
 
 
+def _with_extra(sc, cams, pts):
+    """The scene with extra observations (cam, pt) appended in point order
+    (pairs may repeat existing ones: the oracle adds their information)."""
+    cam = np.concatenate([sc.obs_cam, np.asarray(cams, np.int32)])
+    pt = np.concatenate([sc.obs_pt, np.asarray(pts, np.int32)])
+    u = np.concatenate([sc.obs_u, np.zeros((len(cams), 2))])
+    order = np.lexsort((cam, pt))
+    return synth.Scene(sc.cams, sc.pts, cam[order].astype(np.int32), pt[order].astype(np.int32), u[order],
+                       sc.sigma, None, dict(sc.meta))
+
+
+@pytest.mark.parametrize("prec,tol", [(ccov.CCOV_PREC_FP64, FP64_TOL), (ccov.CCOV_PREC_MIXED, MIXED_TOL)])
+def test_update_one_observation_and_a_repeated_pair(prec, tol):
+    """k = 1, and an added observation of a (camera, point) pair that the scene
+    already has (a second, independent measurement of the same projection)."""
+    sc = synth.shell_scene(n=30, m=2000, seed=12)
+    c, j = int(sc.obs_cam[5]), int(sc.obs_pt[5])
+    other = int(np.flatnonzero(~np.isin(np.arange(sc.n), sc.obs_cam[sc.obs_pt == 7]))[0])
+    for cams, pts in (([other], [7]), ([c], [j])):
+        add = np.zeros(len(cams), dtype=synth.OBS_DTYPE)
+        add["cam"], add["pt"] = cams, pts
+        with ccov.from_scene(sc, precision=prec) as ctx:
+            ctx.run()
+            got = ctx.ccov_update_observations(add)
+        assert_blocks_close(got, covariance.camera_covariance(_with_extra(sc, cams, pts)), tol, "update")
+
+
 def test_update_keeps_the_context_and_repeats_bit_exactly():
     sc = synth.shell_scene(n=30, m=2000, seed=12)
     _, add_a = synth.added_observations(sc, 40, cams=[0, 1, 2, 3], seed=4)
