@@ -999,41 +999,51 @@ potrf_diag_q_kernel(long long* __restrict__ Z, int64_t ld, int64_t k0, __nv_bflo
 // takes entries (a, b), a <= b, of the symmetric blocks (45 per camera) and
 // sums the 128 rows in four interleaved chains.
 constexpr int kGW = 36;
+constexpr int kGT = 192;                    // threads: one per entry (4 cameras x 45 = 180)
 __device__ __forceinline__ void gram_q_body(int64_t n, int64_t Np, int64_t k0, int64_t ncols,
                                             const long long* __restrict__ R, double* __restrict__ Sig, int64_t bid) {
     __shared__ dsf T[kNB][kGW + 1];
     const int tid = threadIdx.x;
     const int64_t c0 = bid * (int64_t)kGW;
     constexpr float kS = 2.2737367544323206e-13f;  // 2^-42
-    for (int e = tid; e < kNB * kGW; e += 128) {
-        int r = e / kGW, c = e % kGW;
-        int64_t gc = c0 + c;
-        T[r][c] = (gc < ncols) ? ds_from_fixed(R[(k0 + r) * Np + gc], kS) : dsf{0.f, 0.f};
+    // every load issued before any is used: the row block comes from L2 or
+    // DRAM, and one load at a time would pay that latency kNB kGW / kGT times
+    constexpr int kPer = kNB * kGW / kGT;
+    long long vals[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = tid + kGT * u, r = e / kGW, c = e % kGW;
+        const int64_t gc = c0 + c;
+        vals[u] = gc < ncols ? R[(k0 + r) * Np + gc] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = tid + kGT * u, r = e / kGW, c = e % kGW;
+        T[r][c] = ds_from_fixed(vals[u], kS);
     }
     __syncthreads();
-    for (int e = tid; e < 4 * 45; e += 128) {
-        const int g = e / 45;
-        int q = e % 45, a = 0;                 // q -> (a, b) of the upper triangle, row by row
-        while (q >= 9 - a) { q -= 9 - a; ++a; }
-        const int b = a + q;
-        const int64_t cam = (c0 / 9) + g;
-        if (cam >= n || c0 + 9 * g >= ncols) continue;
-        const int ca = 9 * g + a, cb = 9 * g + b;
-        dsf v0 = {0.f, 0.f}, v1 = v0, v2 = v0, v3 = v0;
-        for (int r = 0; r < kNB; r += 4) {
-            v0 = ds_fma(v0, T[r][ca], T[r][cb]);
-            v1 = ds_fma(v1, T[r + 1][ca], T[r + 1][cb]);
-            v2 = ds_fma(v2, T[r + 2][ca], T[r + 2][cb]);
-            v3 = ds_fma(v3, T[r + 3][ca], T[r + 3][cb]);
-        }
-        const dsf v = ds_add(ds_add(v0, v1), ds_add(v2, v3));
-        const double sum = (double)v.h + (double)v.l;
-        Sig[81 * cam + 9 * a + b] += sum;
-        if (a != b) Sig[81 * cam + 9 * b + a] += sum;
+    if (tid >= 4 * 45) return;
+    const int g = tid / 45;
+    int q = tid % 45, a = 0;                   // q -> (a, b) of the upper triangle, row by row
+    while (q >= 9 - a) { q -= 9 - a; ++a; }
+    const int b = a + q;
+    const int64_t cam = (c0 / 9) + g;
+    if (cam >= n || c0 + 9 * g >= ncols) return;
+    const int ca = 9 * g + a, cb = 9 * g + b;
+    dsf v0 = {0.f, 0.f}, v1 = v0, v2 = v0, v3 = v0;
+    for (int r = 0; r < kNB; r += 4) {
+        v0 = ds_fma(v0, T[r][ca], T[r][cb]);
+        v1 = ds_fma(v1, T[r + 1][ca], T[r + 1][cb]);
+        v2 = ds_fma(v2, T[r + 2][ca], T[r + 2][cb]);
+        v3 = ds_fma(v3, T[r + 3][ca], T[r + 3][cb]);
     }
+    const dsf v = ds_add(ds_add(v0, v1), ds_add(v2, v3));
+    const double sum = (double)v.h + (double)v.l;
+    Sig[81 * cam + 9 * a + b] += sum;
+    if (a != b) Sig[81 * cam + 9 * b + a] += sum;
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kGT)
 gram_q_kernel(int64_t n, int64_t Np, int64_t k0, int64_t ncols, const long long* __restrict__ R,
               double* __restrict__ Sig) {
     gram_q_body(n, Np, k0, ncols, R, Sig, blockIdx.x);
@@ -1066,7 +1076,7 @@ __global__ void __launch_bounds__(512) potrf_diag_q_grouped(const PotrfP* __rest
     potrf_diag_q_body(a.Z, a.ld, a.k0, a.digL, a.expL, a.s, flag);
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kGT)
 gram_q_grouped(const GramP* __restrict__ P, const int64_t* __restrict__ pre, int k) {
     const int q = find_group(pre, k, blockIdx.x);
     const GramP& a = P[q];
@@ -1274,7 +1284,7 @@ void grp_potrf(cudaStream_t st, const PotrfP* P, int k, int* flag) {
 }
 
 void grp_gram(cudaStream_t st, const GramP* P, const int64_t* pre, int k, int64_t blocks) {
-    gram_q_grouped<<<(unsigned)blocks, 128, 0, st>>>(P, pre, k);
+    gram_q_grouped<<<(unsigned)blocks, kGT, 0, st>>>(P, pre, k);
 }
 
 void grp_zscale(cudaStream_t st, const ZscaleP* P, const int64_t* pre, int k, int64_t blocks, int* flag) {
@@ -1828,7 +1838,7 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         // X[blk, :nc] = L_blk^-1 R[blk, :nc]
         slice_cols(c, 128, (int)nc, Rat(k0, 0), BUF_Q);
         launch_ozaki(c, 128, BUF_L, (int)k0, kNB, BUF_Q, 0, (int)nc, st.mapR, 0, (int)k0, 0, 0, kFX, st.expL, st.expQ);
-        gram_q_kernel<<<(int)((nc + kGW - 1) / kGW), 128, 0, c.stream>>>(c.n, Np, k0, nc, st.R, c.d_Sig);
+        gram_q_kernel<<<(int)((nc + kGW - 1) / kGW), kGT, 0, c.stream>>>(c.n, Np, k0, nc, st.R, c.d_Sig);
         c.launches++;
     };
     for (int64_t p = 0; p < nb; p += 2) {
