@@ -431,7 +431,8 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     CK(dalloc(c, &c.d_J, 24 * t), "alloc");
     CK(dalloc(c, &c.d_pair_desc, c.npairs), "alloc");
     CK(dalloc(c, &c.d_pair_ent, c.nent), "alloc");
-    CK(dalloc(c, &c.d_w7part, 56 * 2048), "alloc");
+    c.w7_wps = ccov::w7_warps_for(m);
+    CK(dalloc(c, &c.d_w7part, 56 * (size_t)c.w7_wps), "alloc");
     CK(dalloc(c, &c.d_Gp, 7 * c.N), "alloc");
     CK(dalloc(c, &c.d_W7, 128), "alloc");
     CK(dalloc(c, &c.d_HP, 63 * n), "alloc");

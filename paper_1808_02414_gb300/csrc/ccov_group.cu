@@ -459,7 +459,7 @@ void group_free(GroupPlan* P) {
                     c.d_HP, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag, P->R, P->d_blob,
                     const_cast<int*>(c.d_cam_scene), const_cast<int64_t*>(c.d_scene_zo),
                     const_cast<int64_t*>(c.d_scene_ld), const_cast<int*>(c.d_scene_co),
-                    const_cast<int*>(c.d_scene_po)};
+                    const_cast<int*>(c.d_scene_po), const_cast<int64_t*>(c.d_scene_wpo)};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 5; ++b) {
@@ -523,9 +523,11 @@ cudaError_t group_create(Ctx* const* ctxs, double* const* outs, int k, GroupPlan
     }
     P.co.push_back(ns); P.po.push_back(ms); P.oo.push_back(ts);
     c.n = ns; c.m = ms; c.t = ts; c.N = 9 * ns; c.Np = 0; c.npairs = np; c.nent = ne; c.nscenes = k;
-    // the same 2048 interleaved partial sums per scene as a single scene's
-    // W7, so that every scene's sums run in the same order as on its own
-    c.w7_wps = 2048;
+    // per scene the same W7 partial sums as on its own (warps by its point
+    // count), so that every scene's sums run in the same order
+    std::vector<int64_t> wpo(k + 1, 0);
+    for (int q = 0; q < k; ++q) wpo[q + 1] = wpo[q] + w7_warps_for(ctxs[q]->m);
+    c.w7_total = wpo[k];
     // index arrays of the super-scene, from each context's device copies
     std::vector<int> pt_ptr(ms + 1, 0), cam_ptr(ns + 1, 0), cam_perm(ts), cam_scene(ns), sco(k), spo(k + 1);
     std::vector<int4> desc;
@@ -561,7 +563,7 @@ cudaError_t group_create(Ctx* const* ctxs, double* const* outs, int k, GroupPlan
     GCK(galloc(c, &c.d_camprep, kCamPrep * ns)); GCK(galloc(c, &c.d_W, 27 * ts)); GCK(galloc(c, &c.d_Ainv, 6 * ms));
     GCK(galloc(c, &c.d_U, 45 * ns)); GCK(galloc(c, &c.d_V, 27 * ts)); GCK(galloc(c, &c.d_J, 24 * ts));
     GCK(galloc(c, &c.d_pair_desc, np)); GCK(galloc(c, &c.d_pair_ent, ne));
-    GCK(galloc(c, &c.d_w7part, (size_t)56 * k * c.w7_wps));
+    GCK(galloc(c, &c.d_w7part, (size_t)56 * c.w7_total));
     GCK(galloc(c, &c.d_Z, zs)); GCK(galloc(c, &c.d_Gp, 7 * 9 * ns)); GCK(galloc(c, &c.d_W7, 128 * k));
     GCK(galloc(c, &c.d_HP, 63 * ns)); GCK(galloc(c, &c.d_F, 7 * 9 * ns)); GCK(galloc(c, &c.d_G, 7 * 9 * ns));
     GCK(galloc(c, &c.d_D, ds)); GCK(galloc(c, &c.d_Sig, 81 * ns)); GCK(galloc(c, &c.d_small, 128 * k));
@@ -579,6 +581,12 @@ cudaError_t group_create(Ctx* const* ctxs, double* const* outs, int k, GroupPlan
     GCK(galloc(c, &d_sld, k)); c.d_scene_ld = d_sld;
     GCK(galloc(c, &d_sco, k)); c.d_scene_co = d_sco;
     GCK(galloc(c, &d_spo, k + 1)); c.d_scene_po = d_spo;
+    {
+        int64_t* d_wpo = nullptr;
+        GCK(galloc(c, &d_wpo, k + 1));
+        c.d_scene_wpo = d_wpo;
+        GCK(cudaMemcpy(d_wpo, wpo.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice));
+    }
     GCK(cudaMemcpy(c.d_pt_ptr, pt_ptr.data(), sizeof(int) * pt_ptr.size(), cudaMemcpyHostToDevice));
     GCK(cudaMemcpy(c.d_cam_ptr, cam_ptr.data(), sizeof(int) * cam_ptr.size(), cudaMemcpyHostToDevice));
     GCK(cudaMemcpy(c.d_cam_perm, cam_perm.data(), sizeof(int) * cam_perm.size(), cudaMemcpyHostToDevice));

@@ -71,7 +71,9 @@ struct Ctx {
     const int64_t* d_scene_ld = nullptr;
     const int* d_scene_co = nullptr;
     const int* d_scene_po = nullptr;
-    int nscenes = 1, w7_wps = 0;
+    const int64_t* d_scene_wpo = nullptr;   // several scenes: prefix of their W7 warp counts
+    int nscenes = 1, w7_wps = 0;            // one scene: its W7 warp count (w7_warps_for(m))
+    int64_t w7_total = 0;                   // several scenes: all their W7 warps
     double* d_Z = nullptr;        // Np x Np row-major, lower triangle
     double* d_Gp = nullptr;       // N x 7: -W A^-1 H_X
     double* d_W7 = nullptr;       // 7 x 7
@@ -128,7 +130,8 @@ void launch_cam_prep(Ctx& c);
 void launch_point_info(Ctx& c);
 void launch_cam_info(Ctx& c);
 void launch_schur(Ctx& c);
-void launch_nullspace(Ctx& c, bool kept_jacobians);   // kept: step (a) ran on the current inputs
+void launch_nullspace(Ctx& c, bool kept_jacobians);
+int w7_warps_for(int64_t m);                      // warps of a scene's W7 partial sums (<= 2048)   // kept: step (a) ran on the current inputs
 
 // ---- launchers (k_dense64.cu) ----
 void launch_form_scaled(Ctx& c);           // G, W7^-1, F, D, Z_s = D (Z + F G^T) D

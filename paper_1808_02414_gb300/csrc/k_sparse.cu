@@ -400,22 +400,29 @@ schur_pairs_kernel(int64_t npairs, const int4* __restrict__ desc, const int2* __
 }
 
 // W7 = sum_j H_Xj^T A_j^-1 H_Xj and sum_j H_Xj^T H_Xj (for H^T H of the gauge
-// term), per scene: wps warps per scene; warp q of scene s takes the points
-// po[s] + q + wps (32 u + l) on its lane l (po null: one scene of m points),
-// each lane forming all 28 upper entries of both sums for its points (a
-// column B_q = A_j^-1 H_Xj e_q at a time, H_X = [I, -[X]x, X]); the warp then
-// sums its lanes by a fixed butterfly.  Partial sums part[w][56], w = s wps +
-// q: W7 entries (p, q), p <= q, row by row, then those of H_X^T H_X.
+// term), per scene: the scene's wps warps (w7_warps_for(its point count), so
+// that a scene's sums run in the same order alone and in a batch); warp q of
+// scene s takes the points po[s] + q + wps (32 u + l) on its lane l, each lane
+// forming all 28 upper entries of both sums for its points (a column B_q =
+// A_j^-1 H_Xj e_q at a time, H_X = [I, -[X]x, X]); the warp then sums its
+// lanes by a fixed butterfly.  Warps of all scenes are numbered one after the
+// other (wpo: prefix of the scenes' warp counts; null for one scene of m points
+// and wps1 warps).  Partial sums part[w][56]: W7 entries (p, q), p <= q, row
+// by row, then those of H_X^T H_X.
 __device__ __forceinline__ constexpr int upper_index(int p, int q) { return p * 7 - p * (p - 1) / 2 + (q - p); }
 
-constexpr int kW7Warps = 2048;
+constexpr int kW7MaxWarps = 2048;
 
 __global__ void __launch_bounds__(32 * kWarps)
 w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __restrict__ pts,
-                  double* __restrict__ part, const int* __restrict__ po, int wps) {
+                  double* __restrict__ part, const int* __restrict__ po, const int64_t* __restrict__ wpo,
+                  int nscenes, int wps1, int64_t total) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t sc = warp / wps, q0 = warp % wps;
+    if (warp >= total) return;
+    const int sc = wpo ? find_group(wpo, nscenes, warp) : 0;
+    const int64_t q0 = wpo ? warp - wpo[sc] : warp;
+    const int64_t wps = wpo ? wpo[sc + 1] - wpo[sc] : wps1;
     const int64_t j0 = po ? po[sc] : 0, j1 = po ? po[sc + 1] : m;
     double w7[28], hh[28];
 #pragma unroll
@@ -455,10 +462,12 @@ w7_partial_kernel(int64_t m, const double* __restrict__ Ainv, const double* __re
 // The partial sums of scene s (block s) in warp order: W7 (upper, row-major
 // 7x7) at W7[128 s, 128 s + 49), H_X^T H_X at W7[128 s + 49, 128 s + 98).
 // One thread per entry.
-__global__ void w7_reduce_kernel(const double* __restrict__ part, double* __restrict__ W7, int wps) {
+__global__ void w7_reduce_kernel(const double* __restrict__ part, double* __restrict__ W7,
+                                 const int64_t* __restrict__ wpo, int wps1) {
     const int lane = threadIdx.x;
     if (lane >= 56) return;
-    part += 56 * (int64_t)wps * blockIdx.x;
+    const int64_t w0 = wpo ? wpo[blockIdx.x] : 0, wps = wpo ? wpo[blockIdx.x + 1] - w0 : wps1;
+    part += 56 * w0;
     W7 += 128 * (int64_t)blockIdx.x;
     const int e0 = lane % 28;
     int e = e0, p = 0;
@@ -725,15 +734,20 @@ void launch_schur(Ctx& c) {
             c.npairs, c.d_pair_desc, c.d_pair_ent, c.d_V, c.d_W, c.d_U, c.d_Z, c.Np, c.d_cam_scene, c.d_scene_zo,
             c.d_scene_ld, c.d_scene_co);
     CCOV_LAUNCH_CHECK(c);
-    const int wps = kW7Warps;
-    w7_partial_kernel<<<(unsigned)(c.nscenes * wps / kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.m, c.d_Ainv, c.d_pts, c.d_w7part, c.d_scene_po, wps);
+    const int64_t total = c.d_scene_wpo ? c.w7_total : c.w7_wps;
+    w7_partial_kernel<<<(unsigned)((total + kWarps - 1) / kWarps), 32 * kWarps, 0, c.stream>>>(
+        c.m, c.d_Ainv, c.d_pts, c.d_w7part, c.d_scene_po, c.d_scene_wpo, c.nscenes, c.w7_wps, total);
     CCOV_LAUNCH_CHECK(c);
-    w7_reduce_kernel<<<c.nscenes, 64, 0, c.stream>>>(c.d_w7part, c.d_W7, wps);
+    w7_reduce_kernel<<<c.nscenes, 64, 0, c.stream>>>(c.d_w7part, c.d_W7, c.d_scene_wpo, c.w7_wps);
     CCOV_LAUNCH_CHECK(c);
     cam_schur_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
         c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_V, c.d_Gp);
     CCOV_LAUNCH_CHECK(c);
+}
+
+int w7_warps_for(int64_t m) {
+    const int64_t w = (m + 511) / 512;   // about 16 points per lane
+    return (int)(w < 1 ? 1 : (w > kW7MaxWarps ? kW7MaxWarps : w));
 }
 
 void launch_nullspace(Ctx& c, bool kept_jacobians) {
