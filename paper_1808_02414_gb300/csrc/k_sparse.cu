@@ -7,6 +7,8 @@
 // block A_p; Sec. 4.1 (Eq. transformation-conditions, rotation-nullspace-
 // equation) gives the nullspace H.  Layout: observations sorted by point
 // (CSR by point, pt_ptr) plus a permutation grouping them by camera.
+#include <type_traits>
+
 #include "ccov_internal.cuh"
 #include "ds_arith.cuh"
 
@@ -20,6 +22,37 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Sums of the mixed form's sparse steps in double-single arithmetic (about
+// 44 bits, above the 39 of the digits step (d) takes of Z); the FP64 form
+// keeps FP64 with the same expressions as before.
+template <class T>
+struct SpAr;
+
+template <>
+struct SpAr<double> {
+    typedef double V;
+    static __device__ __forceinline__ double from(double x) { return x; }
+    static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double value(double a) { return a; }
+    static __device__ __forceinline__ double sum(double v) { return warp_sum(v); }
+};
+
+template <>
+struct SpAr<dsf> {
+    typedef dsf V;
+    static __device__ __forceinline__ dsf from(double x) { return ds_from_double(x); }
+    static __device__ __forceinline__ dsf zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ dsf add(dsf a, dsf b) { return ds_add(a, b); }
+    static __device__ __forceinline__ double value(dsf a) { return (double)a.h + (double)a.l; }
+    static __device__ __forceinline__ dsf sum(dsf v) {   // the same butterfly as warp_sum
+        for (int o = 16; o > 0; o >>= 1)
+            v = ds_add(v, {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+        return v;
+    }
+};
+
 
 __device__ __forceinline__ void set_flag(int* flag, int code, int detail) {
     if (atomicMax(flag, code) < code) flag[1] = detail;
@@ -219,6 +252,7 @@ point_ainv_kernel(int64_t m, const int* __restrict__ pt_ptr, const double* __res
 
 // Step (a), camera part: warp per camera, U_i = sum Jc^T Jc (lower, 45),
 // from the Jacobians that obs_info_kernel kept (J, unwhitened).
+template <class T>
 __global__ void __launch_bounds__(32 * kWarps)
 cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
                 const double* __restrict__ J, const double* __restrict__ prep, double sigma,
@@ -226,10 +260,11 @@ cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restric
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    typedef SpAr<T> Ar;
     for (int64_t i = warp; i < n; i += nwarp) {
-        double u[45];
+        typename Ar::V u[45];
 #pragma unroll
-        for (int e = 0; e < 45; ++e) u[e] = 0.0;
+        for (int e = 0; e < 45; ++e) u[e] = Ar::zero();
         const double* cp = prep + (int64_t)kCamPrep * i;
         for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
             const int o = cam_perm[k];
@@ -241,14 +276,24 @@ cam_info_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restric
             for (int e = 0; e < 6; ++e) Jp[e] = jo[18 + e];
             whiten(Jc, Jp, sigma, cov ? cov + 4 * (int64_t)o : nullptr);
             int e = 0;
+            if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-            for (int p = 0; p < 9; ++p)
+                for (int p = 0; p < 9; ++p)
 #pragma unroll
-                for (int q = 0; q <= p; ++q, ++e) u[e] += Jc[p] * Jc[q] + Jc[9 + p] * Jc[9 + q];
+                    for (int q = 0; q <= p; ++q, ++e) u[e] += Jc[p] * Jc[q] + Jc[9 + p] * Jc[9 + q];
+            } else {
+                dsf jc[18];
+#pragma unroll
+                for (int c = 0; c < 18; ++c) jc[c] = ds_from_double(Jc[c]);
+#pragma unroll
+                for (int p = 0; p < 9; ++p)
+#pragma unroll
+                    for (int q = 0; q <= p; ++q, ++e) u[e] = ds_fma(ds_fma(u[e], jc[p], jc[q]), jc[9 + p], jc[9 + q]);
+            }
         }
 #pragma unroll
         for (int e = 0; e < 45; ++e) {
-            double v = warp_sum(u[e]);
+            double v = Ar::value(Ar::sum(u[e]));
             // centre camera: a unit prior on the value that no observation sees (slot 8)
             if (e == 44 && cp[24] != 0.0) v += 1.0;
             if (lane == 0) U[45 * i + e] = v;
@@ -273,6 +318,7 @@ __device__ __forceinline__ void hx_row(double X0, double X1, double X2, int k, d
 }
 
 // V_o = W_o A_j^-1 for every observation o of point j (thread per observation).
+template <class T>
 __global__ void vmat_kernel(int64_t t, const ccov_obs* __restrict__ obs, const double* __restrict__ W,
                             const double* __restrict__ Ainv, double* __restrict__ V) {
     const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -281,12 +327,26 @@ __global__ void vmat_kernel(int64_t t, const ccov_obs* __restrict__ obs, const d
     const double A00 = ai[0], A01 = ai[1], A02 = ai[2], A11 = ai[3], A12 = ai[4], A22 = ai[5];
     const double* w = W + 27 * o;
     double* v = V + 27 * o;
+    if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        const double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
-        v[3 * p] = w0 * A00 + w1 * A01 + w2 * A02;
-        v[3 * p + 1] = w0 * A01 + w1 * A11 + w2 * A12;
-        v[3 * p + 2] = w0 * A02 + w1 * A12 + w2 * A22;
+        for (int p = 0; p < 9; ++p) {
+            const double w0 = w[3 * p], w1 = w[3 * p + 1], w2 = w[3 * p + 2];
+            v[3 * p] = w0 * A00 + w1 * A01 + w2 * A02;
+            v[3 * p + 1] = w0 * A01 + w1 * A11 + w2 * A12;
+            v[3 * p + 2] = w0 * A02 + w1 * A12 + w2 * A22;
+        }
+    } else {
+        const dsf a[9] = {ds_from_double(A00), ds_from_double(A01), ds_from_double(A02),
+                          ds_from_double(A01), ds_from_double(A11), ds_from_double(A12),
+                          ds_from_double(A02), ds_from_double(A12), ds_from_double(A22)};
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            const dsf w0 = ds_from_double(w[3 * p]), w1 = ds_from_double(w[3 * p + 1]),
+                      w2 = ds_from_double(w[3 * p + 2]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                v[3 * p + q] = SpAr<dsf>::value(ds_fma(ds_fma(ds_mul(w0, a[q]), w1, a[3 + q]), w2, a[6 + q]));
+        }
     }
 }
 
@@ -480,6 +540,7 @@ __global__ void w7_reduce_kernel(const double* __restrict__ part, double* __rest
 
 // Step (b), camera part: warp per camera.  G_i = -sum_j V_ij H_Xj (the border
 // column block of Z_p without H_P), summed in a fixed lane order.
+template <class T>
 __global__ void __launch_bounds__(32 * kWarps)
 cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restrict__ cam_perm,
                  const ccov_obs* __restrict__ obs, const double* __restrict__ pts,
@@ -487,27 +548,47 @@ cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    typedef SpAr<T> Ar;
+    typedef typename Ar::V E;
     for (int64_t i = warp; i < n; i += nwarp) {
         // G_i = -[sum V, -sum V [X]x, sum V X]
-        double sV[27], sVX[9], sVK[27];
+        E sV[27], sVX[9], sVK[27];
 #pragma unroll
-        for (int e = 0; e < 27; ++e) { sV[e] = 0.0; sVK[e] = 0.0; }
+        for (int e = 0; e < 27; ++e) { sV[e] = Ar::zero(); sVK[e] = Ar::zero(); }
 #pragma unroll
-        for (int e = 0; e < 9; ++e) sVX[e] = 0.0;
+        for (int e = 0; e < 9; ++e) sVX[e] = Ar::zero();
         for (int k = cam_ptr[i] + lane; k < cam_ptr[i + 1]; k += 32) {
             int o = cam_perm[k];
             int j = obs[o].pt;
-            double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
             const double* vo = V + 27 * (int64_t)o;   // V = W A^-1 of this observation (vmat_kernel)
+            if constexpr (std::is_same<T, double>::value) {
+                double X0 = pts[3 * j], X1 = pts[3 * j + 1], X2 = pts[3 * j + 2];
 #pragma unroll
-            for (int p = 0; p < 9; ++p) {
-                const double v0 = vo[3 * p], v1 = vo[3 * p + 1], v2 = vo[3 * p + 2];
-                sV[3 * p] += v0; sV[3 * p + 1] += v1; sV[3 * p + 2] += v2;
-                sVX[p] += v0 * X0 + v1 * X1 + v2 * X2;
-                // V [X]x, [X]x = [[0,-X2,X1],[X2,0,-X0],[-X1,X0,0]]
-                sVK[3 * p] += v1 * X2 - v2 * X1;
-                sVK[3 * p + 1] += -v0 * X2 + v2 * X0;
-                sVK[3 * p + 2] += v0 * X1 - v1 * X0;
+                for (int p = 0; p < 9; ++p) {
+                    const double v0 = vo[3 * p], v1 = vo[3 * p + 1], v2 = vo[3 * p + 2];
+                    sV[3 * p] += v0; sV[3 * p + 1] += v1; sV[3 * p + 2] += v2;
+                    sVX[p] += v0 * X0 + v1 * X1 + v2 * X2;
+                    // V [X]x, [X]x = [[0,-X2,X1],[X2,0,-X0],[-X1,X0,0]]
+                    sVK[3 * p] += v1 * X2 - v2 * X1;
+                    sVK[3 * p + 1] += -v0 * X2 + v2 * X0;
+                    sVK[3 * p + 2] += v0 * X1 - v1 * X0;
+                }
+            } else {
+                const dsf X0 = ds_from_double(pts[3 * j]), X1 = ds_from_double(pts[3 * j + 1]),
+                          X2 = ds_from_double(pts[3 * j + 2]);
+                const dsf nX0 = ds_neg(X0), nX1 = ds_neg(X1), nX2 = ds_neg(X2);
+#pragma unroll
+                for (int p = 0; p < 9; ++p) {
+                    const dsf v0 = ds_from_double(vo[3 * p]), v1 = ds_from_double(vo[3 * p + 1]),
+                              v2 = ds_from_double(vo[3 * p + 2]);
+                    sV[3 * p] = ds_add(sV[3 * p], v0);
+                    sV[3 * p + 1] = ds_add(sV[3 * p + 1], v1);
+                    sV[3 * p + 2] = ds_add(sV[3 * p + 2], v2);
+                    sVX[p] = ds_fma(ds_fma(ds_fma(sVX[p], v0, X0), v1, X1), v2, X2);
+                    sVK[3 * p] = ds_fma(ds_fma(sVK[3 * p], v1, X2), v2, nX1);
+                    sVK[3 * p + 1] = ds_fma(ds_fma(sVK[3 * p + 1], v0, nX2), v2, X0);
+                    sVK[3 * p + 2] = ds_fma(ds_fma(sVK[3 * p + 2], v0, X1), v1, nX0);
+                }
             }
         }
         double* g = Gp + 63 * i;
@@ -515,11 +596,11 @@ cam_schur_kernel(int64_t n, const int* __restrict__ cam_ptr, const int* __restri
         for (int p = 0; p < 9; ++p) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                double a = warp_sum(sV[3 * p + q]);
-                double b = warp_sum(sVK[3 * p + q]);
+                double a = Ar::value(Ar::sum(sV[3 * p + q]));
+                double b = Ar::value(Ar::sum(sVK[3 * p + q]));
                 if (lane == 0) { g[7 * p + q] = -a; g[7 * p + 3 + q] = b; }
             }
-            double c = warp_sum(sVX[p]);
+            double c = Ar::value(Ar::sum(sVX[p]));
             if (lane == 0) g[7 * p + 6] = -c;
         }
     }
@@ -717,13 +798,20 @@ void launch_point_info(Ctx& c) {
 }
 
 void launch_cam_info(Ctx& c) {
-    cam_info_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_J, c.d_camprep, c.sigma, c.d_obscov, c.d_U);
+    if (c.opt.precision == CCOV_PREC_MIXED)
+        cam_info_kernel<dsf><<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+            c.n, c.d_cam_ptr, c.d_cam_perm, c.d_J, c.d_camprep, c.sigma, c.d_obscov, c.d_U);
+    else
+        cam_info_kernel<double><<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+            c.n, c.d_cam_ptr, c.d_cam_perm, c.d_J, c.d_camprep, c.sigma, c.d_obscov, c.d_U);
     CCOV_LAUNCH_CHECK(c);
 }
 
 void launch_schur(Ctx& c) {
-    vmat_kernel<<<(int)((c.t + 255) / 256), 256, 0, c.stream>>>(c.t, c.d_obs, c.d_W, c.d_Ainv, c.d_V);
+    if (c.opt.precision == CCOV_PREC_MIXED)
+        vmat_kernel<dsf><<<(int)((c.t + 255) / 256), 256, 0, c.stream>>>(c.t, c.d_obs, c.d_W, c.d_Ainv, c.d_V);
+    else
+        vmat_kernel<double><<<(int)((c.t + 255) / 256), 256, 0, c.stream>>>(c.t, c.d_obs, c.d_W, c.d_Ainv, c.d_V);
     CCOV_LAUNCH_CHECK(c);
     if (c.opt.precision == CCOV_PREC_MIXED)
         schur_pairs_kernel<dsf><<<grid_for(c.npairs, kWarps), 32 * kWarps, 0, c.stream>>>(
@@ -740,8 +828,12 @@ void launch_schur(Ctx& c) {
     CCOV_LAUNCH_CHECK(c);
     w7_reduce_kernel<<<c.nscenes, 64, 0, c.stream>>>(c.d_w7part, c.d_W7, c.d_scene_wpo, c.w7_wps);
     CCOV_LAUNCH_CHECK(c);
-    cam_schur_kernel<<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
-        c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_V, c.d_Gp);
+    if (c.opt.precision == CCOV_PREC_MIXED)
+        cam_schur_kernel<dsf><<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+            c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_V, c.d_Gp);
+    else
+        cam_schur_kernel<double><<<grid_for(c.n, kWarps), 32 * kWarps, 0, c.stream>>>(
+            c.n, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pts, c.d_V, c.d_Gp);
     CCOV_LAUNCH_CHECK(c);
 }
 
