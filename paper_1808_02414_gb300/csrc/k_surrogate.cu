@@ -21,6 +21,7 @@
 // that such a screen serves.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -78,8 +79,10 @@ struct GemmP {
     bf16* out_n;          // RELU, DX: [a_rows x N]
     bf16* out_t;          // RELU, DX: [N x a_rows]
     const bf16* mask;     // DX: [a_rows x N], the activation the gradient passes through
-    float* out_f;         // OUT: row-major, ld N; DW: row-major [a_rows x N], accumulated
-    float* db;            // DX: column sums of the output
+    float* out_f;         // OUT: row-major, ld N; DW: this split's partial [a_rows x N] at
+                          // out_f + blockIdx.y a_rows N (summed in order afterwards)
+    float* db;            // DX: partial column sums of the output, row 4 blockIdx.x + quarter
+                          // of a [tiles 4 x N] array (summed in order afterwards)
     int* flag;
 };
 
@@ -101,6 +104,12 @@ __device__ __forceinline__ void unpack8(uint4 u, float* x) {
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(GemmP g) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const float s = warp_sum(v[j]);
-                            if (lane == 0) atomicAdd(g.db + c0 + j, s);
+                            if (lane == 0) g.db[(4 * (int64_t)blockIdx.x + quarter) * g.N + c0 + j] = s;
                         }
                     }
                 } else if (g.epi == EPI_OUT) {
@@ -220,8 +229,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(GemmP g) {
                     o[1] = make_float4(v[4] + g.bias[c0 + 4], v[5] + g.bias[c0 + 5], v[6] + g.bias[c0 + 6],
                                        v[7] + g.bias[c0 + 7]);
                 } else {
+                    float* o = g.out_f + (int64_t)blockIdx.y * g.a_rows * g.N + grow * g.N + c0;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) atomicAdd(g.out_f + grow * g.N + c0 + j, v[j]);
+                    for (int j = 0; j < 8; ++j) o[j] = v[j];
                 }
             }
         }
@@ -266,8 +276,7 @@ __global__ void pack_kernel(const float* __restrict__ feat, const float* __restr
 // 45 outputs of real rows, zero elsewhere, as bf16 operands (and transpose);
 // db4 and the loss accumulate in fp32.  64 rows per block, thread = column.
 __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict__ T, int B, int Bp,
-                            bf16* __restrict__ Gn, bf16* __restrict__ Gt, float* __restrict__ db4,
-                            float* __restrict__ losses, const int* __restrict__ ctr) {
+                            bf16* __restrict__ Gn, bf16* __restrict__ Gt, float* __restrict__ part) {
     const int o = threadIdx.x;  // 128 threads
     const float inv = 2.f / ((float)B * (float)kOut);
     float acc_db = 0.f, acc_l = 0.f;
@@ -284,12 +293,32 @@ __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict
         Gt[kb_off(o, b, kOutP)] = h;
         acc_db += gv;
     }
-    if (o < kOut) atomicAdd(db4 + o, acc_db);
+    // this block's share: db4 partials [0, 128), the loss at 128
+    part[(int64_t)blockIdx.x * 129 + o] = o < kOut ? acc_db : 0.f;
     __shared__ float red[4];
     acc_l = warp_sum(acc_l);
     if ((o & 31) == 0) red[o >> 5] = acc_l;
     __syncthreads();
-    if (o == 0) atomicAdd(losses + (ctr ? ctr[1] : 0), (red[0] + red[1] + red[2] + red[3]) / ((float)B * (float)kOut));
+    if (o == 0) part[(int64_t)blockIdx.x * 129 + 128] = (red[0] + red[1] + red[2] + red[3]) / ((float)B * (float)kOut);
+}
+
+// out[e] = sum over z < nz, in order, of part[z * stride + e] (e < count).
+__global__ void sum_parts_kernel(const float* __restrict__ part, int nz, int64_t stride, int64_t count,
+                                 float* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    float v = 0.f;
+    for (int z = 0; z < nz; ++z) v += part[(int64_t)z * stride + e];
+    out[e] = v;
+}
+
+// The loss of the step (block shares summed in order) into losses[ctr[1]].
+__global__ void loss_sum_kernel(const float* __restrict__ part, int nb, float* __restrict__ losses,
+                                const int* __restrict__ ctr) {
+    if (threadIdx.x != 0) return;
+    float v = 0.f;
+    for (int b = 0; b < nb; ++b) v += part[(int64_t)b * 129 + 128];
+    losses[ctr ? ctr[1] : 0] = v;
 }
 
 struct Seg {
@@ -499,24 +528,50 @@ features_kernel(int64_t n, const double* __restrict__ U, const double* __restric
         f[46] = (float)(slog / cnt);
         f[47] = (float)(two / cnt);
         f[48] = (float)log((double)n);
-        double c[3];
-        camera_centre(camprep + kCamPrep * i, c);
-        for (int a = 0; a < 3; ++a) atomicAdd(csum + a, c[a]);
     }
     if (lane >= 17) feat[i * kIn + 32 + lane] = 0.f;  // [49, 64); 49 is written by centre_feature_kernel
 }
 
-__global__ void centre_spread_kernel(int64_t n, const double* __restrict__ camprep, double* __restrict__ csum) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double c[3];
-    camera_centre(camprep + kCamPrep * i, c);
-    double s = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        const double dv = c[a] - csum[a] / (double)n;
-        s += dv * dv;
+// The mean camera centre (csum[0..2], as sums) and the sum of squared
+// distances from it (csum[3]): one block of 1024 threads, each a strided
+// share of the cameras, reduced by a fixed tree, so that the features are the
+// same bits on every run.
+__global__ void __launch_bounds__(1024) centre_stats_kernel(int64_t n, const double* __restrict__ camprep,
+                                                           double* __restrict__ csum) {
+    __shared__ double red[4][32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = tid; i < n; i += 1024) {
+        double c[3];
+        camera_centre(camprep + kCamPrep * i, c);
+        for (int a = 0; a < 3; ++a) s[a] += c[a];
     }
-    atomicAdd(csum + 3, s);
+    for (int a = 0; a < 3; ++a) {
+        const double v = warp_sum_d(s[a]);
+        if (lane == 0) red[a][w] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double v = 0.0;
+        for (int k = 0; k < 32; ++k) v += red[tid][k];
+        csum[tid] = v;
+    }
+    __syncthreads();
+    const double m0 = csum[0] / (double)n, m1 = csum[1] / (double)n, m2 = csum[2] / (double)n;
+    double q = 0.0;
+    for (int64_t i = tid; i < n; i += 1024) {
+        double c[3];
+        camera_centre(camprep + kCamPrep * i, c);
+        q += (c[0] - m0) * (c[0] - m0) + (c[1] - m1) * (c[1] - m1) + (c[2] - m2) * (c[2] - m2);
+    }
+    q = warp_sum_d(q);
+    if (lane == 0) red[3][w] = q;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int k = 0; k < 32; ++k) v += red[3][k];
+        csum[3] = v;
+    }
 }
 
 __global__ void centre_feature_kernel(int64_t n, const double* __restrict__ camprep, const double* __restrict__ csum,
@@ -607,11 +662,10 @@ __global__ void predict_out_kernel(int64_t n, const float* __restrict__ Y, const
 void surr_launch_features(Ctx& c, float* feat, double* scale) {
     using namespace surr;
     double* csum = c.d_small + 100;  // 4 slots that nothing else uses
-    cudaMemsetAsync(csum, 0, 4 * sizeof(double), c.stream);
     features_kernel<<<(unsigned)((c.n + kFeatWarps - 1) / kFeatWarps), 32 * kFeatWarps, 0, c.stream>>>(
         c.n, c.d_U, c.d_W, c.d_Ainv, c.d_cam_ptr, c.d_cam_perm, c.d_obs, c.d_pt_ptr, c.d_camprep, csum, feat, scale,
         c.d_flag);
-    centre_spread_kernel<<<(unsigned)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_camprep, csum);
+    centre_stats_kernel<<<1, 1024, 0, c.stream>>>(c.n, c.d_camprep, csum);
     centre_feature_kernel<<<(unsigned)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_camprep, csum, feat);
     c.launches += 3;
 }
@@ -635,6 +689,7 @@ struct ccov_surrogate {
     bf16 *g_n[5] = {}, *g_t[5] = {};   // gradients g1..g4 (index = layer)
     float *Y = nullptr, *T = nullptr;
     float* losses = nullptr;           // device, per in-call step
+    float* part = nullptr;             // partial sums of a step, summed in order (kPartFloats)
     int64_t losses_cap = 0;
     int* ctr = nullptr;                // [0] Adam steps, [1] in-call step
     unsigned* done = nullptr;
@@ -743,7 +798,18 @@ void gemm(ccov_surrogate* s, const bf16* A, int64_t a_rows, const bf16* B, int N
     }
     g.chunks_per_split = (chunks + splits - 1) / splits;
     splits = (chunks + g.chunks_per_split - 1) / g.chunks_per_split;
+    // gradient sums go through partials in s->part, summed in a fixed order
+    // below (bit-for-bit repeatable training), not through atomics
+    if (epi == EPI_DW) g.out_f = s->part;
+    if (epi == EPI_DX) g.db = s->part;
     mlp_gemm_kernel<<<dim3((unsigned)tiles, (unsigned)splits), kGemmThreads, kGemmSmem, s->stream>>>(g);
+    if (epi == EPI_DW) {
+        const int64_t count = a_rows * N;
+        sum_parts_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s->stream>>>(s->part, splits, count, count,
+                                                                                 out_f);
+    } else if (epi == EPI_DX) {
+        sum_parts_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s->stream>>>(s->part, 4 * tiles, N, N, db);
+    }
 }
 
 // One training step's launches (no host synchronisation): pack, forward,
@@ -759,8 +825,9 @@ void enqueue_step(ccov_surrogate* s, const float* feat, const float* targ, int64
     gemm(s, s->a_n[1], Bp, s->wb[1], 256, 256, EPI_RELU, s->p + kOffB2, s->a_n[2], s->a_t[2], nullptr, nullptr, nullptr);
     gemm(s, s->a_n[2], Bp, s->wb[2], 256, 256, EPI_RELU, s->p + kOffB3, s->a_n[3], s->a_t[3], nullptr, nullptr, nullptr);
     gemm(s, s->a_n[3], Bp, s->wb[3], kOutP, 256, EPI_OUT, s->p + kOffB4, nullptr, nullptr, nullptr, s->Y, nullptr);
-    loss_kernel<<<(unsigned)(Bp / 64), 128, 0, s->stream>>>(s->Y, s->T, B, (int)Bp, s->g_n[4], s->g_t[4],
-                                                            s->grad + kOffB4, s->losses, s->ctr);
+    loss_kernel<<<(unsigned)(Bp / 64), 128, 0, s->stream>>>(s->Y, s->T, B, (int)Bp, s->g_n[4], s->g_t[4], s->part);
+    sum_parts_kernel<<<1, 128, 0, s->stream>>>(s->part, (int)(Bp / 64), 129, kOut, s->grad + kOffB4);
+    loss_sum_kernel<<<1, 32, 0, s->stream>>>(s->part, (int)(Bp / 64), s->losses, s->ctr);
     // backward: dW_l = g_l^T a_{l-1}; g_{l-1} = (g_l W_l) * [a_{l-1} > 0]
     gemm(s, s->g_t[4], kOutP, s->a_t[3], 256, (int)Bp, EPI_DW, nullptr, nullptr, nullptr, nullptr, s->grad + kOffW4, nullptr);
     gemm(s, s->g_n[4], Bp, s->wt[3], 256, kOutP, EPI_DX, nullptr, s->g_n[3], s->g_t[3], s->a_n[3], nullptr, s->grad + kOffB3);
@@ -856,6 +923,15 @@ ccov_status ccov_surrogate_create(const float* params, int64_t max_batch, void* 
         SCK(salloc(s, &s->g_t[l], Bp * width[l]), "alloc");
     }
     SCK(salloc(s, &s->Y, Bp * kOutP), "alloc");
+    {
+        // the largest set of partial sums of a step: the weight gradients'
+        // splits (at most 64 x 128 x 256 or 32 x 256 x 256), the bias
+        // gradients' row quarters, the loss blocks
+        int64_t np = (int64_t)1 << 21;
+        np = std::max<int64_t>(np, Bp / 128 * 4 * 256);
+        np = std::max<int64_t>(np, Bp / 64 * 129);
+        SCK(salloc(s, &s->part, np), "alloc");
+    }
     SCK(salloc(s, &s->T, Bp * kOut), "alloc");
     SCK(salloc(s, &s->ctr, 2), "alloc");
     SCK(salloc(s, &s->done, 1), "alloc");

@@ -116,6 +116,29 @@ def test_graph_training_equals_step_by_step():
         np.testing.assert_allclose(a.params(), b.params(), rtol=1e-4, atol=1e-6)
 
 
+def test_features_and_training_repeat_bit_for_bit():
+    """Every sum of the features and of a training step runs in a fixed order
+    (partial sums reduced in order, no atomics), so the same inputs give the
+    same bits: features twice, and two trainings from the same start."""
+    sc = synth.shell_scene(n=60, m=3000, seed=21)
+    f1, _, _ = _scene_data(sc)
+    f2, _, _ = _scene_data(sc)
+    assert torch.equal(f1, f2)
+    rng = np.random.default_rng(7)
+    n, B, steps, lr = 900, 256, 6, 2e-3
+    F = torch.from_numpy(rng.normal(size=(n, 64)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(n, 45)).astype(np.float32)).cuda()
+    idx = torch.from_numpy(synth.minibatch_indices(n, B, steps, seed=4)).cuda()
+    params = _params(8)
+    runs = []
+    for _ in range(2):
+        with surrogate.Surrogate(params, max_batch=B) as sm:
+            losses = np.array(sm.train(F, T, idx, lr))
+            runs.append((losses, sm.params().copy()))
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+
+
 def test_prediction_matches_oracle():
     sc = synth.shell_scene(n=50, m=2500, seed=32)
     f, lz, _ = _scene_data(sc)
