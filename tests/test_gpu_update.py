@@ -59,6 +59,17 @@ def test_update_several_tiles_against_the_oracle(prec, tol):
     assert_blocks_close(got, covariance.camera_covariance(merged), tol, "update")
 
 
+def test_update_many_observations_on_a_small_scene():
+    """2k columns wider than the scene's padded N (200 observations on 30
+    cameras: 405 columns, Np = 384): the mixed form then takes Y = Z'^-1 V in
+    double-single arithmetic and the small products in FP64 instead of the
+    tensor-core panels, whose operand buffers hold Np rows."""
+    sc = synth.shell_scene(n=30, m=2000, seed=12)
+    merged, added = synth.added_observations(sc, 200, seed=5)
+    _, got, _ = _update(sc, added, precision=ccov.CCOV_PREC_MIXED)
+    assert_blocks_close(got, covariance.camera_covariance(merged), MIXED_TOL, "update")
+
+
 def test_update_anisotropic_against_the_oracle():
     sc = _aniso(synth.shell_scene(n=60, m=4000, seed=9))
     merged, added = synth.added_observations(sc, 120, seed=3)
