@@ -17,9 +17,20 @@ scene (value = cameras / s of ccov_information + features + prediction).
 
 `--workload batch256` times the batched form instead: 256 independent
 sub-reconstructions (n ~ U{10..300} cameras, 100 points per camera, track
-length 1 + Geometric(0.2)), all four steps of every scene recorded once as a
-CUDA graph and replayed, one replay per step; `value` = cameras / s over the
-whole batch.
+length 1 + Geometric(0.2)), all four steps of every scene as grouped launches
+(one per step for all scenes) recorded once as a CUDA graph and replayed, one
+replay per step; `value` = cameras / s over the whole batch.
+
+`--workload subrecon` times the Sec. 5 pipeline on a 1000-camera scene with
+visibility locality (sub-reconstructions of 100 view-graph neighbours, three
+decompositions, minimum-trace merge), with the error against the full scene.
+
+`--workload update` times the covariance update after 200 added observations
+(Sec. 5, Woodbury) on the 4000-camera scene, against a new step (d) of the
+merged scene, and the update's time for 20, 50 and 800 added observations.
+
+`--workload shell1k` (or any scene name of synth.workload) runs the default
+step on that scene.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
 instead, on a bounded sub-scene of the same workload.
