@@ -223,8 +223,15 @@ def run_reference(args):
         run_reference_batch(args)
         return
     from paper_1808_02414_gb300 import synth
-    # the surrogate's reference is the exact method on its evaluation scene
-    scene = synth.workload("shell4k" if args.workload == "surrogate" else args.workload)
+    # the surrogate's and the update's reference is the exact method on the
+    # scene they run on (for the update: the covariance from scratch); that of
+    # the sub-reconstructions, the exact method on their scene
+    if args.workload in ("surrogate", "update"):
+        scene = synth.workload("shell4k")
+    elif args.workload == "subrecon":
+        scene = synth.local_scene(n=1000, m=100_000, seed=3)
+    else:
+        scene = synth.workload(args.workload)
     times = []
     sub = None
     for i in range(args.warmup + args.steps):
