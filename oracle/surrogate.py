@@ -29,6 +29,23 @@ Model, per camera i of a scene:
           output in the target's form, so that the network learns how far the
           whole scene moves the camera's covariance away from Z_ii^-1.
 
+Gauge term of the base.  Z_ii^-1 holds every other camera fixed, which also
+pins the datum; in the similarity gauge of Sec. 4.1 the camera moves with
+the datum as well.  On the exact blocks of the shell scenes the difference
+Sigma_i - Z_ii^-1 lies almost entirely (over 99% of its whitened squared
+norm) in the span of the camera's nullspace rows H_i (the 9 x 7 rows of H
+for camera i, Sec. 4.1), and one 7 x 7 matrix per scene explains nearly all
+of that part.  In the scene's own metric that matrix hardly
+depends on the scene's size, so one learned M serves all sizes:
+  AH      sum_i H_i^T Z_ii H_i (7 x 7), L_c the Cholesky factor of AH^-1
+  Q_i     H_i L_c (9 x 7), so that sum_i Q_i^T Z_ii Q_i = I
+  B_i     Z_ii^-1 + Q_i M Q_i^T, the base covariance (M = 0: Z_ii^-1)
+  T_i     the Cholesky factor of B_i^-1 (M = 0: L_z)
+  M       symmetric 7 x 7, least squares over the training cameras of
+          |L_z^T (Sigma_i - Z_ii^-1) L_z - L_z^T Q_i M Q_i^T L_z|_F^2.
+Targets and outputs are then taken with T_i in place of L_z: the network
+learns the remainder of the scene's effect beyond the gauge term.
+
 Network: 64 -> 256 -> 256 -> 256 -> 45, ReLU after the three hidden layers,
 inputs and targets standardised with per-column mean and standard deviation
 of the training set (a deviation below 1e-6 is replaced by 1).  Loss: mean
@@ -43,7 +60,10 @@ the output-side gradients fed to the two backward products.  Biases, the
 output, the loss and every sum stay in float64 here (fp32 on the GPU).  With
 `quantize` off the functions are the exact float64 gradient of the loss.
 
-Parity: forward/backward pinned by finite differences and by torch autograd
+Parity: gauge rows pinned by their normalisation (sum_i Q_i^T Z_ii Q_i = I)
+and by their span; the base factor by M = 0 (T = L_z) and by the push-through
+form of B^-1; the gauge fit by recovery of a planted M and by the optimality
+condition of least squares; forward/backward pinned by finite differences and by torch autograd
 in float64; Adam by torch.optim.Adam; bf16 rounding by torch's conversion;
 features by the dense Schur complement of `covariance` and by brute-force
 counting; targets by the round trip back to Sigma and by the closed form
@@ -160,6 +180,50 @@ def covariance_from_output(t: np.ndarray, Lz: np.ndarray) -> np.ndarray:
     L[:, _IL[0], _IL[1]] = t[:, 9:]
     Li = np.linalg.inv(Lz)
     return Li.transpose(0, 2, 1) @ (L @ L.transpose(0, 2, 1)) @ Li
+
+
+# ---------------------------------------------------------------------------
+# Gauge term of the base covariance
+def gauge_rows(Lz: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """Q_i = H_i L_c (n, 9, 7) for one scene: Lz (n, 9, 9) the factors of the
+    blocks Z_ii, H (n, 9, 7) the cameras' nullspace rows, L_c the Cholesky
+    factor of (sum_i H_i^T Z_ii H_i)^-1."""
+    Zd = Lz @ Lz.transpose(0, 2, 1)
+    AH = np.einsum("iak,iab,ibl->kl", H, Zd, H)
+    Lc = np.linalg.cholesky(np.linalg.inv(AH))
+    return H @ Lc
+
+
+def base_factor(Lz: np.ndarray, Q: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """T_i = chol((Z_ii^-1 + Q_i M Q_i^T)^-1), (n, 9, 9) lower triangular."""
+    Zinv = np.linalg.inv(Lz @ Lz.transpose(0, 2, 1))
+    B = Zinv + Q @ M @ Q.transpose(0, 2, 1)
+    return np.linalg.cholesky(np.linalg.inv(B))
+
+
+def sym_basis() -> np.ndarray:
+    """The 28 symmetric 7 x 7 matrices E_kl (k <= l, row by row): ones at
+    (k, l) and (l, k).  M = sum over k <= l of M_kl E_kl."""
+    out = []
+    for k in range(7):
+        for l in range(k, 7):
+            E = np.zeros((7, 7))
+            E[k, l] = E[l, k] = 1.0
+            out.append(E)
+    return np.stack(out)
+
+
+def fit_gauge(Lz: np.ndarray, Q: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """The symmetric M that minimises, over the given cameras (of any number
+    of scenes, each Q from its own scene),
+        sum_i |L_z^T (Sigma_i - Z_ii^-1) L_z - L_z^T Q_i M Q_i^T L_z|_F^2
+    (L_z^T Z_ii^-1 L_z = I): linear least squares in the 28 entries M_kl,
+    k <= l."""
+    Qt = Lz.transpose(0, 2, 1) @ Q
+    E = Lz.transpose(0, 2, 1) @ sigma @ Lz - np.eye(9)
+    A = np.stack([Qt @ Eb @ Qt.transpose(0, 2, 1) for Eb in sym_basis()], axis=-1)
+    m = np.linalg.lstsq(A.reshape(-1, 28), E.reshape(-1), rcond=None)[0]
+    return np.einsum("p,pkl->kl", m, sym_basis())
 
 
 def gaussian_kl(pred: np.ndarray, true: np.ndarray) -> np.ndarray:

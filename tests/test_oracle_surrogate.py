@@ -192,3 +192,100 @@ def test_normalization():
     np.testing.assert_allclose(z.mean(axis=0), 0, atol=1e-12)
     np.testing.assert_allclose(z[:, [0, 1, 3]].std(axis=0), 1, rtol=1e-12)
     assert sd[2] == 1.0 and np.all(z[:, 2] == 0)
+
+
+# ---------------------------------------------------------------------------
+# Gauge term of the base covariance
+def _gauge_inputs(n=14, m=600, seed=21):
+    from oracle import nullspace
+    sc = synth.shell_scene(n=n, m=m, seed=seed)
+    _, Lz = S.features(sc)
+    H = nullspace.camera_rows_closed_form(sc).reshape(n, 9, 7)
+    return sc, Lz, H
+
+
+def _spd(k, seed):
+    A = np.random.default_rng(seed).normal(size=(k, k))
+    return A @ A.T + k * np.eye(k)
+
+
+def test_gauge_rows_are_normalised_and_span_the_nullspace_rows():
+    sc, Lz, H = _gauge_inputs()
+    Q = S.gauge_rows(Lz, H)
+    Z = S.diagonal_blocks(sc)                 # from the information blocks, not from Lz
+    np.testing.assert_allclose(np.einsum("iak,iab,ibl->kl", Q, Z, Q), np.eye(7), atol=1e-10)
+    # Q_i = H_i C for one 7 x 7 C shared by every camera
+    C = np.linalg.lstsq(H.reshape(-1, 7), Q.reshape(-1, 7), rcond=None)[0]
+    np.testing.assert_allclose(H @ C, Q, rtol=1e-10, atol=1e-12 * np.abs(Q).max())
+
+
+def test_base_factor_against_the_push_through_form():
+    sc, Lz, H = _gauge_inputs()
+    Q = S.gauge_rows(Lz, H)
+    np.testing.assert_allclose(S.base_factor(Lz, Q, np.zeros((7, 7))), Lz, rtol=1e-9,
+                               atol=1e-12 * np.abs(Lz).max())
+    M = 0.05 * _spd(7, 3)
+    T = S.base_factor(Lz, Q, M)
+    assert np.all(np.triu(T, 1) == 0) and np.all(np.einsum("ikk->ik", T) > 0)
+    # (Z^-1 + Q M Q^T)^-1 = Z - Z Q M (I + Q^T Z Q M)^-1 Q^T Z
+    Z = Lz @ Lz.transpose(0, 2, 1)
+    ZQ = Z @ Q
+    inner = np.linalg.inv(np.eye(7) + Q.transpose(0, 2, 1) @ ZQ @ M)
+    want = Z - ZQ @ M @ inner @ ZQ.transpose(0, 2, 1)
+    got = T @ T.transpose(0, 2, 1)
+    err = np.linalg.norm(got - want, axis=(1, 2)) / np.linalg.norm(want, axis=(1, 2))
+    assert err.max() < 1e-9
+
+
+def test_fit_gauge_recovers_a_planted_matrix():
+    parts = []
+    for seed, n in ((21, 14), (22, 20)):
+        sc, Lz, H = _gauge_inputs(n=n, m=40 * n, seed=seed)
+        parts.append((Lz, S.gauge_rows(Lz, H)))
+    Mstar = _spd(7, 5) / 7.0
+    Lz = np.concatenate([p[0] for p in parts])
+    Q = np.concatenate([p[1] for p in parts])
+    sig = np.linalg.inv(Lz @ Lz.transpose(0, 2, 1)) + Q @ Mstar @ Q.transpose(0, 2, 1)
+    M = S.fit_gauge(Lz, Q, sig)
+    np.testing.assert_allclose(M, M.T, atol=0)
+    np.testing.assert_allclose(M, Mstar, rtol=1e-8, atol=1e-9 * np.abs(Mstar).max())
+
+
+def test_fit_gauge_meets_the_least_squares_optimality_condition():
+    sc, Lz, H = _gauge_inputs(n=16, m=900, seed=23)
+    sig = covariance.camera_covariance(sc)
+    Q = S.gauge_rows(Lz, H)
+    M = S.fit_gauge(Lz, Q, sig)
+    # residual orthogonal to every basis image, by explicit sums per camera
+    grad = np.zeros(28)
+    for i in range(sc.n):
+        Qt = Lz[i].T @ Q[i]
+        R = Lz[i].T @ sig[i] @ Lz[i] - np.eye(9) - Qt @ M @ Qt.T
+        for p, Eb in enumerate(S.sym_basis()):
+            grad[p] += np.sum(R * (Qt @ Eb @ Qt.T))
+    scale = np.abs(Lz.transpose(0, 2, 1) @ sig @ Lz).max()
+    assert np.abs(grad).max() < 1e-9 * scale * sc.n
+
+
+def test_gauge_term_explains_the_exact_blocks():
+    """The premise of the base: on exact blocks, Sigma_i - Z_ii^-1 lies almost
+    entirely in the span of H_i (measured: 4.5-6% of its whitened Frobenius
+    norm outside it on 60- and 200-camera shells, so over 99% of the squared
+    norm inside), and one M per scene takes the Gaussian KL far below that of
+    Z_ii^-1."""
+    sc, Lz, H = _gauge_inputs(n=60, m=6000, seed=24)
+    sig = covariance.camera_covariance(sc)
+    Zinv = np.linalg.inv(Lz @ Lz.transpose(0, 2, 1))
+    Ew = Lz.transpose(0, 2, 1) @ (sig - Zinv) @ Lz
+    Hw = Lz.transpose(0, 2, 1) @ H
+    for i in range(sc.n):
+        U, s, _ = np.linalg.svd(Hw[i], full_matrices=False)
+        U = U[:, s > 1e-12 * s[0]]
+        P = U @ U.T
+        assert np.linalg.norm(Ew[i] - P @ Ew[i] @ P) <= 0.1 * np.linalg.norm(Ew[i])
+    Q = S.gauge_rows(Lz, H)
+    T = S.base_factor(Lz, Q, S.fit_gauge(Lz, Q, sig))
+    Ti = np.linalg.inv(T)
+    kl_base = S.gaussian_kl(Ti.transpose(0, 2, 1) @ Ti, sig)
+    kl_local = S.gaussian_kl(Zinv, sig)
+    assert np.median(kl_base) < 0.02 * np.median(kl_local)
