@@ -613,9 +613,10 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
-# kernels of one surrogate step: cam_prep, point_info, cam_info (ccov_information);
-# features, centre spread, centre feature; pack, 4 GEMMs, output (prediction)
-SURR_STEP_LAUNCHES = 12
+# kernels of one surrogate step: cam_prep, obs_info, point_ainv, cam_info
+# (ccov_information); features, centre spread, centre feature; nullspace rows;
+# gauge sums, L_c, gauge rows; base factor; pack, 4 GEMMs, output (prediction)
+SURR_STEP_LAUNCHES = 18
 
 
 def _training_scene(spec):
@@ -624,11 +625,11 @@ def _training_scene(spec):
 
 
 def surrogate_training_set(n_scenes: int, n_heldout: int = 30, group: int = 32):
-    """Features and targets of every camera of the training scenes, on the
-    device, plus (features, L_z, exact blocks) of `n_heldout` further scenes
-    of the same distribution.  Scenes are drawn in worker processes (spawned,
-    so that no worker inherits a CUDA context) and solved exactly with the
-    FP64 path in batches of `group` contexts."""
+    """Per camera of the training scenes, on the device: features, L_z, gauge
+    rows Q and the exact blocks; the same for `n_heldout` further scenes of
+    the same distribution.  Scenes are drawn in worker processes (spawned, so
+    that no worker inherits a CUDA context) and solved exactly with the FP64
+    path in batches of `group` contexts."""
     import multiprocessing as mp
 
     import torch
@@ -636,7 +637,7 @@ def surrogate_training_set(n_scenes: int, n_heldout: int = 30, group: int = 32):
     from paper_1808_02414_gb300 import ccov, surrogate, synth
 
     specs = synth.training_scene_specs(n_scenes + n_heldout)
-    F, TG, HF, HL, HS = [], [], [], [], []
+    train, held = [], []
     procs = max(1, min(16, (os.cpu_count() or 2) - 1))
     with mp.get_context("spawn").Pool(procs) as pool:
         pending, seen = [], 0
@@ -645,28 +646,23 @@ def surrogate_training_set(n_scenes: int, n_heldout: int = 30, group: int = 32):
             seen += 1
             if len(pending) < group and seen not in (n_scenes, len(specs)):
                 continue
-            if seen <= n_scenes:
-                _solve_group(pending, F, TG, ccov, surrogate, torch)
-            else:
-                _solve_group(pending, HF, None, ccov, surrogate, torch, HL, HS)
+            _solve_group(pending, train if seen <= n_scenes else held, ccov, surrogate, torch)
             pending = []
-    held = (torch.cat(HF), torch.cat(HL).cpu().numpy(), torch.cat(HS).cpu().numpy()) if HF else None
-    return torch.cat(F), torch.cat(TG), held
+
+    def cat(parts):
+        return tuple(torch.cat(a) for a in zip(*parts)) if parts else None
+
+    return cat(train), cat(held)
 
 
-def _solve_group(scenes, F, TG, ccov, surrogate, torch, LZ=None, SG=None):
+def _solve_group(scenes, out, ccov, surrogate, torch):
     ctxs = [ccov.from_scene(sc) for sc in scenes]
     outs = [torch.empty((sc.n, 9, 9), dtype=torch.float64, device="cuda") for sc in scenes]
     try:
         ccov.ccov_batch_covariance(ctxs, outs)
         for c, o in zip(ctxs, outs):
             f, lz = surrogate.features(c)
-            F.append(f)
-            if TG is not None:
-                TG.append(surrogate.targets(lz, o))
-            if LZ is not None:
-                LZ.append(lz)
-                SG.append(o)
+            out.append((f, lz, surrogate.gauge_rows(c, lz), o))
     finally:
         for c in ctxs:
             c.close()
@@ -695,14 +691,23 @@ def _cov_from_target(t, Lz):
     return Li.transpose(0, 2, 1) @ (L @ L.transpose(0, 2, 1)) @ Li
 
 
-def _surrogate_accuracy(sm, f, L, truth):
+def _surrogate_accuracy(sm, f, lz, q, truth):
+    """Median and p90 Gaussian KL against the exact blocks of the network's
+    prediction, of the base with the fitted gauge term alone, of Z_ii^-1 and
+    of a constant correction around the base."""
     import numpy as np
-    pred = sm.predict(f, __import__("torch").from_numpy(L).cuda()).cpu().numpy()
+    T = sm.apply_gauge(lz, q)
+    pred = sm.predict(f, T).cpu().numpy()
+    Tn, L = T.cpu().numpy(), lz.cpu().numpy()
     mu_t = sm.normalization()[128:173].astype(np.float64)
     n = L.shape[0]
+    zero = np.zeros((n, 45))
+    f48 = f[:, 48].cpu().numpy().astype(np.float64)
+    hs = np.where(f48 > 0, f48, 1.0)[:, None]        # the output head's size scale
     kl = {"surrogate": _gaussian_kl(pred, truth),
-          "local_block_inverse": _gaussian_kl(_cov_from_target(np.zeros((n, 45)), L), truth),
-          "constant_correction": _gaussian_kl(_cov_from_target(np.tile(mu_t, (n, 1)), L), truth)}
+          "gauge_base": _gaussian_kl(_cov_from_target(zero, Tn), truth),
+          "local_block_inverse": _gaussian_kl(_cov_from_target(zero, L), truth),
+          "constant_correction": _gaussian_kl(_cov_from_target(hs * mu_t, Tn), truth)}
     out = {k: {"median_kl": float(np.median(v)), "p90_kl": float(np.percentile(v, 90))} for k, v in kl.items()}
     out["surrogate"]["median_rel_fro"] = float(np.median(
         np.linalg.norm(pred - truth, axis=(1, 2)) / np.linalg.norm(truth, axis=(1, 2))))
@@ -722,22 +727,30 @@ def run_surrogate(args):
     stream = torch.cuda.current_stream(dev)
 
     t0 = time.perf_counter()
-    F, TG, held = surrogate_training_set(args.surr_scenes)
+    (F, LZ, QG, SG), held = surrogate_training_set(args.surr_scenes)
     data_s = time.perf_counter() - t0
     N, B = int(F.shape[0]), args.surr_batch
     steps = max(1, args.surr_epochs * N // B)
     idx = torch.from_numpy(synth.minibatch_indices(N, B, steps, seed=11)).to(dev)
     sm = surrogate.Surrogate(synth.surrogate_init(0), max_batch=B, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sm.fit_gauge(LZ, QG, SG)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gauge_fit_ms = e0.elapsed_time(e1)
+    TG = surrogate.targets(sm.apply_gauge(LZ, QG), SG)
+    del LZ, QG, SG
     sm.fit_normalization(F, TG)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     losses = sm.train(F, TG, idx, 1e-3)
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
     ms_train_step = train_ms / steps
-    accuracy = {"heldout_scenes_50_500_cams": _surrogate_accuracy(sm, *held)}
+    accuracy = {"heldout_scenes_50_500_cams": _surrogate_accuracy(sm, *held[:3], held[3].cpu().numpy())}
 
     # evaluation on the 4000-camera scene: exact blocks from the mixed path
     scene = synth.workload("shell4k")
@@ -753,16 +766,18 @@ def run_surrogate(args):
     def step():
         ctx.ccov_information()
         f, lz = surrogate.features(ctx)
-        return sm.predict(f, lz), lz
+        ctx.ccov_nullspace()
+        q = surrogate.gauge_rows(ctx, lz)
+        return sm.predict(f, sm.apply_gauge(lz, q)), f, lz, q
 
     for _ in range(args.warmup):
-        pred, lz = step()
+        pred, f, lz, q = step()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
     e0.record(stream)
     for _ in range(args.steps):
-        pred, lz = step()
+        pred, f, lz, q = step()
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -779,14 +794,15 @@ def run_surrogate(args):
     e0.record(stream)
     ctx_h.ccov_load(hc, hp, ho)
     ctx_h.ccov_information()
-    f, l2 = surrogate.features(ctx_h)
-    hout.copy_(sm.predict(f, l2))
+    f2, l2 = surrogate.features(ctx_h)
+    ctx_h.ccov_nullspace()
+    hout.copy_(sm.predict(f2, sm.apply_gauge(l2, surrogate.gauge_rows(ctx_h, l2))))
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
     ctx_h.close()
 
-    accuracy["shell4k_4000_cams"] = _surrogate_accuracy(sm, f, lz.cpu().numpy(), exact.cpu().numpy())
+    accuracy["shell4k_4000_cams"] = _surrogate_accuracy(sm, f, lz, q, exact.cpu().numpy())
     ctx.close()
 
     # executed tensor flops of one training step (padded widths 128/256/256/256/128)
@@ -800,7 +816,8 @@ def run_surrogate(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "surrogate", "train_scenes": args.surr_scenes, "train_samples": N,
                        "batch": B, "train_steps": steps, "eval": "shell4k (4000 cameras)",
-                       "step": "ccov_information + surrogate features + prediction",
+                       "step": "ccov_information + surrogate features + ccov_nullspace + gauge rows "
+                               "+ base factor + prediction",
                        "l2": "eval inputs 90 MB + blocks, working set > L2 in the information step"},
             "clocks": clk,
             "e2e": {"value": scene.n / (ms_e2e / 1e3), "unit": UNIT,
@@ -812,17 +829,18 @@ def run_surrogate(args):
                          "kernel": "mlp_gemm (training step, 11 GEMMs + pack/loss/Adam, one graph node each)",
                          "peak_source": f"bf16 burst ({src})",
                          "note": "executed GEMM flops per training step / whole step time: launch-bound"},
-            "training": {"data_seconds": data_s, "ms_per_step": ms_train_step,
+            "training": {"data_seconds": data_s, "gauge_fit_ms": gauge_fit_ms, "ms_per_step": ms_train_step,
                          "samples_per_s": B / (ms_train_step / 1e3), "loss_first": float(losses[:10].mean()),
                          "loss_last": float(losses[-50:].mean())},
             "accuracy_vs_exact": accuracy}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import surrogate as S
+        from oracle import nullspace as NS, surrogate as S
         sub = synth.subscene(scene, np.arange(300))
         t0 = time.perf_counter()
         f_o, lz_o = S.features(sub)
+        q_o = S.gauge_rows(lz_o, NS.camera_rows_closed_form(sub).reshape(sub.n, 9, 7))
         norm = sm.normalization().astype(np.float64)
-        S.predict(S.unpack(sm.params().astype(np.float64)), f_o, lz_o,
+        S.predict(S.unpack(sm.params().astype(np.float64)), f_o, S.base_factor(lz_o, q_o, sm.gauge()),
                   (norm[:64], norm[64:128], norm[128:173], norm[173:]))
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": sub.n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

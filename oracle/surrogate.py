@@ -19,7 +19,10 @@ Model, per camera i of a scene:
           45        log of the camera's observation count
           46        mean over its observations of log L_j (L_j = track length)
           47        fraction of its observations with L_j = 2
-          48        log n (cameras in the scene)
+          48        10 / sqrt(n), n the cameras in the scene (around the base
+                    with the gauge term below, what remains shrinks about as
+                    n^-1/2, so a network that is linear in this feature
+                    beyond the training sizes follows it to larger scenes)
           49        |c_i - c_mean| / rms radius of the camera centres c = -R^T t
           [50, 64)  zero
   target  (45 values): the Cholesky factor L of the whitened exact block
@@ -48,7 +51,16 @@ learns the remainder of the scene's effect beyond the gauge term.
 
 Network: 64 -> 256 -> 256 -> 256 -> 45, ReLU after the three hidden layers,
 inputs and targets standardised with per-column mean and standard deviation
-of the training set (a deviation below 1e-6 is replaced by 1).  Loss: mean
+of the training set (a deviation below 1e-6 is replaced by 1).  The output
+head carries a size scale s = feature 48 (10 / sqrt(n); 1 if that feature
+is not positive): the network learns the standardised t / s, and its output
+y stands for t = s (mu_t + sd_t y), the target normalisation being taken on
+t / s.  Around the base with the gauge term the remainder shrinks about as
+n^-1/2 (60-1000 cameras), so t / s keeps its size from scene to scene and
+the network need not extrapolate in the scene's size.  Feature 48 sets only
+that scale: its standardised input column is zero (every other feature has
+the same distribution at 60 and at 2000 cameras, so no input leaves the
+training range on larger scenes).  Loss: mean
 squared error over the 45 standardised outputs and the batch.  Optimiser:
 Adam (Kingma and Ba, 2015) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8.
 
@@ -159,7 +171,7 @@ def features(scene):
     f[:, :36] = C[:, _IU[0], _IU[1]]
     f[:, 36:45] = np.log(d)
     f[:, 45:48] = degree_stats(scene)
-    f[:, 48] = np.log(scene.n)
+    f[:, 48] = 10.0 / np.sqrt(scene.n)
     f[:, 49] = centre_distance(scene)
     return f, np.linalg.cholesky(Z)
 
@@ -292,8 +304,21 @@ def adam(params, grads, m, v, step, lr):
     return out_p, out_m, out_v
 
 
+def network_input(f: np.ndarray, mu_f: np.ndarray, sd_f: np.ndarray) -> np.ndarray:
+    """Standardised features with the size feature's column set to zero."""
+    x = (f - mu_f) / sd_f
+    x[:, 48] = 0.0
+    return x
+
+
+def head_scale(f: np.ndarray) -> np.ndarray:
+    """The output head's size scale per row of raw features f (n, 64)."""
+    return np.where(f[:, 48] > 0, f[:, 48], 1.0)
+
+
 def predict(params, f, Lz, norm, quantize=True):
-    """Sigma_hat for raw features f (n, 64) with normalisation (mu_f, sd_f, mu_t, sd_t)."""
+    """Sigma_hat for raw features f (n, 64) with normalisation (mu_f, sd_f, mu_t, sd_t)
+    and whitening factors Lz (L_z, or the base factors T)."""
     mu_f, sd_f, mu_t, sd_t = norm
-    y, _ = forward(params, (f - mu_f) / sd_f, quantize)
-    return covariance_from_output(y * sd_t + mu_t, Lz)
+    y, _ = forward(params, network_input(f, mu_f, sd_f), quantize)
+    return covariance_from_output(head_scale(f)[:, None] * (y * sd_t + mu_t), Lz)

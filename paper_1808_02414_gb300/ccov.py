@@ -134,6 +134,11 @@ def load() -> C.CDLL:
         "ccov_surrogate_predict": ([P, P, P, I64, P], I),
         "ccov_surrogate_destroy": ([P], None),
         "ccov_surrogate_last_error": ([P], C.c_char_p),
+        "ccov_surrogate_gauge_rows": ([P, P, P], I),
+        "ccov_surrogate_set_gauge": ([P, P], I),
+        "ccov_surrogate_get_gauge": ([P, P], I),
+        "ccov_surrogate_fit_gauge": ([P, P, P, P, I64], I),
+        "ccov_surrogate_apply_gauge": ([P, P, P, I64, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

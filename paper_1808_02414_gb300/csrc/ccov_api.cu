@@ -54,7 +54,7 @@ void free_all(Ctx& c) {
     void* ptrs[] = {c.d_cams, c.d_pts, c.d_obs, c.d_obscov, c.d_pt_ptr, c.d_cam_ptr, c.d_cam_perm,
                     c.d_camprep, c.d_W, c.d_Ainv, c.d_U, c.d_Z, c.d_Gp, c.d_W7, c.d_HP, c.d_R,
                     c.d_P, c.d_Linv, c.d_F, c.d_G, c.d_D, c.d_Sig, c.d_small, c.d_flag,
-                    c.d_V, c.d_J, c.d_pair_desc, c.d_pair_ent, c.d_w7part};
+                    c.d_V, c.d_J, c.d_pair_desc, c.d_pair_ent, c.d_w7part, c.d_sgauge};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ccov::mixed_free(c);
@@ -441,6 +441,7 @@ ccov_status ccov_create(const double* cameras, int64_t n, const double* points, 
     CK(dalloc(c, &c.d_D, Np), "alloc");
     CK(dalloc(c, &c.d_Sig, 81 * n), "alloc");
     CK(dalloc(c, &c.d_small, 256), "alloc");
+    CK(dalloc(c, &c.d_sgauge, 28 * ccov::kSurrGaugeBlocks + 49), "alloc");
     CK(dalloc(c, &c.d_flag, 2), "alloc");
     CK(dalloc(c, &c.d_Linv, (Np / ccov::kNB) * ccov::kNB * ccov::kNB), "alloc");
     if (c.opt.precision == CCOV_PREC_FP64) {
@@ -778,9 +779,23 @@ ccov_status ccov_surrogate_features(ccov_ctx* h, float* features, double* scale)
     if (!h || !features || !scale) return CCOV_ERR_INVALID_ARG;
     Ctx& c = h->c;
     if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_features: call ccov_information first");
+    if (c.opt.camera_model != CCOV_CAMERA_RT9)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_features: the surrogate takes 9-value cameras");
     ccov::surr_launch_features(c, features, scale);
     CK(cudaGetLastError(), "ccov_surrogate_features launch");
     return check_device(c, "ccov_surrogate_features");
+}
+
+ccov_status ccov_surrogate_gauge_rows(ccov_ctx* h, const double* scale, double* q) {
+    if (!h || !scale || !q) return CCOV_ERR_INVALID_ARG;
+    Ctx& c = h->c;
+    if (c.stage < 2) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_gauge_rows: call ccov_information first");
+    if (!c.null_done) return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_gauge_rows: call ccov_nullspace first");
+    if (c.opt.camera_model != CCOV_CAMERA_RT9)
+        return fail(&c, CCOV_ERR_INVALID_ARG, "ccov_surrogate_gauge_rows: the surrogate takes 9-value cameras");
+    ccov::surr_launch_gauge_rows(c, scale, q);
+    CK(cudaGetLastError(), "ccov_surrogate_gauge_rows launch");
+    return check_device(c, "ccov_surrogate_gauge_rows");
 }
 
 ccov_status ccov_batch_covariance(ccov_ctx* const* ctxs, int k, double* const* outs, int out_memory) {

@@ -87,6 +87,7 @@ struct Ctx {
     double* d_D = nullptr;        // Np Jacobi scale
     double* d_Sig = nullptr;      // n x 81 scaled, then unscaled blocks
     double* d_small = nullptr;    // 64: W7^-1 and scratch
+    double* d_sgauge = nullptr;   // surrogate gauge rows: kSurrGaugeBlocks x 28 partial sums, then L_c (49)
     int* d_flag = nullptr;        // [0] error code, [1] detail
     int64_t bytes = 0;
     int64_t launches = 0;
@@ -150,6 +151,8 @@ void launch_upd_obs(Ctx& c, int64_t k, const ccov_obs* add, const double* add_co
 
 // ---- surrogate features (k_surrogate.cu) ----
 void surr_launch_features(Ctx& c, float* feat, double* scale);
+constexpr int kSurrGaugeBlocks = 152;
+void surr_launch_gauge_rows(Ctx& c, const double* scale, double* q);
 
 // ---- mixed path (k_mixed.cu) ----
 cudaError_t mixed_alloc(Ctx& c);

@@ -244,9 +244,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(GemmP g) {
     }
 }
 
-// Gather rows idx[b] of the raw features and targets, standardise, and write
-// the input operand (and its transpose) as bf16; rows b >= B are zero.  The
-// row offset into idx is ctr[1] * B (the step within a training call).
+// Size scale of the output head: feature 48 (10 / sqrt(n)) when positive,
+// else 1.  The network learns target / s, and its output is multiplied by s:
+// around the base with the gauge term the remainder shrinks about as
+// n^-1/2, so the scaled target keeps its size from scene to scene.  Feature
+// 48 is not a network input (its column of the input operand is zero), so
+// that no input leaves the training range on larger scenes.
+constexpr int kSizeFeature = 48;
+__device__ __forceinline__ float head_scale(const float* feat_row) {
+    const float v = feat_row[kSizeFeature];
+    return v > 0.f ? v : 1.f;
+}
+
+// Gather rows idx[b] of the raw features and targets, standardise (targets
+// after the division by the head's size scale), and write the input operand
+// (and its transpose) as bf16; rows b >= B are zero.  The row offset into idx
+// is ctr[1] * B (the step within a training call).
 __global__ void pack_kernel(const float* __restrict__ feat, const float* __restrict__ targ,
                             const int* __restrict__ idx, int64_t n, const int* __restrict__ ctr, int B, int Bp,
                             const float* __restrict__ norm, bf16* __restrict__ A0n, bf16* __restrict__ A0t,
@@ -260,14 +273,16 @@ __global__ void pack_kernel(const float* __restrict__ feat, const float* __restr
             src = -1;
         }
     }
-    float x = 0.f;
-    if (src >= 0 && k < kIn) x = (feat[(int64_t)src * kIn + k] - norm[k]) / norm[kIn + k];
+    float x = 0.f;  // feature 48 sets only the head's size scale: its input column stays zero
+    if (src >= 0 && k < kIn && k != kSizeFeature) x = (feat[(int64_t)src * kIn + k] - norm[k]) / norm[kIn + k];
     const bf16 h = __float2bfloat16_rn(x);
     A0n[kb_off(b, k, Bp)] = h;
     A0t[kb_off(k, b, kInP)] = h;
     if (T && k < kOut) {
         float t = 0.f;
-        if (src >= 0) t = (targ[(int64_t)src * kOut + k] - norm[2 * kIn + k]) / norm[2 * kIn + kOut + k];
+        if (src >= 0)
+            t = (targ[(int64_t)src * kOut + k] / head_scale(feat + src * kIn) - norm[2 * kIn + k]) /
+                norm[2 * kIn + kOut + k];
         T[(int64_t)b * kOut + k] = t;
     }
 }
@@ -388,14 +403,20 @@ __global__ void cast_kernel(const float* __restrict__ p, int64_t P, Segs S) {
     write_bf16(S, seg, e - S.s[seg].off, p[e]);
 }
 
-// Column mean and population deviation of x (n x w) into mu[w], sd[w] (a
+// Column mean and population deviation of x (n x w), each row divided by the
+// head's size scale of feat's row when feat is given, into mu[w], sd[w] (a
 // deviation below 1e-6 becomes 1); one block per column, fp64 sums.
-__global__ void norm_kernel(const float* __restrict__ x, int64_t n, int w, float* __restrict__ mu,
-                            float* __restrict__ sd) {
+__device__ __forceinline__ double norm_value(const float* x, const float* feat, int64_t r, int w, int col) {
+    const double v = x[r * w + col];
+    return feat ? v / head_scale(feat + r * kIn) : v;
+}
+
+__global__ void norm_kernel(const float* __restrict__ x, const float* __restrict__ feat, int64_t n, int w,
+                            float* __restrict__ mu, float* __restrict__ sd) {
     const int col = blockIdx.x;
     __shared__ double red[2][8];
     double s = 0.0;
-    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += x[r * w + col];
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += norm_value(x, feat, r, w, col);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = s;
     __syncthreads();
@@ -404,7 +425,7 @@ __global__ void norm_kernel(const float* __restrict__ x, int64_t n, int w, float
     mean /= (double)n;
     double q = 0.0;
     for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
-        const double d = x[r * w + col] - mean;
+        const double d = norm_value(x, feat, r, w, col) - mean;
         q += d * d;
     }
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -527,7 +548,7 @@ features_kernel(int64_t n, const double* __restrict__ U, const double* __restric
         f[45] = (float)log(cnt);
         f[46] = (float)(slog / cnt);
         f[47] = (float)(two / cnt);
-        f[48] = (float)log((double)n);
+        f[48] = (float)(10.0 / sqrt((double)n));
     }
     if (lane >= 17) feat[i * kIn + 32 + lane] = 0.f;  // [49, 64); 49 is written by centre_feature_kernel
 }
@@ -626,21 +647,24 @@ __global__ void targets_kernel(int64_t n, const double* __restrict__ scale, cons
     }
 }
 
+// Target form t = s (y sd + mu) (s the head's size scale), then
 // Sigma_hat = L_z^-T L L^T L_z^-1 = X X^T with L_z^T X = L (back substitution).
 __global__ void predict_out_kernel(int64_t n, const float* __restrict__ Y, const float* __restrict__ norm,
-                                   const double* __restrict__ scale, double* __restrict__ sigma) {
+                                   const float* __restrict__ feat, const double* __restrict__ scale,
+                                   double* __restrict__ sigma) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float* y = Y + kOutP * i;
     const float* mu = norm + 2 * kIn;
     const float* sd = mu + kOut;
+    const double hs = head_scale(feat + i * kIn);
     double X[9][9];
     for (int r = 0; r < 9; ++r)
         for (int c = 0; c < 9; ++c) X[r][c] = 0.0;
     int q = 9;
     for (int r = 0; r < 9; ++r) {
-        X[r][r] = exp((double)y[r] * sd[r] + mu[r]);
-        for (int c = 0; c < r; ++c, ++q) X[r][c] = (double)y[q] * sd[q] + mu[q];
+        X[r][r] = exp(hs * ((double)y[r] * sd[r] + mu[r]));
+        for (int c = 0; c < r; ++c, ++q) X[r][c] = hs * ((double)y[q] * sd[q] + mu[q]);
     }
     const double* Lz = scale + 81 * i;
     for (int c = 0; c < 9; ++c)
@@ -657,6 +681,311 @@ __global__ void predict_out_kernel(int64_t n, const float* __restrict__ Y, const
         }
 }
 
+// ---- gauge term of the base covariance (fp64, small dense blocks) ----
+// Z_ii^-1 holds every other camera fixed and so pins the datum as well; in
+// the similarity gauge (Sec. 4.1) the camera moves with the datum too, along
+// its own nullspace rows H_i.  The base B_i = Z_ii^-1 + Q_i M Q_i^T adds that
+// motion: Q_i = H_i L_c, L_c the Cholesky factor of (sum_i H_i^T Z_ii H_i)^-1,
+// and M a learned symmetric 7 x 7 matrix.  Targets and predictions are then
+// whitened by T_i = chol(B_i^-1) in place of L_z (T_i = L_z when M = 0).
+
+// Cholesky factor (lower, row-major, zero above) of a K x K SPD matrix;
+// false when a pivot is not above `tiny`.
+template <int K>
+__device__ bool chol_k(const double* a, double* l, double tiny = 0.0) {
+    for (int r = 0; r < K; ++r)
+        for (int c = 0; c < K; ++c) l[K * r + c] = 0.0;
+    for (int r = 0; r < K; ++r)
+        for (int c = 0; c <= r; ++c) {
+            double v = a[K * r + c];
+            for (int k = 0; k < c; ++k) v -= l[K * r + k] * l[K * c + k];
+            if (r == c) {
+                if (!(v > tiny)) return false;
+                l[K * r + r] = sqrt(v);
+            } else {
+                l[K * r + c] = v / l[K * c + c];
+            }
+        }
+    return true;
+}
+
+// x = l^-1 for a lower-triangular l (forward substitution column by column).
+template <int K>
+__device__ void tri_inv_k(const double* l, double* x) {
+    for (int c = 0; c < K; ++c)
+        for (int r = 0; r < K; ++r) {
+            if (r < c) {
+                x[K * r + c] = 0.0;
+                continue;
+            }
+            double v = r == c ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) v -= l[K * r + k] * x[K * k + c];
+            x[K * r + c] = v / l[K * r + r];
+        }
+}
+
+// a^-1 = x^T x with x = chol(a)^-1; false when a is not positive definite.
+template <int K>
+__device__ bool spd_inv_k(const double* a, double* ainv) {
+    double l[K * K], x[K * K];
+    if (!chol_k<K>(a, l)) return false;
+    tri_inv_k<K>(l, x);
+    for (int r = 0; r < K; ++r)
+        for (int c = 0; c < K; ++c) {
+            double v = 0.0;
+            for (int k = r > c ? r : c; k < K; ++k) v += x[K * k + r] * x[K * k + c];
+            ainv[K * r + c] = v;
+        }
+    return true;
+}
+
+// AH = sum_i P_i^T P_i with P_i = L_z^T H_i (9 x 7), over a scene's cameras:
+// block b sums the cameras [b chunk, (b + 1) chunk) (its threads strided, the
+// 28 entries k <= l reduced by fixed trees), and one block then adds the
+// blocks' sums in order (the same bits on every run), forms
+// L_c = chol(AH^-1), and a camera-parallel kernel writes Q_i = H_i L_c.
+constexpr int kGaugeThreads = 256;
+
+__global__ void __launch_bounds__(kGaugeThreads)
+gauge_sum_kernel(int64_t n, const double* __restrict__ Lz, const double* __restrict__ HP,
+                 double* __restrict__ part) {
+    __shared__ double red[28][kGaugeThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t chunk = (n + kSurrGaugeBlocks - 1) / kSurrGaugeBlocks;
+    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    double acc[28];
+#pragma unroll
+    for (int e = 0; e < 28; ++e) acc[e] = 0.0;
+    for (int64_t i = i0 + tid; i < i1; i += kGaugeThreads) {
+        const double* L = Lz + 81 * i;
+        const double* H = HP + 63 * i;
+        double P[63];
+        for (int a = 0; a < 9; ++a)
+            for (int k = 0; k < 7; ++k) {
+                double v = 0.0;
+                for (int b = a; b < 9; ++b) v += L[9 * b + a] * H[7 * b + k];
+                P[7 * a + k] = v;
+            }
+        int e = 0;
+        for (int k = 0; k < 7; ++k)
+            for (int l = k; l < 7; ++l, ++e) {
+                double v = 0.0;
+                for (int a = 0; a < 9; ++a) v += P[7 * a + k] * P[7 * a + l];
+                acc[e] += v;
+            }
+    }
+#pragma unroll
+    for (int e = 0; e < 28; ++e) {
+        const double v = warp_sum_d(acc[e]);
+        if (lane == 0) red[e][w] = v;
+    }
+    __syncthreads();
+    if (tid < 28) {
+        double v = 0.0;
+        for (int q = 0; q < kGaugeThreads / 32; ++q) v += red[tid][q];
+        part[28 * (int64_t)blockIdx.x + tid] = v;
+    }
+}
+
+// One warp: the blocks' sums in order, then L_c (49 values after the partials).
+__global__ void gauge_factor_kernel(double* __restrict__ part, int* flag) {
+    __shared__ double AH[49];
+    const int tid = threadIdx.x;
+    if (tid < 28) {
+        int k = 0, rem = tid;
+        while (rem >= 7 - k) { rem -= 7 - k; ++k; }
+        const int l = k + rem;
+        double v = 0.0;
+        for (int b = 0; b < kSurrGaugeBlocks; ++b) v += part[28 * b + tid];
+        AH[7 * k + l] = AH[7 * l + k] = v;
+    }
+    __syncwarp();
+    if (tid != 0) return;
+    double AHi[49], L7[49];
+    const bool ok = spd_inv_k<7>(AH, AHi) && chol_k<7>(AHi, L7);
+    if (!ok) set_flag(flag, DEV_NOT_SPD, 0);
+    double* Lc = part + 28 * kSurrGaugeBlocks;
+    for (int k = 0; k < 49; ++k) Lc[k] = ok ? L7[k] : 0.0;
+}
+
+__global__ void gauge_q_kernel(int64_t n, const double* __restrict__ HP, const double* __restrict__ Lcg,
+                               double* __restrict__ Q) {
+    __shared__ double Lc[49];
+    if (threadIdx.x < 49) Lc[threadIdx.x] = Lcg[threadIdx.x];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* H = HP + 63 * i;
+    double* q = Q + 63 * i;
+    for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 7; ++c) {
+            double v = 0.0;
+            for (int k = c; k < 7; ++k) v += H[7 * r + k] * Lc[7 * k + c];
+            q[7 * r + c] = v;
+        }
+}
+
+// Least squares for M over the training cameras.  Per camera:
+// Qt = L_z^T Q_i (9 x 7), E = L_z^T Sigma_i L_z - I, G = Qt^T Qt and
+// R = Qt^T E Qt.  With the 28 symmetric basis matrices E_p (p = (k, l),
+// k <= l, ones at (k, l) and (l, k)) the normal equations are
+//   sum_q N_pq m_q = r_p,  N_pq = sum_i tr(E_p G E_q G),  r_p = sum_i tr(R E_p).
+// The 406 entries p <= q of N and the 28 of r are summed per block (fixed
+// camera ranges, warp trees, warps in order) and the blocks in order.
+constexpr int kFitBlocks = 256, kFitThreads = 256, kFitN = 406, kFitEntries = kFitN + 28;
+
+__constant__ unsigned char c_sym_k[28], c_sym_l[28];
+__constant__ unsigned char c_pair_p[kFitN], c_pair_q[kFitN];
+
+__global__ void __launch_bounds__(kFitThreads)
+gauge_fit_partial_kernel(int64_t n, const double* __restrict__ Lz, const double* __restrict__ Qg,
+                         const double* __restrict__ sigma, double* __restrict__ part) {
+    __shared__ double wacc[kFitThreads / 32][kFitEntries];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int e = lane; e < kFitEntries; e += 32) wacc[w][e] = 0.0;
+    const int64_t chunk = (n + kFitBlocks - 1) / kFitBlocks;
+    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    for (int64_t base = i0; base < i1; base += kFitThreads) {
+        const int64_t i = base + tid;
+        double G[49], R[49];
+        if (i < i1) {
+            const double* L = Lz + 81 * i;
+            const double* q = Qg + 63 * i;
+            const double* S = sigma + 81 * i;
+            double Qt[63], Y[81], E[81];
+            for (int a = 0; a < 9; ++a)
+                for (int k = 0; k < 7; ++k) {
+                    double v = 0.0;
+                    for (int b = a; b < 9; ++b) v += L[9 * b + a] * q[7 * b + k];
+                    Qt[7 * a + k] = v;
+                }
+            for (int r = 0; r < 9; ++r)  // Y = Sigma L_z
+                for (int c = 0; c < 9; ++c) {
+                    double v = 0.0;
+                    for (int k = c; k < 9; ++k) v += S[9 * r + k] * L[9 * k + c];
+                    Y[9 * r + c] = v;
+                }
+            for (int r = 0; r < 9; ++r)  // E = L_z^T Y - I
+                for (int c = 0; c < 9; ++c) {
+                    double v = 0.0;
+                    for (int k = r; k < 9; ++k) v += L[9 * k + r] * Y[9 * k + c];
+                    E[9 * r + c] = v - (r == c ? 1.0 : 0.0);
+                }
+            for (int k = 0; k < 7; ++k)
+                for (int l = 0; l < 7; ++l) {
+                    double g = 0.0, rr = 0.0;
+                    for (int a = 0; a < 9; ++a) {
+                        g += Qt[7 * a + k] * Qt[7 * a + l];
+                        double t = 0.0;
+                        for (int b = 0; b < 9; ++b) t += E[9 * a + b] * Qt[7 * b + l];
+                        rr += Qt[7 * a + k] * t;
+                    }
+                    G[7 * k + l] = g;
+                    R[7 * k + l] = rr;
+                }
+        } else {
+            for (int k = 0; k < 49; ++k) G[k] = R[k] = 0.0;
+        }
+        for (int e = 0; e < kFitEntries; ++e) {
+            double v;
+            if (e < kFitN) {
+                const int p = c_pair_p[e], q = c_pair_q[e];
+                const int k = c_sym_k[p], l = c_sym_l[p], a = c_sym_k[q], b = c_sym_l[q];
+                // tr(E_p G E_q G): sum over the unit terms e_x e_y^T of E_p and e_u e_v^T of E_q
+                v = G[7 * b + k] * G[7 * l + a];
+                if (a != b) v += G[7 * a + k] * G[7 * l + b];
+                if (k != l) {
+                    v += G[7 * b + l] * G[7 * k + a];
+                    if (a != b) v += G[7 * a + l] * G[7 * k + b];
+                }
+            } else {
+                const int p = e - kFitN, k = c_sym_k[p], l = c_sym_l[p];
+                v = k == l ? R[7 * k + k] : R[7 * k + l] + R[7 * l + k];
+            }
+            v = warp_sum_d(v);
+            if (lane == 0) wacc[w][e] += v;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kFitEntries; e += kFitThreads) {
+        double v = 0.0;
+        for (int q = 0; q < kFitThreads / 32; ++q) v += wacc[q][e];
+        part[(int64_t)blockIdx.x * kFitEntries + e] = v;
+    }
+}
+
+// Blocks' partial sums in order, then N m = r by Cholesky (one thread).
+__global__ void __launch_bounds__(512) gauge_fit_solve_kernel(const double* __restrict__ part,
+                                                             double* __restrict__ M, int* flag) {
+    __shared__ double tot[kFitEntries];
+    __shared__ double N[28 * 28], L[28 * 28];  // shared, not per-thread: one thread factors them
+    for (int e = threadIdx.x; e < kFitEntries; e += blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < kFitBlocks; ++b) v += part[(int64_t)b * kFitEntries + e];
+        tot[e] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double m[28], dmax = 0.0;
+    for (int e = 0; e < kFitN; ++e) {
+        const int p = c_pair_p[e], q = c_pair_q[e];
+        N[28 * p + q] = N[28 * q + p] = tot[e];
+        if (p == q) dmax = fmax(dmax, tot[e]);
+    }
+    // a pivot below 1e-9 of the largest diagonal entry: the cameras do not
+    // determine M (one camera's rows have rank 6, so it fixes 21 of the 28
+    // entries; the normal matrices of real scenes have eigenvalue ratios near 0.4)
+    if (!(dmax > 0.0) || !chol_k<28>(N, L, 1e-9 * dmax)) {
+        set_flag(flag, DEV_NOT_SPD, 0);
+        return;
+    }
+    for (int p = 0; p < 28; ++p) {  // L y = r
+        double v = tot[kFitN + p];
+        for (int k = 0; k < p; ++k) v -= L[28 * p + k] * m[k];
+        m[p] = v / L[28 * p + p];
+    }
+    for (int p = 27; p >= 0; --p) {  // L^T m = y
+        double v = m[p];
+        for (int k = p + 1; k < 28; ++k) v -= L[28 * k + p] * m[k];
+        m[p] = v / L[28 * p + p];
+    }
+    for (int p = 0; p < 28; ++p) {
+        const int k = c_sym_k[p], l = c_sym_l[p];
+        M[7 * k + l] = M[7 * l + k] = m[p];
+    }
+}
+
+// T_i = chol(B_i^-1), B_i = Z_ii^-1 + Q_i M Q_i^T, Z_ii^-1 = X^T X with X = L_z^-1.
+__global__ void gauge_apply_kernel(int64_t n, const double* __restrict__ Lz, const double* __restrict__ Qg,
+                                   const double* __restrict__ Mg, double* __restrict__ T, int* flag) {
+    __shared__ double Ms[49];
+    if (threadIdx.x < 49) Ms[threadIdx.x] = Mg[threadIdx.x];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* q = Qg + 63 * i;
+    double X[81], B[81], QM[63], Bi[81], Tl[81];
+    tri_inv_k<9>(Lz + 81 * i, X);
+    for (int a = 0; a < 9; ++a)  // (Q M)^T, 7 x 9
+        for (int l = 0; l < 7; ++l) {
+            double v = 0.0;
+            for (int k = 0; k < 7; ++k) v += q[7 * a + k] * Ms[7 * k + l];
+            QM[9 * l + a] = v;
+        }
+    for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) {
+            double v = 0.0;
+            for (int k = r > c ? r : c; k < 9; ++k) v += X[9 * k + r] * X[9 * k + c];
+            for (int l = 0; l < 7; ++l) v += QM[9 * l + r] * q[7 * c + l];
+            B[9 * r + c] = v;
+        }
+    for (int r = 0; r < 9; ++r)  // symmetric to the last bit before the factorisations
+        for (int c = 0; c < r; ++c) B[9 * c + r] = B[9 * r + c] = 0.5 * (B[9 * r + c] + B[9 * c + r]);
+    const bool ok = spd_inv_k<9>(B, Bi) && chol_k<9>(Bi, Tl);
+    if (!ok) set_flag(flag, DEV_NOT_SPD, (int)i);
+    for (int k = 0; k < 81; ++k) T[81 * i + k] = ok ? Tl[k] : 0.0;
+}
+
 }  // namespace surr
 
 void surr_launch_features(Ctx& c, float* feat, double* scale) {
@@ -667,6 +996,14 @@ void surr_launch_features(Ctx& c, float* feat, double* scale) {
         c.d_flag);
     centre_stats_kernel<<<1, 1024, 0, c.stream>>>(c.n, c.d_camprep, csum);
     centre_feature_kernel<<<(unsigned)((c.n + 127) / 128), 128, 0, c.stream>>>(c.n, c.d_camprep, csum, feat);
+    c.launches += 3;
+}
+
+void surr_launch_gauge_rows(Ctx& c, const double* scale, double* q) {
+    surr::gauge_sum_kernel<<<kSurrGaugeBlocks, surr::kGaugeThreads, 0, c.stream>>>(c.n, scale, c.d_HP, c.d_sgauge);
+    surr::gauge_factor_kernel<<<1, 32, 0, c.stream>>>(c.d_sgauge, c.d_flag);
+    surr::gauge_q_kernel<<<(unsigned)((c.n + 127) / 128), 128, 0, c.stream>>>(
+        c.n, c.d_HP, c.d_sgauge + 28 * kSurrGaugeBlocks, q);
     c.launches += 3;
 }
 
@@ -694,6 +1031,8 @@ struct ccov_surrogate {
     int* ctr = nullptr;                // [0] Adam steps, [1] in-call step
     unsigned* done = nullptr;
     int* flag = nullptr;
+    double* gauge = nullptr;           // M, 7 x 7 row-major (zero until fitted or set)
+    double* gpart = nullptr;           // partial sums of the gauge fit, kFitBlocks x kFitEntries
     std::vector<void*> allocs;
 };
 
@@ -778,6 +1117,8 @@ ccov_status check_flag(ccov_surrogate* s, const char* where) {
     if (f[0] == ccov::DEV_TIMEOUT) return sfail(s, CCOV_ERR_TIMEOUT, "%s: device wait gave up (site %d)", where, f[1]);
     if (f[0] == ccov::DEV_BAD_INDEX)
         return sfail(s, CCOV_ERR_INVALID_ARG, "%s: sample index of batch row %d outside the training set", where, f[1]);
+    if (f[0] == ccov::DEV_NOT_SPD)
+        return sfail(s, CCOV_ERR_DEGENERATE, "%s: a matrix is not positive definite (row %d)", where, f[1]);
     if (f[0] != 0) return sfail(s, CCOV_ERR_CUDA, "%s: device error %d", where, f[0]);
     return CCOV_OK;
 }
@@ -936,6 +1277,22 @@ ccov_status ccov_surrogate_create(const float* params, int64_t max_batch, void* 
     SCK(salloc(s, &s->ctr, 2), "alloc");
     SCK(salloc(s, &s->done, 1), "alloc");
     SCK(salloc(s, &s->flag, 2), "alloc");
+    SCK(salloc(s, &s->gauge, 49), "alloc");
+    SCK(salloc(s, &s->gpart, (size_t)kFitBlocks * kFitEntries), "alloc");
+    SCK(cudaMemsetAsync(s->gauge, 0, 49 * sizeof(double), s->stream), "memset");
+    {
+        unsigned char sk[28], sl[28], pp[kFitN], pq[kFitN];
+        int p = 0;
+        for (int k = 0; k < 7; ++k)
+            for (int l = k; l < 7; ++l, ++p) sk[p] = (unsigned char)k, sl[p] = (unsigned char)l;
+        int e = 0;
+        for (int a = 0; a < 28; ++a)
+            for (int b = a; b < 28; ++b, ++e) pp[e] = (unsigned char)a, pq[e] = (unsigned char)b;
+        SCK(cudaMemcpyToSymbol(c_sym_k, sk, sizeof sk), "constants");
+        SCK(cudaMemcpyToSymbol(c_sym_l, sl, sizeof sl), "constants");
+        SCK(cudaMemcpyToSymbol(c_pair_p, pp, sizeof pp), "constants");
+        SCK(cudaMemcpyToSymbol(c_pair_q, pq, sizeof pq), "constants");
+    }
     ccov_status st = ensure_losses(s, 1);
     if (st != CCOV_OK) return st;
     SCK(cudaMemsetAsync(s->m, 0, sizeof(float) * kPadParams, s->stream), "memset");
@@ -1007,8 +1364,9 @@ ccov_status ccov_surrogate_get_normalization(const ccov_surrogate* cs, float* no
 ccov_status ccov_surrogate_fit_normalization(ccov_surrogate* s, const float* features, const float* targets,
                                              int64_t n) {
     if (!s || !features || !targets || n < 1) return CCOV_ERR_INVALID_ARG;
-    norm_kernel<<<kIn, 256, 0, s->stream>>>(features, n, kIn, s->norm, s->norm + kIn);
-    norm_kernel<<<kOut, 256, 0, s->stream>>>(targets, n, kOut, s->norm + 2 * kIn, s->norm + 2 * kIn + kOut);
+    norm_kernel<<<kIn, 256, 0, s->stream>>>(features, nullptr, n, kIn, s->norm, s->norm + kIn);
+    norm_kernel<<<kOut, 256, 0, s->stream>>>(targets, features, n, kOut, s->norm + 2 * kIn,
+                                             s->norm + 2 * kIn + kOut);
     SCK(cudaGetLastError(), "normalisation");
     return check_flag(s, "ccov_surrogate_fit_normalization");
 }
@@ -1078,11 +1436,50 @@ ccov_status ccov_surrogate_predict(ccov_surrogate* s, const float* features, con
         gemm(s, s->a_n[1], Bp, s->wb[1], 256, 256, EPI_RELU, s->p + kOffB2, s->a_n[2], s->a_t[2], nullptr, nullptr, nullptr);
         gemm(s, s->a_n[2], Bp, s->wb[2], 256, 256, EPI_RELU, s->p + kOffB3, s->a_n[3], s->a_t[3], nullptr, nullptr, nullptr);
         gemm(s, s->a_n[3], Bp, s->wb[3], kOutP, 256, EPI_OUT, s->p + kOffB4, nullptr, nullptr, nullptr, s->Y, nullptr);
-        predict_out_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s->stream>>>(B, s->Y, s->norm, scale + 81 * r0,
+        predict_out_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s->stream>>>(B, s->Y, s->norm, features + r0 * kIn,
+                                                                               scale + 81 * r0,
                                                                                sigma + 81 * r0);
         SCK(cudaGetLastError(), "ccov_surrogate_predict launch");
     }
     return check_flag(s, "ccov_surrogate_predict");
+}
+
+ccov_status ccov_surrogate_set_gauge(ccov_surrogate* s, const double* M) {
+    if (!s || !M) return CCOV_ERR_INVALID_ARG;
+    for (int k = 0; k < 7; ++k)
+        for (int l = 0; l < 7; ++l)
+            if (!std::isfinite(M[7 * k + l]) || M[7 * k + l] != M[7 * l + k])
+                return sfail(s, CCOV_ERR_INVALID_ARG, "gauge matrix not finite and symmetric at (%d, %d)", k, l);
+    SCK(cudaMemcpyAsync(s->gauge, M, 49 * sizeof(double), cudaMemcpyHostToDevice, s->stream), "copy");
+    SCK(cudaStreamSynchronize(s->stream), "sync");
+    return CCOV_OK;
+}
+
+ccov_status ccov_surrogate_get_gauge(const ccov_surrogate* cs, double* M) {
+    ccov_surrogate* s = const_cast<ccov_surrogate*>(cs);
+    if (!s || !M) return CCOV_ERR_INVALID_ARG;
+    SCK(cudaStreamSynchronize(s->stream), "sync");
+    SCK(cudaMemcpy(M, s->gauge, 49 * sizeof(double), cudaMemcpyDeviceToHost), "copy");
+    return CCOV_OK;
+}
+
+ccov_status ccov_surrogate_fit_gauge(ccov_surrogate* s, const double* scale, const double* q, const double* sigma,
+                                     int64_t n) {
+    if (!s || !scale || !q || !sigma || n < 1) return CCOV_ERR_INVALID_ARG;
+    SCK(cudaMemsetAsync(s->flag, 0, 2 * sizeof(int), s->stream), "memset");
+    gauge_fit_partial_kernel<<<kFitBlocks, kFitThreads, 0, s->stream>>>(n, scale, q, sigma, s->gpart);
+    gauge_fit_solve_kernel<<<1, 512, 0, s->stream>>>(s->gpart, s->gauge, s->flag);
+    SCK(cudaGetLastError(), "ccov_surrogate_fit_gauge launch");
+    return check_flag(s, "ccov_surrogate_fit_gauge");
+}
+
+ccov_status ccov_surrogate_apply_gauge(ccov_surrogate* s, const double* scale, const double* q, int64_t n,
+                                       double* base) {
+    if (!s || !scale || !q || !base || n < 1) return CCOV_ERR_INVALID_ARG;
+    SCK(cudaMemsetAsync(s->flag, 0, 2 * sizeof(int), s->stream), "memset");
+    gauge_apply_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s->stream>>>(n, scale, q, s->gauge, base, s->flag);
+    SCK(cudaGetLastError(), "ccov_surrogate_apply_gauge launch");
+    return check_flag(s, "ccov_surrogate_apply_gauge");
 }
 
 void ccov_surrogate_destroy(ccov_surrogate* s) {

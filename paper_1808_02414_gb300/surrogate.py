@@ -20,7 +20,8 @@ EXPORTED = ["ccov_surrogate_features", "ccov_surrogate_targets", "ccov_surrogate
             "ccov_surrogate_get_normalization", "ccov_surrogate_set_params", "ccov_surrogate_get_params",
             "ccov_surrogate_backward", "ccov_surrogate_get_grads", "ccov_surrogate_adam",
             "ccov_surrogate_train", "ccov_surrogate_predict", "ccov_surrogate_destroy",
-            "ccov_surrogate_last_error"]
+            "ccov_surrogate_last_error", "ccov_surrogate_gauge_rows", "ccov_surrogate_set_gauge",
+            "ccov_surrogate_get_gauge", "ccov_surrogate_fit_gauge", "ccov_surrogate_apply_gauge"]
 
 
 def _dev(t, dtype_name: str):
@@ -31,6 +32,13 @@ def _dev(t, dtype_name: str):
     return t.data_ptr()
 
 
+def _rows(n: int, **arrays):
+    """Each array holds n rows of the given width (the C calls read n rows)."""
+    for name, (a, width) in arrays.items():
+        if a.numel() != n * width:
+            raise ValueError(f"{name} must hold {n} rows of {width} values")
+
+
 def features(ctx: ccov.Context):
     """(features (n, 64) float32, L_z (n, 9, 9) float64) on the device, from
     a context that has run ccov_information."""
@@ -39,6 +47,17 @@ def features(ctx: ccov.Context):
     d = torch.empty((ctx.n, 9, 9), dtype=torch.float64, device="cuda")
     ctx._check(ccov.load().ccov_surrogate_features(ctx._h, _dev(f, "float32"), _dev(d, "float64")))
     return f, d
+
+
+def gauge_rows(ctx: ccov.Context, scale):
+    """Q_i = H_i L_c (n, 9, 7) float64 on the device, from a context that has
+    run ccov_information and ccov_nullspace; scale: L_z from `features`."""
+    import torch
+    if tuple(scale.shape) != (ctx.n, 9, 9):
+        raise ValueError("scale must be (n, 9, 9)")
+    q = torch.empty((ctx.n, 9, 7), dtype=torch.float64, device="cuda")
+    ctx._check(ccov.load().ccov_surrogate_gauge_rows(ctx._h, _dev(scale, "float64"), _dev(q, "float64")))
+    return q
 
 
 def targets(scale, sigma):
@@ -85,6 +104,32 @@ class Surrogate:
         a = np.empty(N_NORM, dtype=np.float32)
         self._check(ccov.load().ccov_surrogate_get_normalization(self._h, a.ctypes.data))
         return a
+
+    def set_gauge(self, M: np.ndarray):
+        a = np.ascontiguousarray(M, dtype=np.float64).reshape(49)
+        self._check(ccov.load().ccov_surrogate_set_gauge(self._h, a.ctypes.data))
+
+    def gauge(self) -> np.ndarray:
+        a = np.empty(49, dtype=np.float64)
+        self._check(ccov.load().ccov_surrogate_get_gauge(self._h, a.ctypes.data))
+        return a.reshape(7, 7)
+
+    def fit_gauge(self, scale, q, sigma):
+        """M by least squares over the cameras of (L_z, Q, exact blocks)."""
+        n = int(scale.shape[0])
+        _rows(n, scale=(scale, 81), q=(q, 63), sigma=(sigma, 81))
+        self._check(ccov.load().ccov_surrogate_fit_gauge(
+            self._h, _dev(scale, "float64"), _dev(q, "float64"), _dev(sigma.reshape(n, 81), "float64"), n))
+
+    def apply_gauge(self, scale, q):
+        """T_i = chol((Z_ii^-1 + Q_i M Q_i^T)^-1) (n, 9, 9) on the device."""
+        import torch
+        n = int(scale.shape[0])
+        _rows(n, scale=(scale, 81), q=(q, 63))
+        out = torch.empty((n, 9, 9), dtype=torch.float64, device="cuda")
+        self._check(ccov.load().ccov_surrogate_apply_gauge(
+            self._h, _dev(scale, "float64"), _dev(q, "float64"), n, _dev(out, "float64")))
+        return out
 
     def set_params(self, params: np.ndarray):
         a = np.ascontiguousarray(params, dtype=np.float32)

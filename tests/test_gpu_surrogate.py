@@ -11,7 +11,7 @@ Adam runs in fp32 against the oracle's fp64: 1e-5 relative."""
 import numpy as np
 import pytest
 
-from oracle import covariance, metrics, surrogate as S
+from oracle import covariance, metrics, nullspace, surrogate as S
 from paper_1808_02414_gb300 import ccov, surrogate, synth
 
 pytestmark = pytest.mark.gpu
@@ -28,6 +28,30 @@ def _scene_data(sc):
         sig = torch.empty((sc.n, 9, 9), dtype=torch.float64, device="cuda")
         ctx.ccov_covariance(out=sig)
     return f, lz, sig
+
+
+def _gauge_data(sc):
+    """GPU features, L_z, gauge rows Q and exact FP64 covariance blocks of one scene."""
+    with ccov.from_scene(sc) as ctx:
+        ctx.ccov_information()
+        ctx.ccov_schur()
+        f, lz = surrogate.features(ctx)
+        ctx.ccov_nullspace()
+        q = surrogate.gauge_rows(ctx, lz)
+        sig = torch.empty((sc.n, 9, 9), dtype=torch.float64, device="cuda")
+        ctx.ccov_covariance(out=sig)
+    return f, lz, q, sig
+
+
+def _oracle_gauge(sc):
+    """The oracle's L_z and gauge rows of one scene (H_i in closed form)."""
+    _, lzo = S.features(sc)
+    H = nullspace.camera_rows_closed_form(sc).reshape(sc.n, 9, 7)
+    return lzo, S.gauge_rows(lzo, H)
+
+
+def _block_rel(a, b):
+    return np.linalg.norm(a - b, axis=(1, 2)) / np.linalg.norm(b, axis=(1, 2))
 
 
 def _params(seed):
@@ -60,6 +84,7 @@ def test_loss_and_gradients_match_oracle(B):
     n = 1500
     F = rng.normal(size=(n, 64)).astype(np.float32)
     F[:, 50:] = 0
+    F[:, 48] = rng.uniform(0.3, 1.5, n)        # the head's size scale, as 10/sqrt(n) gives it
     T = rng.normal(size=(n, 45)).astype(np.float32)
     params = _params(3)
     norm = _random_norm(rng)
@@ -69,8 +94,8 @@ def test_loss_and_gradients_match_oracle(B):
         loss = sm.backward(torch.from_numpy(F).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(idx).cuda())
         g = sm.grads()
     mu_f, sd_f, mu_t, sd_t = norm[:64], norm[64:128], norm[128:173], norm[173:]
-    x = (F[idx].astype(np.float64) - mu_f) / sd_f
-    t = (T[idx].astype(np.float64) - mu_t) / sd_t
+    x = S.network_input(F[idx].astype(np.float64), mu_f, sd_f)
+    t = (T[idx].astype(np.float64) / S.head_scale(F[idx].astype(np.float64))[:, None] - mu_t) / sd_t
     lo, go = S.loss_and_grads(S.unpack(params.astype(np.float64)), x, t, quantize=True)
     assert abs(loss - lo) <= 1e-4 * lo
     for a, b in zip(S.unpack(g.astype(np.float64)), go):
@@ -158,45 +183,167 @@ def test_normalization_fit_matches_oracle():
     rng = np.random.default_rng(9)
     F = rng.normal(2.0, 3.0, size=(3000, 64)).astype(np.float32)
     F[:, 60:] = 0.0
+    # the head's size scale: positive (divides the targets) or not (scale 1)
+    F[:, 48] = np.where(rng.random(3000) < 0.5, rng.uniform(0.3, 1.5, 3000), -1.0)
     T = rng.normal(-1.0, 0.5, size=(3000, 45)).astype(np.float32)
     with surrogate.Surrogate(synth.surrogate_init(0), max_batch=128) as sm:
         sm.fit_normalization(torch.from_numpy(F).cuda(), torch.from_numpy(T).cuda())
         got = sm.normalization()
     mf, sf = S.normalization(F.astype(np.float64))
-    mt, st = S.normalization(T.astype(np.float64))
+    mt, st = S.normalization(T.astype(np.float64) / S.head_scale(F.astype(np.float64))[:, None])
     np.testing.assert_allclose(got, np.concatenate([mf, sf, mt, st]), rtol=1e-5, atol=1e-6)
 
 
-def test_trained_surrogate_gains_over_the_local_block():
-    """Trained on exact blocks of small scenes, the network predicts held-out
-    scenes' blocks far better than Z_ii^-1 (the covariance with every other
-    camera fixed, which costs the same) and better than a constant learned
-    correction, in the unit-free Gaussian KL measure."""
-    train = synth.batch_scenes(k=24, n_lo=30, n_hi=120, pts_per_cam=60, seed=41)
-    test = synth.batch_scenes(k=4, n_lo=60, n_hi=120, pts_per_cam=60, seed=42)
-    F, LZ, TG = [], [], []
-    for sc in train:
-        f, lz, sig = _scene_data(sc)
+def test_gauge_rows_match_oracle():
+    sc = synth.shell_scene(n=40, m=2000, seed=31)
+    _, lz, q, _ = _gauge_data(sc)
+    lzo, qo = _oracle_gauge(sc)
+    assert _block_rel(q.cpu().numpy(), qo).max() < 1e-8
+    # normalisation: sum_i Q_i^T Z_ii Q_i = I with the oracle's Z_ii
+    Zo = lzo @ lzo.transpose(0, 2, 1)
+    np.testing.assert_allclose(np.einsum("iak,iab,ibl->kl", q.cpu().numpy(), Zo, q.cpu().numpy()), np.eye(7),
+                               atol=1e-8)
+
+
+def test_gauge_fit_and_base_factor_match_oracle():
+    """The fit and the base factor on the oracle's own inputs (two scenes,
+    exact blocks from the covariance oracle), against the oracle's least
+    squares and its base factor."""
+    LZ, Q, SG = [], [], []
+    for n, seed in ((30, 33), (45, 34)):
+        sc = synth.shell_scene(n=n, m=50 * n, seed=seed)
+        lzo, qo = _oracle_gauge(sc)
+        LZ.append(lzo)
+        Q.append(qo)
+        SG.append(covariance.camera_covariance(sc))
+    LZ, Q, SG = (np.concatenate(a) for a in (LZ, Q, SG))
+    Mo = S.fit_gauge(LZ, Q, SG)
+    dl, dq, ds = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (LZ, Q, SG))
+    with surrogate.Surrogate(synth.surrogate_init(0), max_batch=64) as sm:
+        np.testing.assert_array_equal(sm.gauge(), 0.0)
+        np.testing.assert_allclose(sm.apply_gauge(dl, dq).cpu().numpy(), LZ, rtol=1e-9,
+                                   atol=1e-12 * np.abs(LZ).max())   # M = 0: T = L_z
+        sm.fit_gauge(dl, dq, ds)
+        M = sm.gauge()
+        np.testing.assert_array_equal(M, M.T)
+        assert np.linalg.norm(M - Mo) < 1e-8 * np.linalg.norm(Mo)
+        sm.set_gauge(Mo)
+        T = sm.apply_gauge(dl, dq).cpu().numpy()
+    assert _block_rel(T, S.base_factor(LZ, Q, Mo)).max() < 1e-9
+
+
+def test_gauge_fit_repeats_bit_for_bit_and_rejects_bad_calls():
+    sc = synth.shell_scene(n=50, m=2500, seed=35)
+    _, lz, q, sig = _gauge_data(sc)
+    _, lz2, q2, _ = _gauge_data(sc)
+    assert torch.equal(q, q2) and torch.equal(lz, lz2)
+    with surrogate.Surrogate(synth.surrogate_init(0), max_batch=64) as sm:
+        sm.fit_gauge(lz, q, sig)
+        M1 = sm.gauge()
+        sm.fit_gauge(lz, q, sig)
+        np.testing.assert_array_equal(sm.gauge(), M1)
+        with pytest.raises(ccov.CcovError) as e:             # not symmetric
+            bad = M1.copy()
+            bad[0, 1] += 1.0
+            sm.set_gauge(bad)
+        assert e.value.status == ccov.CCOV_ERR_INVALID_ARG
+        with pytest.raises(ccov.CcovError) as e:             # one camera does not determine M
+            sm.fit_gauge(lz[:1].contiguous(), q[:1].contiguous(), sig[:1].contiguous())
+        assert e.value.status == ccov.CCOV_ERR_DEGENERATE
+        np.testing.assert_array_equal(sm.gauge(), M1)        # a failed fit keeps the matrix
+    with ccov.from_scene(sc) as ctx:                         # gauge rows before ccov_nullspace
+        ctx.ccov_information()
+        _, lz3 = surrogate.features(ctx)
+        with pytest.raises(ccov.CcovError) as e:
+            surrogate.gauge_rows(ctx, lz3)
+        assert e.value.status == ccov.CCOV_ERR_INVALID_ARG
+
+
+def _train_with_gauge(scenes, steps=600, batch=512, seed=1):
+    """Features, gauge fit, targets around the base, and training; returns the model."""
+    F, LZ, Q, SG = [], [], [], []
+    for sc in scenes:
+        f, lz, q, sig = _gauge_data(sc)
         F.append(f)
-        TG.append(surrogate.targets(lz, sig))
-    F, TG = torch.cat(F), torch.cat(TG)
-    idx = torch.from_numpy(synth.minibatch_indices(F.shape[0], 512, 600, seed=1)).cuda()
-    with surrogate.Surrogate(synth.surrogate_init(0), max_batch=512) as sm:
-        sm.fit_normalization(F, TG)
-        losses = sm.train(F, TG, idx, 1e-3)
-        assert losses[-50:].mean() < 0.2 * losses[:10].mean()
-        kl_sur, kl_loc, kl_mean = [], [], []
-        mu_t = sm.normalization()[128:173].astype(np.float64)
-        for sc in test:
-            f, lz, sig = _scene_data(sc)
-            pred = sm.predict(f, lz).cpu().numpy()
-            truth, L = sig.cpu().numpy(), lz.cpu().numpy()
-            kl_sur.append(S.gaussian_kl(pred, truth))
-            kl_loc.append(S.gaussian_kl(S.covariance_from_output(np.zeros((sc.n, 45)), L), truth))
-            kl_mean.append(S.gaussian_kl(S.covariance_from_output(np.tile(mu_t, (sc.n, 1)), L), truth))
-    kl_sur, kl_loc, kl_mean = (np.median(np.concatenate(k)) for k in (kl_sur, kl_loc, kl_mean))
-    assert kl_sur < 0.01 * kl_loc
-    assert kl_sur < 0.6 * kl_mean
+        LZ.append(lz)
+        Q.append(q)
+        SG.append(sig)
+    F, LZ, Q, SG = (torch.cat(a) for a in (F, LZ, Q, SG))
+    sm = surrogate.Surrogate(synth.surrogate_init(0), max_batch=batch)
+    sm.fit_gauge(LZ, Q, SG)
+    TG = surrogate.targets(sm.apply_gauge(LZ, Q), SG)
+    idx = torch.from_numpy(synth.minibatch_indices(F.shape[0], batch, steps, seed=seed)).cuda()
+    sm.fit_normalization(F, TG)
+    losses = sm.train(F, TG, idx, 1e-3)
+    return sm, losses
+
+
+def _kl_table(sm, scenes, exact=None):
+    """Median and p90 Gaussian KL over the scenes' cameras of the network's
+    prediction, of the base alone, of Z_ii^-1 and of a constant correction
+    around the base."""
+    out = {k: [] for k in ("surrogate", "base", "local", "mean")}
+    mu_t = sm.normalization()[128:173].astype(np.float64)
+    for k, sc in enumerate(scenes):
+        if exact is None:
+            f, lz, q, sig = _gauge_data(sc)
+        else:
+            f, lz, q, sig = exact[k]
+        T = sm.apply_gauge(lz, q)
+        pred = sm.predict(f, T).cpu().numpy()
+        truth, L, Tn = sig.cpu().numpy(), lz.cpu().numpy(), T.cpu().numpy()
+        zero = np.zeros((sc.n, 45))
+        out["surrogate"].append(S.gaussian_kl(pred, truth))
+        out["base"].append(S.gaussian_kl(S.covariance_from_output(zero, Tn), truth))
+        out["local"].append(S.gaussian_kl(S.covariance_from_output(zero, L), truth))
+        hs = S.head_scale(f.cpu().numpy().astype(np.float64))[:, None]
+        out["mean"].append(S.gaussian_kl(S.covariance_from_output(hs * mu_t, Tn), truth))
+    return {k: (np.median(np.concatenate(v)), np.percentile(np.concatenate(v), 90)) for k, v in out.items()}
+
+
+def test_trained_surrogate_gains_over_the_local_block():
+    """Trained on exact blocks of small scenes, around the base with the
+    fitted gauge term, the network predicts held-out scenes' blocks far
+    better than Z_ii^-1 (the covariance with every other camera fixed, which
+    costs the same) and better than the base alone, in the unit-free
+    Gaussian KL measure."""
+    train = synth.batch_scenes(k=60, n_lo=30, n_hi=120, pts_per_cam=60, seed=41)
+    test = synth.batch_scenes(k=4, n_lo=60, n_hi=120, pts_per_cam=60, seed=42)
+    sm, losses = _train_with_gauge(train)
+    with sm:
+        # around the base most of the target variance is scene-to-scene
+        # scatter that no per-camera feature explains: the loss falls, but by
+        # less than around Z_ii^-1 (2000 training scenes: 1.38 -> 0.69)
+        assert losses[-50:].mean() < 0.9 * losses[:10].mean()
+        kl = _kl_table(sm, test)
+    print("KL on held-out 60-120-camera scenes (median, p90):", kl)
+    assert kl["surrogate"][0] < 0.01 * kl["local"][0]
+    assert kl["base"][0] < 0.05 * kl["local"][0]
+    assert kl["surrogate"][0] < kl["base"][0]
+
+
+def test_surrogate_trained_on_50_500_cameras_gains_at_4000():
+    """Trained on scenes of 50-500 cameras (the training law of the surrogate
+    workload), evaluated on a 4000-camera shell scene against its exact
+    blocks (mixed path): the median and the p90 KL of the prediction are far
+    below those of Z_ii^-1."""
+    train = [synth.training_scene(sp) for sp in synth.training_scene_specs(40, seed=6)]
+    sm, _ = _train_with_gauge(train, steps=800)
+    sc = synth.workload("shell4k")
+    with ccov.from_scene(sc, precision=ccov.CCOV_PREC_MIXED) as ctx:
+        ctx.ccov_information()
+        f, lz = surrogate.features(ctx)
+        ctx.ccov_nullspace()
+        q = surrogate.gauge_rows(ctx, lz)
+        sig = torch.empty((sc.n, 9, 9), dtype=torch.float64, device="cuda")
+        ctx.ccov_schur()
+        ctx.ccov_nullspace()
+        ctx.ccov_covariance(out=sig)
+    with sm:
+        kl = _kl_table(sm, [sc], exact=[(f, lz, q, sig)])
+    print("KL at 4000 cameras (median, p90):", kl)
+    assert kl["surrogate"][0] < 0.2 * kl["local"][0]
+    assert kl["surrogate"][1] < 0.2 * kl["local"][1]
 
 
 def test_sample_index_outside_the_training_set_is_rejected():

@@ -151,6 +151,7 @@ def test_features_layout():
     assert f[3, 0] == pytest.approx(Z[3, 0, 1] / (d[3, 0] * d[3, 1]), rel=1e-14)   # C_01
     assert f[3, 35] == pytest.approx(Z[3, 7, 8] / (d[3, 7] * d[3, 8]), rel=1e-14)  # C_78
     np.testing.assert_allclose(f[:, 36:45], np.log(d), rtol=1e-14)
+    np.testing.assert_allclose(f[:, 48], 10.0 / np.sqrt(8.0), rtol=1e-15)
     assert np.all(f[:, 50:] == 0)
     assert np.all(np.abs(f[:, :36]) < 1)   # off-diagonal correlations of an SPD block
 
@@ -289,3 +290,26 @@ def test_gauge_term_explains_the_exact_blocks():
     kl_base = S.gaussian_kl(Ti.transpose(0, 2, 1) @ Ti, sig)
     kl_local = S.gaussian_kl(Zinv, sig)
     assert np.median(kl_base) < 0.02 * np.median(kl_local)
+
+
+def test_predict_head_scale_closed_form():
+    """Output weights zero: y = 0, so t = s mu_t.  With mu_t = log 2 on the
+    diagonal entries and zero elsewhere, L = 2^s I and Sigma_hat =
+    4^s (T T^T)^-1 for each camera's own s (1 where feature 48 is not
+    positive)."""
+    rng = np.random.default_rng(4)
+    n = 6
+    p = _params(2)
+    p[6] = np.zeros_like(p[6])
+    p[7] = np.zeros_like(p[7])
+    f = rng.normal(size=(n, 64))
+    f[:, 48] = [0.2, 0.7, 1.3, -1.0, 0.0, 2.0]
+    A = rng.normal(size=(n, 9, 9))
+    T = np.linalg.cholesky(A @ A.transpose(0, 2, 1) + 9 * np.eye(9))
+    mu_t = np.concatenate([np.full(9, np.log(2.0)), np.zeros(36)])
+    norm = (np.zeros(64), np.ones(64), mu_t, np.ones(45))
+    got = S.predict(p, f, T, norm)
+    s = np.array([0.2, 0.7, 1.3, 1.0, 1.0, 2.0])
+    base = np.linalg.inv(T @ T.transpose(0, 2, 1))
+    want = (4.0 ** s)[:, None, None] * base
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
