@@ -18,7 +18,8 @@
 // shifts: no FP64 arithmetic in the O(N^3) part.
 //
 // Blocking: 128-column sub-panels factored and inverted one at a time, with
-// the big trailing updates applied for two sub-panels at once (K = 256).  The
+// the big trailing updates applied for four sub-panels at once (K = 512; two,
+// K = 256, for s = 6 and in the grouped batch).  The
 // diagonal blocks are factored and inverted by one CTA in double-single
 // arithmetic.  The triangular inverse runs on a second stream, each pair of
 // row blocks as soon as the Cholesky has finished the same pair of columns,
@@ -50,14 +51,15 @@ constexpr int kCBox = kBM * 16 * 8;                        // 16 KB: 16 int64 co
 constexpr int kCTile = kCBox;                              // 16 KB: a quarter of the result tile, staged for TMA
 constexpr int kFX = 42;                                    // fixed point of X = L^-1
 constexpr int kFL = 60;                                    // fixed point of Z_s and L
-constexpr int kKMax = 256;
+constexpr int kKMax = 512;                                 // digit columns of the per-scene buffers
+constexpr int kKMaxGroup = 256;                            // of the grouped batch's buffers
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;              // producer, MMA, epilogue warps
 constexpr int kEpiCols = kBN / (kEpiWarps / 4);            // tile columns per epilogue thread
 
 struct MixedState {
     int s = 5;
-    __nv_bfloat16* digP = nullptr;   // s digit planes of Np rows x 256, layout of blk_off
+    __nv_bfloat16* digP = nullptr;   // s digit planes of Np rows x kKMax, layout of blk_off
     __nv_bfloat16* digQ = nullptr;
     int* expP = nullptr;             // Np
     int* expQ = nullptr;             // Np
@@ -76,7 +78,7 @@ struct MixedState {
     long long skip_fill = -1;        // test hook: a pipeline fill the GEMM producer leaves out
     cudaStream_t side = nullptr;     // triangular inverse, lowest priority
     cudaStream_t hi = nullptr;       // Cholesky (the critical path), highest priority
-    std::vector<cudaEvent_t> ev;     // [0] fork, [1] inverse done, [2] Cholesky done, [3 + k] pair k final
+    std::vector<cudaEvent_t> ev;     // [0] fork, [1] inverse done, [2] Cholesky done, [3 + p] group at p final
 
     void swap_sets() {
         std::swap(digP, digP2);
@@ -114,13 +116,19 @@ __host__ __device__ __forceinline__ int64_t blk_off(int plane, int r, int k, int
 // (columns 64 (S + g - cap)).  With the B planes side by side in shared
 // memory, plane a then meets all B planes in one MMA of N = 64 (S - a)
 // (split at N = 256), whose output columns land on the orders a .. S-1.
+// With S = 2 cap + 1 (S = 5, K = 512) the second accumulator of the lowest
+// kept order, g = S - 1, takes cap + 1 products: its sum (below 1.5 2^24)
+// may round, by at most a few units of that order per K-step.  Its weight
+// is 2^-8(S-1) of the leading order's, so over K = 512 the rounding stays
+// near 2^-49 of the largest result, against the 2^-39 of the orders that
+// the split drops; every other accumulator stays exact.
 template <int S, int K>
 struct Slots {
     static constexpr int cap = 1024 / K;
     static constexpr int extra = S > cap ? S - cap : 0;
     static constexpr int total = S + extra;
     static_assert(total * kBN <= 512, "TMEM columns");
-    static_assert(S <= 2 * cap, "two accumulator levels at most");
+    static_assert(S <= 2 * cap + (K == 512 ? 1 : 0), "two accumulator levels at most");
     // digit products summed in accumulator sl (main accumulators of the
     // orders 0..S-1, then the second ones of the orders cap..S-1)
     __host__ __device__ static constexpr int products(int sl) {
@@ -1129,10 +1137,10 @@ bool make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t cols, in
 
 // The B-operand view of a digit buffer: (128 elements of an 8-row group,
 // 8 groups, 2 halves of a 128-row block, s planes, K slice x row block).
-bool make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) {
+bool make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np, int kmax) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[5] = {128, 8, 2, (cuuint64_t)s, (cuuint64_t)(kKMax / 16) * (cuuint64_t)(Np / 128)};
+    cuuint64_t dims[5] = {128, 8, 2, (cuuint64_t)s, (cuuint64_t)(kmax / 16) * (cuuint64_t)(Np / 128)};
     cuuint64_t strides[4] = {256, 2048, 4096, (cuuint64_t)s * 4096};
     cuuint32_t box[5] = {128, 8, 1, (cuuint32_t)s, 1};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
@@ -1203,7 +1211,13 @@ void launch_ozaki(Ctx& c, int K, Buf ba, int a_row0, int M, Buf bb, int b_row0, 
     const GemmProblem* no_probs = nullptr;
     int no_n = 0;
 #define CCOV_OZ(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_, false>, mapC, mapB, g, no_probs, no_n)
-    if (K == 256) {
+    if (K == 512) {
+        switch (st.s) {
+            case 4: CCOV_OZ(4, 512); break;
+            case 5: CCOV_OZ(5, 512); break;
+            default: c.mixed_bad_launch = true; break;   // six digits: eight accumulators do not suffice
+        }
+    } else if (K == 256) {
         switch (st.s) {
             case 4: CCOV_OZ(4, 256); break;
             case 5: CCOV_OZ(5, 256); break;
@@ -1228,7 +1242,10 @@ void slice_rows(Ctx& c, int K, int rows, const long long* src, Buf b) {
     // one warp per 16 rows x 16 values
     const int grid = (int)(((int64_t)rows / 16 * (K / 16) * 32 + 255) / 256);
     if (rows % 16) { c.mixed_bad_launch = true; return; }
-    if (K == 256)
+    if (K == 512)
+        slice_rows_kernel<512><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex,
+                                                           c.d_flag);
+    else if (K == 256)
         slice_rows_kernel<256><<<grid, 256, 0, c.stream>>>(rows, src, c.Np, kFL, st.s, (int)c.Np, dst, ex,
                                                            c.d_flag);
     else
@@ -1243,7 +1260,10 @@ void slice_cols(Ctx& c, int K, int ncols, const long long* src, Buf b) {
     int* ex = b == BUF_P ? st.expP : st.expQ;
     const int grid = (ncols + 31) / 32;
     const size_t smem = (size_t)K * 33 * 8;
-    if (K == 256)
+    if (K == 512)
+        slice_cols_kernel<512><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex,
+                                                              c.d_flag);
+    else if (K == 256)
         slice_cols_kernel<256><<<grid, 256, smem, c.stream>>>(ncols, src, c.Np, kFX, st.s, (int)c.Np, dst, ex,
                                                               c.d_flag);
     else
@@ -1336,8 +1356,8 @@ cudaError_t grp_gemm(cudaStream_t st, int s, int K, const GemmProblem* probs, in
 
 // Kernel attributes of the mixed path (shared memory sizes) and the SM count.
 cudaError_t mixed_setup() {
-    cudaError_t a[6] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(),
-                        set_attr<4, 256>(), set_attr<5, 256>(), set_attr<6, 256>()};
+    cudaError_t a[8] = {set_attr<4, 128>(), set_attr<5, 128>(), set_attr<6, 128>(), set_attr<4, 256>(),
+                        set_attr<5, 256>(), set_attr<6, 256>(), set_attr<4, 512>(), set_attr<5, 512>()};
     for (cudaError_t x : a)
         if (x != cudaSuccess) return x;
     cudaError_t e;
@@ -1349,6 +1369,9 @@ cudaError_t mixed_setup() {
         return e;
     if ((e = cudaFuncSetAttribute(slice_cols_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   256 * 33 * 8)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(slice_cols_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  512 * 33 * 8)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(slice_cols_grouped<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   256 * 33 * 8)) != cudaSuccess)
@@ -1363,7 +1386,9 @@ bool mixed_make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t co
     return make_c_map(map, buf, rows, cols, ld);
 }
 
-bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) { return make_b_map(map, buf, s, Np); }
+bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) {
+    return make_b_map(map, buf, s, Np, kKMaxGroup);
+}
 
 int mixed_stages(int s) { return pick_stages(s); }
 
@@ -1400,14 +1425,14 @@ cudaError_t mixed_alloc(Ctx& c) {
     if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess) return e;
     if ((e = cudaStreamCreateWithPriority(&st.side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess) return e;
     if ((e = cudaStreamCreateWithPriority(&st.hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess) return e;
-    st.ev.assign(3 + (size_t)(Np / kNB + 1) / 2, nullptr);
+    st.ev.assign(3 + (size_t)(Np / kNB), nullptr);
     for (auto& ev : st.ev)
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
     if (c.d_Z && !make_c_map(&st.mapZ, reinterpret_cast<long long*>(c.d_Z), Np, Np, Np)) return cudaErrorInvalidValue;
     if (!make_c_map(&st.mapR, st.R, Np, Np, Np)) return cudaErrorInvalidValue;
-    if (!make_b_map(&st.mapBP, st.digP, st.s, Np) || !make_b_map(&st.mapBQ, st.digQ, st.s, Np) ||
-        !make_b_map(&st.mapBP2, st.digP2, st.s, Np) || !make_b_map(&st.mapBQ2, st.digQ2, st.s, Np) ||
-        !make_b_map(&st.mapBL, st.digL, st.s, Np))
+    if (!make_b_map(&st.mapBP, st.digP, st.s, Np, kKMax) || !make_b_map(&st.mapBQ, st.digQ, st.s, Np, kKMax) ||
+        !make_b_map(&st.mapBP2, st.digP2, st.s, Np, kKMax) || !make_b_map(&st.mapBQ2, st.digQ2, st.s, Np, kKMax) ||
+        !make_b_map(&st.mapBL, st.digL, st.s, Np, kKMax))
         return cudaErrorInvalidValue;
     return mixed_setup();
 }
@@ -1770,8 +1795,8 @@ void mixed_free(Ctx& c) {
 }
 
 // Z_s -> Q60, blocked Cholesky, blocked triangular inverse (both with the big
-// trailing updates for pairs of 128-column sub-panels, K = 256) and the
-// camera Gram blocks of the inverse.
+// trailing updates for groups of four 128-column sub-panels, K = 512) and
+// the camera Gram blocks of the inverse.
 cudaError_t mixed_factor_inverse(Ctx& c) {
     MixedState& st = *c.mixed;
     const int64_t Np = c.Np, nb = Np / kNB;
@@ -1791,41 +1816,54 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     }
     auto Zat = [&](int64_t row, int64_t col) { return Zq + row * Np + col; };
     auto Rat = [&](int64_t row, int64_t col) { return st.R + row * Np + col; };
-    // ---- Cholesky (context stream); event 2 + p / 2 once sub-panels p, p + 1 are final ----
-    auto pair_done = [&](int64_t p) { return cudaEventRecord(st.ev[3 + p / 2], c.stream); };
-    for (int64_t p = 0; p < nb; p += 2) {
-        const int64_t q = p + 1;
-        const int64_t kp = p * kNB, remP = Np - kp - kNB;
-        potrf_block(c, p);
-        if (remP <= 0) { pair_done(p); break; }
-        // L[rows > p, p] = A[rows > p, p] L_pp^-T
-        slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
-        launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_L, (int)kp, kNB, st.mapZ, (int)kp, (int)(kp + kNB), 0, 0, kFL,
-                     nullptr, st.expL);
-        // column strip q: A[rows >= q, q] -= L[rows >= q, p] L[q, p]^T
-        slice_rows(c, 128, (int)remP, Zat(kp + kNB, kp), BUF_P);
-        launch_ozaki(c, 128, BUF_P, 0, (int)remP, BUF_P, 0, kNB, st.mapZ, (int)(q * kNB), (int)(q * kNB), 0, 1,
+    // Sub-panels in groups of m = 4 (2 for six digits, whose eight
+    // accumulators hold K = 256 at most; fewer at the end): inside a group,
+    // each sub-panel's update of the group's later columns (K = 128); after
+    // it, one trailing update with all m sub-panels (K = 128 m).
+    const int64_t gmax = st.s <= 5 ? 4 : 2;
+    auto group_len = [&](int64_t p) {
+        const int64_t left = nb - p;
+        return left >= gmax ? gmax : (left >= 2 ? 2 : 1);
+    };
+    // ---- Cholesky (context stream); event 3 + p once the group at p is final ----
+    auto group_done = [&](int64_t p) { return cudaEventRecord(st.ev[3 + p], c.stream); };
+    for (int64_t p = 0; p < nb;) {
+        const int64_t m = group_len(p);
+        bool last = false;
+        for (int64_t j = p; j < p + m; ++j) {
+            const int64_t kj = j * kNB, remJ = Np - kj - kNB;
+            potrf_block(c, j);
+            if (remJ <= 0) { last = true; break; }
+            // L[rows > j, j] = A[rows > j, j] L_jj^-T
+            slice_rows(c, 128, (int)remJ, Zat(kj + kNB, kj), BUF_P);
+            launch_ozaki(c, 128, BUF_P, 0, (int)remJ, BUF_L, (int)kj, kNB, st.mapZ, (int)kj, (int)(kj + kNB), 0, 0,
+                         kFL, nullptr, st.expL);
+            // the group's later columns: A[rows > j, j+1 .. p+m-1] -= L[rows > j, j] L[j+1 .. p+m-1, j]^T
+            const int64_t w = p + m - 1 - j;
+            if (w > 0) {
+                slice_rows(c, 128, (int)remJ, Zat(kj + kNB, kj), BUF_P);
+                launch_ozaki(c, 128, BUF_P, 0, (int)remJ, BUF_P, 0, (int)(w * kNB), st.mapZ, (int)(kj + kNB),
+                             (int)(kj + kNB), 1, 1, kFL, nullptr, nullptr);
+            }
+        }
+        const int64_t kg = (p + m) * kNB, remG = Np - kg;
+        if (last || remG <= 0) { group_done(p); break; }
+        // trailing update with the group's sub-panels: A22 -= L[:, group] L[:, group]^T (lower tiles)
+        slice_rows(c, (int)(m * kNB), (int)remG, Zat(kg, p * kNB), BUF_P);
+        // the group's columns of L are final once the trailing update is
+        // issued: it only writes columns beyond the group
+        group_done(p);
+        launch_ozaki(c, (int)(m * kNB), BUF_P, 0, (int)remG, BUF_P, 0, (int)remG, st.mapZ, (int)kg, (int)kg, 1, 1,
                      kFL, nullptr, nullptr);
-        potrf_block(c, q);
-        const int64_t kq = q * kNB, remQ = Np - kq - kNB;
-        if (remQ <= 0) { pair_done(p); break; }
-        slice_rows(c, 128, (int)remQ, Zat(kq + kNB, kq), BUF_P);
-        launch_ozaki(c, 128, BUF_P, 0, (int)remQ, BUF_L, (int)kq, kNB, st.mapZ, (int)kq, (int)(kq + kNB), 0, 0, kFL,
-                     nullptr, st.expL);
-        // trailing update with both sub-panels: A22 -= L[:, p:q] L[:, p:q]^T (lower tiles)
-        slice_rows(c, 256, (int)remQ, Zat(kq + kNB, kp), BUF_P);
-        // columns p, q of L are final once the trailing update is issued: it
-        // only writes columns beyond q
-        pair_done(p);
-        launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_P, 0, (int)remQ, st.mapZ, (int)(kq + kNB), (int)(kq + kNB),
-                     1, 1, kFL, nullptr, nullptr);
+        p += m;
     }
     if (!c.capturing) cudaEventRecord(c.ev[3], c.stream);
     if ((e = cudaEventRecord(st.ev[2], c.stream)) != cudaSuccess) { c.stream = main_stream; return e; }
-    // ---- triangular inverse X = L^-1 (Q42), row blocks of 128, on a
-    // low-priority stream with the second digit buffers: row block pair k
-    // waits only for Cholesky pair k, so its GEMMs fill the GPU while the
-    // Cholesky (high priority) runs its serial diagonal blocks ----
+    // ---- triangular inverse X = L^-1 (Q42), row blocks of 128 in the same
+    // groups, on a low-priority stream with the second digit buffers: the
+    // group at p waits only for the Cholesky's group at p, so its GEMMs fill
+    // the GPU while the Cholesky (high priority) runs its serial diagonal
+    // blocks ----
     if ((e = cudaStreamWaitEvent(st.side, st.ev[0], 0)) != cudaSuccess) { c.stream = main_stream; return e; }
     c.stream = st.side;
     st.swap_sets();
@@ -1841,26 +1879,29 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
         gram_q_kernel<<<(int)((nc + kGW - 1) / kGW), kGT, 0, c.stream>>>(c.n, Np, k0, nc, st.R, c.d_Sig);
         c.launches++;
     };
-    for (int64_t p = 0; p < nb; p += 2) {
-        const int64_t q = p + 1;
-        const int64_t kp = p * kNB;
-        cudaStreamWaitEvent(c.stream, st.ev[3 + p / 2], 0);
-        finalize(p);
-        if (q >= nb) break;
-        const int64_t kq = q * kNB;
-        // R[q, :kp+128] -= L[q, p] X[p, :kp+128]
-        slice_cols(c, 128, (int)(kp + kNB), Rat(kp, 0), BUF_Q);
-        slice_rows(c, 128, kNB, Zat(kq, kp), BUF_P);
-        launch_ozaki(c, 128, BUF_P, 0, kNB, BUF_Q, 0, (int)(kp + kNB), st.mapR, 0, (int)kq, 0, 1, kFX, nullptr,
-                     st.expQ);
-        finalize(q);
-        const int64_t remQ = Np - kq - kNB, nc = kq + kNB;
-        if (remQ <= 0) break;
-        // R[rows > q, :nc] -= L[rows > q, p:q] X[p:q, :nc]  (K = 256)
-        slice_cols(c, 256, (int)nc, Rat(kp, 0), BUF_Q);
-        slice_rows(c, 256, (int)remQ, Zat(kq + kNB, kp), BUF_P);
-        launch_ozaki(c, 256, BUF_P, 0, (int)remQ, BUF_Q, 0, (int)nc, st.mapR, 0, (int)(kq + kNB), 0, 1, kFX,
+    for (int64_t p = 0; p < nb;) {
+        const int64_t m = group_len(p);
+        cudaStreamWaitEvent(c.stream, st.ev[3 + p], 0);
+        for (int64_t j = p; j < p + m; ++j) {
+            const int64_t kj = j * kNB, ncj = kj + kNB;
+            finalize(j);
+            // the group's later rows: R[j+1 .. p+m-1, :ncj] -= L[j+1 .. p+m-1, j] X[j, :ncj]
+            const int64_t w = p + m - 1 - j;
+            if (w > 0) {
+                slice_cols(c, 128, (int)ncj, Rat(kj, 0), BUF_Q);
+                slice_rows(c, 128, (int)(w * kNB), Zat(kj + kNB, kj), BUF_P);
+                launch_ozaki(c, 128, BUF_P, 0, (int)(w * kNB), BUF_Q, 0, (int)ncj, st.mapR, 0, (int)(kj + kNB), 0, 1,
+                             kFX, nullptr, st.expQ);
+            }
+        }
+        const int64_t kg = (p + m) * kNB, remG = Np - kg;
+        if (remG <= 0) break;
+        // R[rows >= kg, :kg] -= L[rows >= kg, group] X[group, :kg]  (K = 128 m)
+        slice_cols(c, (int)(m * kNB), (int)kg, Rat(p * kNB, 0), BUF_Q);
+        slice_rows(c, (int)(m * kNB), (int)remG, Zat(kg, p * kNB), BUF_P);
+        launch_ozaki(c, (int)(m * kNB), BUF_P, 0, (int)remG, BUF_Q, 0, (int)kg, st.mapR, 0, (int)kg, 0, 1, kFX,
                      nullptr, st.expQ);
+        p += m;
     }
     st.swap_sets();
     c.stream = main_stream;
@@ -1880,7 +1921,8 @@ static ccov_status test_gemm(int s, int K, int M, int N, const uint16_t* digA, c
                              const uint16_t* digB, const int* expB, int Fc, int sub, int lower, long long* C,
                              long long skip_fill, unsigned long long wait_ns) {
     using namespace ccov;
-    if (s < 4 || s > 6 || (K != 128 && K != 256) || M <= 0 || N <= 0 || M % kBM || N % (2 * kBN) || !digA ||
+    if (s < 4 || s > 6 || (K != 128 && K != 256 && K != 512) || (K == 512 && s > 5) || M <= 0 || N <= 0 ||
+        M % kBM || N % (2 * kBN) || !digA ||
         !digB || !C || wait_ns < 100000ull || wait_ns > 10000000000ull)
         return CCOV_ERR_INVALID_ARG;
     if (lower && N != M) return CCOV_ERR_INVALID_ARG;

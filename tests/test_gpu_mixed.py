@@ -112,6 +112,47 @@ def test_ozaki_gemm_overwrite_with_exponents_k256():
     assert np.array_equal(got, want)
 
 
+# K = 512 (the trailing updates of four sub-panels): eight accumulators.  With
+# four digits every one is exact; with five, the second accumulator of the
+# lowest order takes three products and may round once its sum passes 2^24,
+# which uniform digits never reach (their sums stay near 2^17).
+@pytest.mark.parametrize("s", [4, 5])
+def test_ozaki_gemm_k512_single_tile_bit_exact(s):
+    got, want = _run(s, 128, 128, 60, 1, 0, seed=30 + s, with_exp=False, K=512)
+    assert np.array_equal(got, want)
+
+
+def test_ozaki_gemm_k512_many_tiles_lower_and_exponents():
+    got, want = _run(5, 1280, 1280, 60, 1, 1, seed=33, with_exp=False, K=512)
+    assert np.array_equal(got, want)
+    got, want = _run(5, 384, 640, 42, 0, 0, seed=34, K=512)
+    assert np.array_equal(got, want)
+
+
+def test_ozaki_gemm_k512_extreme_digits_within_the_rounding_bound():
+    """Digits near +-128 with odd products, so that every accumulator sum
+    passes 2^23 and the lowest order's second one (three products) passes
+    2^24 with odd partial sums: every other order stays exact, and the
+    lowest order's rounding (at most one unit of 2 per accumulation into
+    an fp32 value below 2^25: 32 K-steps x 3 MMAs) enters T with weight 1,
+    shifted to Q60 by 2^(60 - 14 - 32)."""
+    s, K, M, N = 5, 512, 128, 128
+    dA = np.full((s, M, K), 128, dtype=np.int64)
+    dB = np.full((s, N, K), 128, dtype=np.int64)
+    dA[:, :, ::16] = 127                    # one odd product per 16-wide K step
+    dB[:, :, ::16] = 127
+    C0 = np.zeros((M, N), dtype=np.int64)
+    Cg = C0.copy()
+    fn = ccov.load().ccov_test_ozaki_gemm
+    ba, bb = _bf16_bits(dA), _bf16_bits(dB)
+    assert fn(s, K, M, N, ba.ctypes.data, None, bb.ctypes.data, None, 60, 1, 0, Cg.ctypes.data) == 0
+    want = _expected(dA, np.zeros(M, np.int64), dB, np.zeros(N, np.int64), s, 60, 1, 0, C0)
+    bound = 32 * 3 * 2 * 2 ** (60 - 14 - 32)
+    assert np.abs(Cg - want).max() <= bound
+    # the rest of T is exact: the error is below one unit of the next order up
+    assert np.abs(Cg - want).max() < 2 ** 8 * 2 ** (60 - 14 - 32)
+
+
 @pytest.mark.parametrize("case", ["ring20", "shell10", "shell30", "shell100", "shell300"])
 def test_mixed_covariance_vs_oracle(case):
     # shell10: one 128-column block; shell30: three (an odd count: the last
