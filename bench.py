@@ -7,13 +7,16 @@ workload is the synthetic 4000-camera shell scene (400k points, track length
 1 + Geometric(1/7), about 3.2M observations, reduced camera matrix
 36000 x 36000).  For the mixed form the line also carries one pass of the
 plain FP64 GPU form on the same scene (`vs_fp64_gpu`: its time and the mixed
-blocks' relative Frobenius error against it).  `value` = cameras / s with the inputs resident on the device;
+blocks' relative Frobenius error against it), and a short timing of the
+batched form below (`batch256`; `--no-batch-extra` leaves it out).  `value` =
+cameras / s with the inputs resident on the device;
 `e2e` = the same through the C ABI with host buffers (host-to-device upload and
 the device-to-host copy of the 9x9 blocks inside every timed step).
 
 `--workload surrogate` trains the learned surrogate on exact blocks of
 2000 scenes (n ~ U{50..500}) and times its prediction on the 4000-camera
-scene (value = cameras / s of ccov_information + features + prediction).
+scene (value = cameras / s of ccov_information + features + the nullspace
+rows + the gauge term of the base + prediction).
 
 `--workload batch256` times the batched form instead: 256 independent
 sub-reconstructions (n ~ U{10..300} cameras, 100 points per camera, track
@@ -67,6 +70,8 @@ def parse():
     ap.add_argument("--cpu-sample-cams", type=int, default=900)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-batch-extra", action="store_true",
+                    help="leave the batched form's figure out of the default (4000-camera) line")
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: the same as --steps")
     ap.add_argument("--surr-scenes", type=int, default=2000)
     ap.add_argument("--surr-epochs", type=int, default=30)
@@ -432,6 +437,9 @@ def run_ours(args):
                                "max_norm_err_per_block": float(errs["norm_err"].max()),
                                "max_pose_err_per_block": float(errs["pose_err"].max()),
                                "max_intr_err_per_block": float(errs["intr_err"].max())}
+    if (world == 1 and args.workload == "shell4k" and prec == ccov.CCOV_PREC_MIXED
+            and not args.no_batch_extra):
+        line["batch256"] = batch_extra(dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub, dt = cpu_oracle_sample(scene, args.cpu_sample_cams)
         line["cpu_baseline"] = {"value": sub.n / dt, "unit": UNIT, "cores": os.cpu_count(),
@@ -446,6 +454,45 @@ def run_ours(args):
 
 
 BATCH_K = 256
+
+
+def batch_extra(dev, stream, warmup: int = 3, steps: int = 5):
+    """The batched form (`--workload batch256`: 256 scenes of 10-300 cameras,
+    mixed, grouped launches replayed as one graph) timed briefly, so that the
+    default line carries its figure too: device-resident inputs, CUDA events
+    around `steps` replays after `warmup`."""
+    import numpy as np
+    import torch
+
+    from paper_1808_02414_gb300 import ccov
+    scenes = batch_workload()
+    ctxs, outs = [], []
+    for sc in scenes:
+        rec = sc.obs_records()
+        ctxs.append(ccov.Context(torch.from_numpy(sc.cams).to(dev), torch.from_numpy(sc.pts).to(dev),
+                                 torch.from_numpy(rec.view(np.uint8)).to(dev), sc.sigma,
+                                 precision=ccov.CCOV_PREC_MIXED))
+        outs.append(torch.empty((sc.n, 9, 9), dtype=torch.float64, device=dev))
+    try:
+        with ccov.Batch(ctxs, outs) as b:
+            info = b.info()
+            for _ in range(warmup):
+                b.run(stream.cuda_stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                b.run(stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+    finally:
+        for c in ctxs:
+            c.close()
+    ms = e0.elapsed_time(e1) / steps
+    cams = sum(sc.n for sc in scenes)
+    return {"value": cams / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "scenes": len(scenes), "cameras": cams, "launches_per_step": int(info["launches"]),
+            "form": "grouped launches, one CUDA graph replay per step (bench.py --workload batch256)"}
 
 
 def batch_workload():
