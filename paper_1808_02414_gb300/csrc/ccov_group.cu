@@ -158,7 +158,7 @@ struct GemmStep {
 
 // ---------------------------------------------------------------------------
 // Plan building: the same sequence as mixed_factor_inverse, per scene, merged
-// by (sub-panel pair p, sub-step).
+// by (window of sub-panel groups, sub-panel, sub-step).
 
 namespace {
 
@@ -193,7 +193,7 @@ static cudaError_t plan_ops(GroupPlan& P) {
     const int k = P.k, s = P.s;
     int64_t max_nb = 0;
     for (int q = 0; q < k; ++q) max_nb = std::max(max_nb, P.nb[q]);
-    P.ev.assign(3 + (size_t)(max_nb + 1) / 2, nullptr);
+    P.ev.assign(3 + (size_t)max_nb, nullptr);
 
     auto add_slice_rows = [&](int side, int K, Step<SliceRowsP>& st) {
         if (st.rec.empty()) return;
@@ -265,49 +265,76 @@ static cudaError_t plan_ops(GroupPlan& P) {
         P.ops.push_back(o);
     }
     const int kN = kNB;
-    for (int64_t p = 0; p < max_nb; p += 2) {
-        const int64_t kp = p * kN, q1 = p + 1, kq = q1 * kN;
-        std::vector<PotrfP> pot_p, pot_q;
-        Step<SliceRowsP> s1, s2, s3, s4;
-        GemmStep g1, g2, g3, g4;
-        for (int q = 0; q < k; ++q) {
-            if (P.nb[q] <= p) continue;
-            const int64_t Npq = P.Np[q], remP = Npq - kp - kN;
-            pot_p.push_back({P.Zq(q), Npq, kp, P.D(G_L, q), P.E(G_L, q), s});
-            if (remP <= 0) continue;
-            const long long* colp = P.Zq(q) + (kp + kN) * Npq + kp;
-            s1.add(srows(q, (int)remP, colp, G_P), grp_slice_rows_blocks(128, (int)remP));
-            gemm_add(g1, problem(P, q, 128, G_P, 0, (int)remP, G_L, (int)kp, kN, false, (int)kp, (int)(kp + kN), 0, 0,
-                                 kFLq, nullptr, P.E(G_L, q)));
-            s2.add(srows(q, (int)remP, colp, G_P), grp_slice_rows_blocks(128, (int)remP));
-            gemm_add(g2, problem(P, q, 128, G_P, 0, (int)remP, G_P, 0, kN, false, (int)kq, (int)kq, 0, 1, kFLq,
-                                 nullptr, nullptr));
-            pot_q.push_back({P.Zq(q), Npq, kq, P.D(G_L, q), P.E(G_L, q), s});
-            const int64_t remQ = Npq - kq - kN;
-            if (remQ <= 0) continue;
-            const long long* colq = P.Zq(q) + (kq + kN) * Npq + kq;
-            s3.add(srows(q, (int)remQ, colq, G_P), grp_slice_rows_blocks(128, (int)remQ));
-            gemm_add(g3, problem(P, q, 128, G_P, 0, (int)remQ, G_L, (int)kq, kN, false, (int)kq, (int)(kq + kN), 0, 0,
-                                 kFLq, nullptr, P.E(G_L, q)));
-            s4.add(srows(q, (int)remQ, P.Zq(q) + (kq + kN) * Npq + kp, G_P), grp_slice_rows_blocks(256, (int)remQ));
-            gemm_add(g4, problem(P, q, 256, G_P, 0, (int)remQ, G_P, 0, (int)remQ, false, (int)(kq + kN), (int)(kq + kN),
-                                 1, 1, kFLq, nullptr, nullptr));
+    // Sub-panel groups as in mixed_factor_inverse: per scene, m = its
+    // mixed_group_max (4 or 2) while that many are left, else 2, else 1.
+    // Group starts lie in windows of gmax sub-panels (the largest group of
+    // any scene); slot j of a window holds, for every scene with sub-panel
+    // j, exactly the single-scene operations of j, so each scene's
+    // arithmetic (and result) is the single-scene one.
+    int64_t gmax = 2;
+    for (int q = 0; q < k; ++q) gmax = std::max(gmax, mixed_group_max(s, P.nb[q]));
+    auto group_of = [&](int64_t nbq, int64_t j, int64_t& gs, int64_t& m) {
+        const int64_t gq = mixed_group_max(s, nbq);
+        gs = 0;
+        for (;;) {
+            const int64_t left = nbq - gs;
+            m = left >= gq ? gq : (left >= 2 ? 2 : 1);
+            if (j < gs + m) return;
+            gs += m;
         }
-        // single-scene order: potrf p; slice; L panel p; slice; strip q;
-        // potrf q; slice; L panel q; slice (K = 256); [pair final]; trailing
-        add_potrf(pot_p);
-        add_slice_rows(0, 128, s1);
-        add_gemm(0, 128, g1);
-        add_slice_rows(0, 128, s2);
-        add_gemm(0, 128, g2);
-        add_potrf(pot_q);
-        add_slice_rows(0, 128, s3);
-        add_gemm(0, 128, g3);
-        add_slice_rows(0, 256, s4);
-        Op rec;
-        rec.kind = OP_RECORD; rec.ev = 3 + (int)(p / 2);
-        P.ops.push_back(rec);
-        add_gemm(0, 256, g4);
+    };
+    const int kKs[3] = {128, 256, 512};
+    auto kidx = [&](int64_t K) { return K == 128 ? 0 : (K == 256 ? 1 : 2); };
+    for (int64_t p = 0; p < max_nb; p += gmax) {
+        for (int64_t j = p; j < p + gmax; ++j) {
+            const int64_t kj = j * kN;
+            std::vector<PotrfP> pot;
+            Step<SliceRowsP> s1, s2, s4[3];
+            GemmStep g1, g2, g4[3];
+            for (int q = 0; q < k; ++q) {
+                if (P.nb[q] <= j) continue;
+                const int64_t Npq = P.Np[q], remJ = Npq - kj - kN;
+                int64_t gs, m;
+                group_of(P.nb[q], j, gs, m);
+                pot.push_back({P.Zq(q), Npq, kj, P.D(G_L, q), P.E(G_L, q), s});
+                if (remJ <= 0) continue;
+                const long long* colj = P.Zq(q) + (kj + kN) * Npq + kj;
+                // L[rows > j, j] = A[rows > j, j] L_jj^-T
+                s1.add(srows(q, (int)remJ, colj, G_P), grp_slice_rows_blocks(128, (int)remJ));
+                gemm_add(g1, problem(P, q, 128, G_P, 0, (int)remJ, G_L, (int)kj, kN, false, (int)kj, (int)(kj + kN), 0,
+                                     0, kFLq, nullptr, P.E(G_L, q)));
+                // the group's later columns
+                const int64_t w = gs + m - 1 - j;
+                if (w > 0) {
+                    s2.add(srows(q, (int)remJ, colj, G_P), grp_slice_rows_blocks(128, (int)remJ));
+                    gemm_add(g2, problem(P, q, 128, G_P, 0, (int)remJ, G_P, 0, (int)(w * kN), false, (int)(kj + kN),
+                                         (int)(kj + kN), 1, 1, kFLq, nullptr, nullptr));
+                }
+                // after the group's last sub-panel: its trailing update (K = 128 m)
+                const int64_t kg = (gs + m) * kN, remG = Npq - kg;
+                if (j == gs + m - 1 && remG > 0) {
+                    const int K = (int)(m * kN), x = kidx(K);
+                    s4[x].add(srows(q, (int)remG, P.Zq(q) + kg * Npq + gs * kN, G_P),
+                              grp_slice_rows_blocks(K, (int)remG));
+                    gemm_add(g4[x], problem(P, q, K, G_P, 0, (int)remG, G_P, 0, (int)remG, false, (int)kg, (int)kg, 1,
+                                            1, kFLq, nullptr, nullptr));
+                }
+            }
+            add_potrf(pot);
+            add_slice_rows(0, 128, s1);
+            add_gemm(0, 128, g1);
+            add_slice_rows(0, 128, s2);
+            add_gemm(0, 128, g2);
+            for (int x = 0; x < 3; ++x) add_slice_rows(0, kKs[x], s4[x]);
+            if (j == p + gmax - 1) {
+                // the window's columns of L are final once its last trailing
+                // updates are issued: they only write columns beyond it
+                Op rec;
+                rec.kind = OP_RECORD; rec.ev = 3 + (int)(p / gmax);
+                P.ops.push_back(rec);
+            }
+            for (int x = 0; x < 3; ++x) add_gemm(0, kKs[x], g4[x]);
+        }
     }
     {
         Op rec;
@@ -322,54 +349,58 @@ static cudaError_t plan_ops(GroupPlan& P) {
         o.kind = OP_IDENT; o.side = 1; o.k = k; o.rec = P.put(id.rec); o.pre = P.put(id.pre); o.blocks = id.pre.back();
         P.ops.push_back(o);
     }
-    for (int64_t p = 0; p < max_nb; p += 2) {
-        const int64_t kp = p * kN, q1 = p + 1, kq = q1 * kN;
-        Op w;
-        w.kind = OP_WAIT; w.side = 1; w.ev = 3 + (int)(p / 2);
-        P.ops.push_back(w);
-        Step<SliceColsP> c1, c2, c3, c5;
-        Step<SliceRowsP> r2, r5;
-        Step<GramP> gr1, gr3;
-        GemmStep f1, m2, f3, m5;
-        for (int q = 0; q < k; ++q) {
-            if (P.nb[q] <= p) continue;
-            const int64_t Npq = P.Np[q];
-            // finalize(p): X[p, :kp+128] = L_pp^-1 R[p, :kp+128], Gram blocks
-            c1.add(scols(q, (int)(kp + kN), P.Rq(q) + kp * Npq, G_Q2), grp_slice_cols_blocks((int)(kp + kN)));
-            gemm_add(f1, problem(P, q, 128, G_L, (int)kp, kN, G_Q2, 0, (int)(kp + kN), true, 0, (int)kp, 0, 0, kFXq,
-                                 P.E(G_L, q), P.E(G_Q2, q)));
-            gr1.add({P.n[q], Npq, kp, kp + kN, P.Rq(q), P.sup.d_Sig + 81 * P.co[q]}, grp_gram_blocks(kp + kN));
-            if (q1 >= P.nb[q]) continue;
-            // R[q, :kp+128] -= L[q, p] X[p, :kp+128]
-            c2.add(scols(q, (int)(kp + kN), P.Rq(q) + kp * Npq, G_Q2), grp_slice_cols_blocks((int)(kp + kN)));
-            r2.add(srows(q, kN, P.Zq(q) + kq * Npq + kp, G_P2), grp_slice_rows_blocks(128, kN));
-            gemm_add(m2, problem(P, q, 128, G_P2, 0, kN, G_Q2, 0, (int)(kp + kN), true, 0, (int)kq, 0, 1, kFXq,
-                                 nullptr, P.E(G_Q2, q)));
-            // finalize(q)
-            c3.add(scols(q, (int)(kq + kN), P.Rq(q) + kq * Npq, G_Q2), grp_slice_cols_blocks((int)(kq + kN)));
-            gemm_add(f3, problem(P, q, 128, G_L, (int)kq, kN, G_Q2, 0, (int)(kq + kN), true, 0, (int)kq, 0, 0, kFXq,
-                                 P.E(G_L, q), P.E(G_Q2, q)));
-            gr3.add({P.n[q], Npq, kq, kq + kN, P.Rq(q), P.sup.d_Sig + 81 * P.co[q]}, grp_gram_blocks(kq + kN));
-            const int64_t remQ = Npq - kq - kN, nc = kq + kN;
-            if (remQ <= 0) continue;
-            // R[rows > q, :nc] -= L[rows > q, p:q] X[p:q, :nc]  (K = 256)
-            c5.add(scols(q, (int)nc, P.Rq(q) + kp * Npq, G_Q2), grp_slice_cols_blocks((int)nc));
-            r5.add(srows(q, (int)remQ, P.Zq(q) + (kq + kN) * Npq + kp, G_P2), grp_slice_rows_blocks(256, (int)remQ));
-            gemm_add(m5, problem(P, q, 256, G_P2, 0, (int)remQ, G_Q2, 0, (int)nc, true, 0, (int)(kq + kN), 0, 1, kFXq,
-                                 nullptr, P.E(G_Q2, q)));
+    for (int64_t p = 0; p < max_nb; p += gmax) {
+        Op wt;
+        wt.kind = OP_WAIT; wt.side = 1; wt.ev = 3 + (int)(p / gmax);
+        P.ops.push_back(wt);
+        for (int64_t j = p; j < p + gmax; ++j) {
+            const int64_t kj = j * kN, ncj = kj + kN;
+            Step<SliceColsP> c1, c2, c5[3];
+            Step<SliceRowsP> r2, r5[3];
+            Step<GramP> gr1;
+            GemmStep f1, m2, m5[3];
+            for (int q = 0; q < k; ++q) {
+                if (P.nb[q] <= j) continue;
+                const int64_t Npq = P.Np[q];
+                int64_t gs, m;
+                group_of(P.nb[q], j, gs, m);
+                // finalize(j): X[j, :ncj] = L_jj^-1 R[j, :ncj], Gram blocks
+                c1.add(scols(q, (int)ncj, P.Rq(q) + kj * Npq, G_Q2), grp_slice_cols_blocks((int)ncj));
+                gemm_add(f1, problem(P, q, 128, G_L, (int)kj, kN, G_Q2, 0, (int)ncj, true, 0, (int)kj, 0, 0, kFXq,
+                                     P.E(G_L, q), P.E(G_Q2, q)));
+                gr1.add({P.n[q], Npq, kj, ncj, P.Rq(q), P.sup.d_Sig + 81 * P.co[q]}, grp_gram_blocks(ncj));
+                // the group's later rows: R[j+1 .. gs+m-1, :ncj] -= L[j+1 .. gs+m-1, j] X[j, :ncj]
+                const int64_t w = gs + m - 1 - j;
+                if (w > 0) {
+                    c2.add(scols(q, (int)ncj, P.Rq(q) + kj * Npq, G_Q2), grp_slice_cols_blocks((int)ncj));
+                    r2.add(srows(q, (int)(w * kN), P.Zq(q) + (kj + kN) * Npq + kj, G_P2),
+                           grp_slice_rows_blocks(128, (int)(w * kN)));
+                    gemm_add(m2, problem(P, q, 128, G_P2, 0, (int)(w * kN), G_Q2, 0, (int)ncj, true, 0, (int)(kj + kN),
+                                         0, 1, kFXq, nullptr, P.E(G_Q2, q)));
+                }
+                // after the group: R[rows >= kg, :kg] -= L[rows >= kg, group] X[group, :kg]  (K = 128 m)
+                const int64_t kg = (gs + m) * kN, remG = Npq - kg;
+                if (j == gs + m - 1 && remG > 0) {
+                    const int K = (int)(m * kN), x = kidx(K);
+                    c5[x].add(scols(q, (int)kg, P.Rq(q) + gs * kN * Npq, G_Q2), grp_slice_cols_blocks((int)kg));
+                    r5[x].add(srows(q, (int)remG, P.Zq(q) + kg * Npq + gs * kN, G_P2),
+                              grp_slice_rows_blocks(K, (int)remG));
+                    gemm_add(m5[x], problem(P, q, K, G_P2, 0, (int)remG, G_Q2, 0, (int)kg, true, 0, (int)kg, 0, 1,
+                                            kFXq, nullptr, P.E(G_Q2, q)));
+                }
+            }
+            add_slice_cols(1, 128, c1);
+            add_gemm(1, 128, f1);
+            add_gram(gr1);
+            add_slice_cols(1, 128, c2);
+            add_slice_rows(1, 128, r2);
+            add_gemm(1, 128, m2);
+            for (int x = 0; x < 3; ++x) {
+                add_slice_cols(1, kKs[x], c5[x]);
+                add_slice_rows(1, kKs[x], r5[x]);
+                add_gemm(1, kKs[x], m5[x]);
+            }
         }
-        add_slice_cols(1, 128, c1);
-        add_gemm(1, 128, f1);
-        add_gram(gr1);
-        add_slice_cols(1, 128, c2);
-        add_slice_rows(1, 128, r2);
-        add_gemm(1, 128, m2);
-        add_slice_cols(1, 128, c3);
-        add_gemm(1, 128, f3);
-        add_gram(gr3);
-        add_slice_cols(1, 256, c5);
-        add_slice_rows(1, 256, r5);
-        add_gemm(1, 256, m5);
     }
     Op rec;
     rec.kind = OP_RECORD; rec.side = 1; rec.ev = 2;
@@ -518,7 +549,7 @@ cudaError_t group_create(Ctx* const* ctxs, double* const* outs, int k, GroupPlan
         P.nb.push_back(x.Np / kNB);
         P.co.push_back(ns); P.po.push_back(ms); P.oo.push_back(ts); P.zo.push_back(zs); P.dofs.push_back(ds);
         P.dig_off.push_back(dg);
-        ns += x.n; ms += x.m; ts += x.t; zs += x.Np * x.Np; ds += x.Np; dg += (int64_t)P.s * x.Np * 256;
+        ns += x.n; ms += x.m; ts += x.t; zs += x.Np * x.Np; ds += x.Np; dg += (int64_t)P.s * x.Np * kGroupDigitK;
         np += x.npairs; ne += x.nent;
     }
     P.co.push_back(ns); P.po.push_back(ms); P.oo.push_back(ts);

@@ -152,6 +152,14 @@ void launch_upd_obs(Ctx& c, int64_t k, const ccov_obs* add, const double* add_co
 // ---- surrogate features (k_surrogate.cu) ----
 void surr_launch_features(Ctx& c, float* feat, double* scale);
 constexpr int kSurrGaugeBlocks = 152;
+constexpr int kGroupDigitK = 512;   // digit columns per row of the grouped batch's digit buffers
+// Sub-panels per group of the mixed step (d): four (trailing updates with
+// K = 512) for scenes of at least 64 sub-panels of 128 columns and at most
+// five digits, else two (K = 256): below that size the in-group launches
+// cost more than the longer K saves.  The single-scene path and the grouped
+// batch take the same groups, so their results agree bit for bit.
+constexpr int64_t kGroup4MinBlocks = 64;
+inline int64_t mixed_group_max(int s, int64_t nb) { return s <= 5 && nb >= kGroup4MinBlocks ? 4 : 2; }
 void surr_launch_gauge_rows(Ctx& c, const double* scale, double* q);
 
 // ---- mixed path (k_mixed.cu) ----

@@ -19,7 +19,7 @@
 //
 // Blocking: 128-column sub-panels factored and inverted one at a time, with
 // the big trailing updates applied for four sub-panels at once (K = 512; two,
-// K = 256, for s = 6 and in the grouped batch).  The
+// K = 256, for scenes under 64 sub-panels and for s = 6).  The
 // diagonal blocks are factored and inverted by one CTA in double-single
 // arithmetic.  The triangular inverse runs on a second stream, each pair of
 // row blocks as soon as the Cholesky has finished the same pair of columns,
@@ -52,7 +52,6 @@ constexpr int kCTile = kCBox;                              // 16 KB: a quarter o
 constexpr int kFX = 42;                                    // fixed point of X = L^-1
 constexpr int kFL = 60;                                    // fixed point of Z_s and L
 constexpr int kKMax = 512;                                 // digit columns of the per-scene buffers
-constexpr int kKMaxGroup = 256;                            // of the grouped batch's buffers
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;              // producer, MMA, epilogue warps
 constexpr int kEpiCols = kBN / (kEpiWarps / 4);            // tile columns per epilogue thread
@@ -1288,14 +1287,16 @@ int64_t grp_gram_blocks(int64_t ncols) { return (ncols + kGW - 1) / kGW; }
 
 void grp_slice_rows(cudaStream_t st, int K, const SliceRowsP* P, const int64_t* pre, int k, int64_t blocks,
                     int* flag) {
-    if (K == 256) slice_rows_grouped<256><<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
+    if (K == 512) slice_rows_grouped<512><<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
+    else if (K == 256) slice_rows_grouped<256><<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
     else slice_rows_grouped<128><<<(unsigned)blocks, 256, 0, st>>>(P, pre, k, flag);
 }
 
 void grp_slice_cols(cudaStream_t st, int K, const SliceColsP* P, const int64_t* pre, int k, int64_t blocks,
                     int* flag) {
     const size_t smem = (size_t)K * 33 * 8;
-    if (K == 256) slice_cols_grouped<256><<<(unsigned)blocks, 256, smem, st>>>(P, pre, k, flag);
+    if (K == 512) slice_cols_grouped<512><<<(unsigned)blocks, 256, smem, st>>>(P, pre, k, flag);
+    else if (K == 256) slice_cols_grouped<256><<<(unsigned)blocks, 256, smem, st>>>(P, pre, k, flag);
     else slice_cols_grouped<128><<<(unsigned)blocks, 256, smem, st>>>(P, pre, k, flag);
 }
 
@@ -1337,7 +1338,13 @@ cudaError_t grp_gemm(cudaStream_t st, int s, int K, const GemmProblem* probs, in
     std::memset(&none, 0, sizeof none);
 #define CCOV_OZG(S_, K_) cudaLaunchKernelEx(&cfg, ozaki_gemm_kernel<S_, K_, true>, none, none, g, probs, nprobs)
     cudaError_t e;
-    if (K == 256) {
+    if (K == 512) {
+        switch (s) {
+            case 4: e = CCOV_OZG(4, 512); break;
+            case 5: e = CCOV_OZG(5, 512); break;
+            default: e = cudaErrorInvalidValue; break;   // six digits group by pairs (K <= 256)
+        }
+    } else if (K == 256) {
         switch (s) {
             case 4: e = CCOV_OZG(4, 256); break;
             case 5: e = CCOV_OZG(5, 256); break;
@@ -1376,6 +1383,9 @@ cudaError_t mixed_setup() {
     if ((e = cudaFuncSetAttribute(slice_cols_grouped<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   256 * 33 * 8)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(slice_cols_grouped<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  512 * 33 * 8)) != cudaSuccess)
+        return e;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1387,7 +1397,7 @@ bool mixed_make_c_map(CUtensorMap* map, long long* buf, int64_t rows, int64_t co
 }
 
 bool mixed_make_b_map(CUtensorMap* map, __nv_bfloat16* buf, int s, int64_t Np) {
-    return make_b_map(map, buf, s, Np, kKMaxGroup);
+    return make_b_map(map, buf, s, Np, kGroupDigitK);
 }
 
 int mixed_stages(int s) { return pick_stages(s); }
@@ -1816,11 +1826,12 @@ cudaError_t mixed_factor_inverse(Ctx& c) {
     }
     auto Zat = [&](int64_t row, int64_t col) { return Zq + row * Np + col; };
     auto Rat = [&](int64_t row, int64_t col) { return st.R + row * Np + col; };
-    // Sub-panels in groups of m = 4 (2 for six digits, whose eight
-    // accumulators hold K = 256 at most; fewer at the end): inside a group,
-    // each sub-panel's update of the group's later columns (K = 128); after
-    // it, one trailing update with all m sub-panels (K = 128 m).
-    const int64_t gmax = st.s <= 5 ? 4 : 2;
+    // Sub-panels in groups of m = mixed_group_max (4, or 2 for small scenes
+    // and for six digits, whose eight accumulators hold K = 256 at most;
+    // fewer at the end): inside a group, each sub-panel's update of the
+    // group's later columns (K = 128); after it, one trailing update with all
+    // m sub-panels (K = 128 m).
+    const int64_t gmax = mixed_group_max(st.s, nb);
     auto group_len = [&](int64_t p) {
         const int64_t left = nb - p;
         return left >= gmax ? gmax : (left >= 2 ? 2 : 1);

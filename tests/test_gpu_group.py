@@ -2,8 +2,9 @@
 step of every scene in one launch per step.
 
 Every sum of the grouped form runs in the same order as in a scene's own
-launches (the same pair lists, the same 2048 partial sums of W7 per scene,
-integer tensor-core products that commute exactly), so the grouped batch must
+launches (the same pair lists, the same W7 partial sums per scene, the same
+sub-panel groups, integer tensor-core products that commute exactly), so the
+grouped batch must
 equal the per-scene batch and the single-scene path bit for bit; against the
 oracle it is held to the mixed form's bar (four measures, 1e-6)."""
 import numpy as np
@@ -49,6 +50,25 @@ def test_grouped_equals_per_scene_and_single_scene_bit_for_bit():
         assert np.array_equal(a.cpu().numpy(), ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED))
     for i in (0, int(np.argmax([sc.n for sc in scenes]))):
         assert_blocks_close(og[i].cpu().numpy(), covariance.camera_covariance(scenes[i]), MIXED_TOL)
+
+
+def test_grouped_with_groups_of_four_and_pairs_equals_single_scene_bit_for_bit():
+    """A 950-camera scene (72 sub-panels: groups of four, K = 512 trailing
+    updates) in one grouped batch with small scenes (pairs, K = 256): every
+    scene's blocks are those of its own single-scene step, bit for bit."""
+    torch = pytest.importorskip("torch")
+    scenes = [synth.shell_scene(n=950, m=95_000, seed=44)] + _scenes(3, 45, n_hi=120)
+    ctxs = [ccov.from_scene(sc, precision=ccov.CCOV_PREC_MIXED) for sc in scenes]
+    outs = [torch.zeros((sc.n, 9, 9), dtype=torch.float64, device="cuda") for sc in scenes]
+    try:
+        with ccov.Batch(ctxs, outs, form=ccov.CCOV_BATCH_GROUPED) as b:
+            assert b.info()["form"] == ccov.CCOV_BATCH_GROUPED
+            b.run()
+    finally:
+        for c in ctxs:
+            c.close()
+    for sc, o in zip(scenes, outs):
+        assert np.array_equal(o.cpu().numpy(), ccov.camera_covariances(sc, precision=ccov.CCOV_PREC_MIXED))
 
 
 def test_grouped_replay_reads_reloaded_inputs():
