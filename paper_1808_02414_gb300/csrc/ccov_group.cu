@@ -8,8 +8,9 @@
 // each scene's own dense matrix (per camera its scene, per scene the offset
 // and leading dimension of its matrix) and the 7x7 sums are kept per scene.
 // Step (d) (mixed precision) follows the single-scene schedule of
-// mixed_factor_inverse sub-panel pair by sub-panel pair; at each step every
-// sub-step is one grouped launch over the scenes that still have it (their
+// mixed_factor_inverse sub-panel by sub-panel, in each scene's own groups of
+// sub-panels; at each step every sub-step is one grouped launch over the
+// scenes that have it (their
 // parameter records and block prefixes were written to device memory when
 // the plan was built), the trailing-update GEMMs as one persistent kernel
 // over the tiles of all those scenes.  The Cholesky runs on one stream, the

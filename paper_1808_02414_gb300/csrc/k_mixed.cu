@@ -69,7 +69,7 @@ struct MixedState {
     int* expL = nullptr;             // their row exponents
     CUtensorMap mapBL;
     // the triangular inverse runs on a second stream with a second set of
-    // digit buffers, behind the Cholesky one pair of sub-panels at a time
+    // digit buffers, behind the Cholesky one group of sub-panels at a time
     __nv_bfloat16 *digP2 = nullptr, *digQ2 = nullptr;
     int *expP2 = nullptr, *expQ2 = nullptr;
     CUtensorMap mapBP2, mapBQ2;
