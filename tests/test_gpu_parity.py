@@ -85,6 +85,15 @@ def test_covariance_vs_oracle(case):
     np.testing.assert_allclose(got, np.transpose(got, (0, 2, 1)), rtol=0, atol=1e-12 * np.abs(got).max())
 
 
+@pytest.mark.parametrize("prec,tol", [(ccov.CCOV_PREC_FP64, FP64_TOL), (ccov.CCOV_PREC_MIXED, 1e-6)])
+def test_three_cameras_one_padded_block(prec, tol):
+    """The smallest well-posed scene: three cameras (N = 27 in one 128-row
+    block, 101 rows of padding; with two cameras the intrinsics are not
+    determined and the system is singular beyond the gauge)."""
+    sc = synth.ring_scene(n=3, m=40, track_len=3, seed=3)
+    assert_blocks_close(ccov.camera_covariances(sc, precision=prec), covariance.camera_covariance(sc), tol)
+
+
 def test_paper_route_and_closed_form_nullspace_agree_on_covariance():
     sc = synth.shell_scene(n=60, m=4000, seed=9)
     a = ccov.camera_covariances(sc, nullspace_route=ccov.CCOV_NULL_PAPER)
